@@ -1,0 +1,310 @@
+"""Patch geometry, fringes, donor search and Neville interpolation (oracle).
+
+Test infrastructure only (see oracle/__init__.py).
+
+Sec. 3.1-3.2: each patch is the image of Q = [0,1]^2 under a smooth map M_p;
+its grid is the image of a Cartesian parameter grid (eq. param-grid). Two map
+kinds are used by the workloads: affine boxes (C/I-type patches) and an
+annulus around the cylinder whose angular direction is periodic (a reading:
+the paper would use S-type patches, eq. param_S).
+Sec. 3.3: Jacobian J = dq/dx of the inverse map, grad_x = J^T grad_q
+(eq. general_curvilinear).
+Sec. 3.4: n-point fringe regions from the maximum-index-norm distance to the
+grid points on internal sides (eq. fringe_region, read with "< n"), donor
+choice (the patch where the receiver is farthest from the boundary) and a 3x3
+donor stencil with iterated 1-D quadratic interpolation in parameter space,
+evaluated by Neville's algorithm (Sec. 3.4.1). Donor points must not be
+receivers (Remark overlap_cond); the testing phase reports a violation.
+
+Readings (paper silent): patches that cover the obstacle are blanked inside a
+hole radius and their grid lines split into segments at blanked points; points
+next to blanked points count as internal-boundary points; the index distance
+is capped at `depth_cap`; the stencil is centred at rnd(s) (half up, as in
+eq. zeta) and, if it would touch a donor receiver or blanked point, shifted by
+the first valid offset in the order 0, -1, +1, -2, +2 (smallest |o1|+|o2|
+first); donor ties go to the lowest patch index.
+"""
+import numpy as np
+
+from paper_2506_16076_gb300 import workloads as W
+
+CONTAIN_TOL = 1e-9
+OFFSETS = (0, -1, 1, -2, 2)
+
+
+def rnd(t):
+    """Nearest integer with rnd(n + 1/2) = n + 1 (Sec. 5.2, after eq. zeta)."""
+    return np.floor(np.asarray(t) + 0.5).astype(np.int64)
+
+
+class PatchGeo:
+    def __init__(self, desc: W.PatchDesc, params: W.Params):
+        self.desc = desc
+        self.kind = desc.kind
+        self.n1, self.n2 = desc.n1, desc.n2
+        self.periodic1 = desc.kind == W.OGRID
+        # parameter spacings (eq. param-grid without the sub-patch vicinity; periodic: 1/n)
+        self.h1 = 1.0 / self.n1 if self.periodic1 else 1.0 / (self.n1 - 1)
+        self.h2 = 1.0 / (self.n2 - 1)
+        self.x, self.y = W.patch_xy(desc)
+        self._metrics()
+        self._spacings()
+        self._blank()
+        self._depth(params)
+        self.receiver = (~self.blank) & (self.depth < params.n_f)
+        self.gen = (~self.blank) & (self.depth >= params.n_v)
+        self._segments(params)
+
+    # Sec. 3.3: J = dq/dx
+    def _metrics(self):
+        if self.kind == W.AFFINE:
+            x0, x1, y0, y1 = self.desc.geom
+            z = np.zeros((self.n2, self.n1))
+            self.J = np.stack([z + 1.0 / (x1 - x0), z, z, z + 1.0 / (y1 - y0)])  # J1x, J1y, J2x, J2y
+        else:
+            xc, yc, r0, r1 = self.desc.geom
+            dx, dy = self.x - xc, self.y - yc
+            r = np.hypot(dx, dy)
+            c, s = dx / r, dy / r
+            self.J = np.stack([-s / (2 * np.pi * r), c / (2 * np.pi * r), c / (r1 - r0), s / (r1 - r0)])
+            self.cos, self.sin = c, s
+
+    def _spacings(self):
+        """h_hat (max) and h_tilde (min) distance between index-adjacent points (Sec. 5.1, eq. CFL)."""
+        if self.kind == W.AFFINE:
+            x0, x1, y0, y1 = self.desc.geom
+            hx, hy = (x1 - x0) / (self.n1 - 1), (y1 - y0) / (self.n2 - 1)
+            self.hhat, self.htil = max(hx, hy), min(hx, hy)
+        else:
+            xc, yc, r0, r1 = self.desc.geom
+            dr = (r1 - r0) / (self.n2 - 1)
+            ch = 2.0 * np.sin(np.pi / self.n1)
+            self.hhat, self.htil = max(dr, r1 * ch), min(dr, r0 * ch)
+
+    def _blank(self):
+        hx, hy, R = self.desc.hole
+        if R > 0 and self.kind == W.AFFINE:
+            dx, dy = self.x - hx, self.y - hy
+            self.blank = (dx * dx + dy * dy) < R * R
+        else:
+            self.blank = np.zeros((self.n2, self.n1), bool)
+
+    def _dilate(self, m):
+        out = m.copy()
+        if self.periodic1:
+            for s in (-1, 1):
+                out |= np.roll(m, s, axis=1)
+        else:
+            out[:, 1:] |= m[:, :-1]
+            out[:, :-1] |= m[:, 1:]
+        o2 = out.copy()
+        o2[1:, :] |= out[:-1, :]
+        o2[:-1, :] |= out[1:, :]
+        return o2
+
+    def _depth(self, params):
+        """Capped max-index-norm distance to internal-boundary points (eq. fringe_region)."""
+        side = self.desc.side
+        I = np.zeros((self.n2, self.n1), bool)
+        if side[0] == W.INTERNAL:
+            I[:, 0] = True
+        if side[1] == W.INTERNAL:
+            I[:, -1] = True
+        if side[2] == W.INTERNAL:
+            I[0, :] = True
+        if side[3] == W.INTERNAL:
+            I[-1, :] = True
+        I |= self._dilate(self.blank) & ~self.blank
+        I &= ~self.blank
+        cap = params.depth_cap
+        depth = np.full((self.n2, self.n1), cap, np.int64)
+        reached = I.copy()
+        depth[I] = 0
+        for k in range(1, cap):
+            nxt = self._dilate(reached)
+            new = nxt & ~reached
+            depth[new] = k
+            reached = nxt
+            if reached.all():
+                break
+        depth[self.blank] = 0
+        self.depth = depth
+
+    def _segments(self, params):
+        """Maximal runs of non-blanked points along each grid line (q1 rows, q2 columns)."""
+        self.seg1, self.seg2 = [], []  # (line index, start, length, periodic)
+        for j in range(self.n2):
+            if self.periodic1:
+                self.seg1.append((j, 0, self.n1, True))
+            else:
+                self.seg1 += [(j, a, n, False) for a, n in _runs(~self.blank[j, :])]
+        for i in range(self.n1):
+            self.seg2 += [(i, a, n, False) for a, n in _runs(~self.blank[:, i])]
+        d = params.d
+        self.nodiff = self.blank.copy()  # points where a derivative is not defined (set to 0)
+        for (j, a, n, per) in self.seg1:
+            if not per and n < 2 * d:
+                self.nodiff[j, a:a + n] = True
+        for (i, a, n, per) in self.seg2:
+            if n < 2 * d:
+                self.nodiff[a:a + n, i] = True
+
+    # inverse map: physical point -> fractional grid indices (s1, s2)
+    def frac_index(self, x, y):
+        if self.kind == W.AFFINE:
+            x0, x1, y0, y1 = self.desc.geom
+            return (x - x0) / (x1 - x0) * (self.n1 - 1), (y - y0) / (y1 - y0) * (self.n2 - 1)
+        xc, yc, r0, r1 = self.desc.geom
+        th = np.mod(np.arctan2(y - yc, x - xc), 2 * np.pi)
+        r = np.hypot(x - xc, y - yc)
+        return th / (2 * np.pi) * self.n1, (r - r0) / (r1 - r0) * (self.n2 - 1)
+
+    def contains(self, s1, s2):
+        ok2 = (s2 >= -CONTAIN_TOL) & (s2 <= self.n2 - 1 + CONTAIN_TOL)
+        if self.periodic1:
+            ok1 = np.ones_like(ok2)
+        else:
+            ok1 = (s1 >= -CONTAIN_TOL) & (s1 <= self.n1 - 1 + CONTAIN_TOL)
+        ok = ok1 & ok2
+        z1, z2 = self.nearest(s1, s2)
+        ok &= ~self.blank[z2, z1]
+        return ok
+
+    def nearest(self, s1, s2):
+        """zeta of eq. zeta as integer indices (clamped / wrapped into the grid)."""
+        z1, z2 = rnd(s1), rnd(s2)
+        z1 = np.mod(z1, self.n1) if self.periodic1 else np.clip(z1, 0, self.n1 - 1)
+        return z1, np.clip(z2, 0, self.n2 - 1)
+
+    def bbox(self):
+        return self.x.min(), self.x.max(), self.y.min(), self.y.max()
+
+
+def _runs(mask):
+    out, a = [], None
+    for i, m in enumerate(mask):
+        if m and a is None:
+            a = i
+        if not m and a is not None:
+            out.append((a, i - a))
+            a = None
+    if a is not None:
+        out.append((a, len(mask) - a))
+    return out
+
+
+def stencil_search(g: PatchGeo, s1, s2):
+    """Stencil start (a1, a2) and validity for fractional indices s1, s2 (arrays)."""
+    c1, c2 = rnd(s1), rnd(s2)
+    bad = g.blank | g.receiver
+    cands = sorted(((o1, o2) for o1 in OFFSETS for o2 in OFFSETS),
+                   key=lambda o: (abs(o[0]) + abs(o[1]), OFFSETS.index(o[0]), OFFSETS.index(o[1])))
+    a1 = np.zeros_like(c1)
+    a2 = np.zeros_like(c2)
+    found = np.zeros(c1.shape, bool)
+    for o1, o2 in cands:
+        b1, b2 = c1 - 1 + o1, c2 - 1 + o2
+        ok = ~found & (b2 >= 0) & (b2 <= g.n2 - 3)
+        if not g.periodic1:
+            ok &= (b1 >= 0) & (b1 <= g.n1 - 3)
+        for m2 in range(3):
+            for m1 in range(3):
+                i1 = np.mod(b1 + m1, g.n1) if g.periodic1 else np.clip(b1 + m1, 0, g.n1 - 1)
+                i2 = np.clip(b2 + m2, 0, g.n2 - 1)
+                ok &= ~bad[i2, i1]
+        a1 = np.where(ok, b1, a1)
+        a2 = np.where(ok, b2, a2)
+        found |= ok
+    return a1, a2, found
+
+
+def neville(nodes, vals, t):
+    """Neville's algorithm: value at t of the polynomial through (nodes[i], vals[i]).
+
+    vals: list of arrays (one per node); t: array. (Sec. 3.4.1.)"""
+    P = [v.copy() for v in vals]
+    n = len(nodes)
+    for m in range(1, n):
+        for i in range(n - m):
+            xi, xj = nodes[i], nodes[i + m]
+            P[i] = ((t - xj) * P[i] - (t - xi) * P[i + 1]) / (xi - xj)
+    return P[0]
+
+
+class Connectivity:
+    """Receivers of every patch with their donors and stencils (Sec. 3.4.1)."""
+
+    def __init__(self, geos, params):
+        self.geos = geos
+        self.items = []  # per patch: dict(recv flat idx, donor, a1, a2, t1, t2)
+        self.errors = []
+        boxes = [g.bbox() for g in geos]
+        for p, g in enumerate(geos):
+            rj, ri = np.nonzero(g.receiver)
+            n = len(rj)
+            xr, yr = g.x[rj, ri], g.y[rj, ri]
+            best_depth = np.full(n, -1, np.int64)
+            donor = np.full(n, -1, np.int64)
+            A1 = np.zeros(n, np.int64)
+            A2 = np.zeros(n, np.int64)
+            T1 = np.zeros(n)
+            T2 = np.zeros(n)
+            for q, h in enumerate(geos):
+                if q == p or n == 0 or not _overlap(boxes[p], boxes[q]):
+                    continue
+                s1, s2 = h.frac_index(xr, yr)
+                ok = h.contains(s1, s2)
+                a1, a2, found = stencil_search(h, s1, s2)
+                ok &= found
+                z1, z2 = h.nearest(s1, s2)
+                dep = h.depth[z2, z1]
+                better = ok & (dep > best_depth)  # strict: ties keep the lower patch index
+                best_depth = np.where(better, dep, best_depth)
+                donor = np.where(better, q, donor)
+                A1 = np.where(better, a1, A1)
+                A2 = np.where(better, a2, A2)
+                t1 = s1 - a1
+                if h.periodic1:
+                    t1 = np.mod(s1 - a1 + 0.5 * h.n1, h.n1) - 0.5 * h.n1  # unwrap across theta = 0
+                T1 = np.where(better, t1, T1)
+                T2 = np.where(better, s2 - a2, T2)
+            if n and (donor < 0).any():
+                self.errors.append((p, int((donor < 0).sum())))
+            self.items.append(dict(j=rj, i=ri, donor=donor, a1=A1, a2=A2, t1=T1, t2=T2))
+
+    def exchange(self, states):
+        """Overwrite every receiver with its interpolated donor value (Sec. 3.4.1), in place."""
+        nodes = (0.0, 1.0, 2.0)
+        new = []
+        for p, it in enumerate(self.items):
+            vals = np.zeros((states[p].shape[0], len(it["j"])))
+            for q in np.unique(it["donor"]):
+                if q < 0:
+                    continue
+                sel = it["donor"] == q
+                h, e = self.geos[q], states[q]
+                a1, a2, t1, t2 = it["a1"][sel], it["a2"][sel], it["t1"][sel], it["t2"][sel]
+                rows = []
+                for m2 in range(3):
+                    i2 = a2 + m2
+                    pts = []
+                    for m1 in range(3):
+                        i1 = np.mod(a1 + m1, h.n1) if h.periodic1 else a1 + m1
+                        pts.append(e[:, i2, i1])
+                    rows.append(neville(nodes, pts, t1))  # along q1 for each of 3 rows
+                vals[:, sel] = neville(nodes, rows, t2)  # then along q2
+            new.append(vals)
+        for p, it in enumerate(self.items):
+            if len(it["j"]):
+                states[p][:, it["j"], it["i"]] = new[p]
+        return states
+
+
+def _overlap(a, b):
+    return not (a[1] < b[0] or b[1] < a[0] or a[3] < b[2] or b[3] < a[2])
+
+
+def build(w: W.Workload):
+    geos = [PatchGeo(p, w.params) for p in w.patches]
+    conn = Connectivity(geos, w.params)
+    return geos, conn

@@ -1,0 +1,269 @@
+"""Seeded synthetic inputs: patch layouts, initial states, parameters.
+
+This module holds no arithmetic of the FC-SDNN method. It only describes
+geometry (patch kinds, point counts, bounds, side types, the blanked hole),
+the initial primitive states, and the flat state layout. Both the oracle
+(test infrastructure) and the CUDA path consume what it produces.
+
+Workloads (stand-ins for the paper's meshes, which are not published):
+  sod128      single affine patch [0,1]^2, 128x128, Sod tube along x
+  cyl_m3      O-grid r in [0.5,1.5] (512 theta x 96 r) + 4x4 affine 160x160
+              patches on [-4,8]x[-6,6] with 10-point overlaps, Mach 3 free stream
+  cyl_m2_half same geometry at half resolution (256x48, 80x80), Mach 2 at 2 deg
+  cyl_m25_32  [-8,16]x[-12,12] as 32x32 affine patches with seeded uneven sizes
+              48..384 (refined toward the body) + 1024x192 O-grid, Mach 25
+  cyl_m25_4096 64x64 affine patches with seeded sizes 64..512 + O-grid, Mach 25
+  The two seeded arrays use the rule n = nmin + round((nmax-nmin)*u*(1-a*dc/dmax)),
+  u ~ U[0,1) from numpy.random.default_rng(seed), dc = distance from the patch
+  centre to the cylinder centre; a is the taper coefficient.
+"""
+from dataclasses import dataclass, field
+import math
+import numpy as np
+
+# patch kinds
+AFFINE, OGRID = 0, 1
+# side types (side order: q1=0, q1=1, q2=0, q2=1)
+INTERNAL, DIRICHLET, SLIPWALL, OUTFLOW, PERIODIC = 0, 1, 2, 3, 4
+
+GAMMA = 1.4
+
+
+@dataclass
+class PatchDesc:
+    kind: int
+    n1: int
+    n2: int
+    geom: tuple  # AFFINE: (x0, x1, y0, y1); OGRID: (xc, yc, r0, r1)
+    side: tuple  # 4 side types
+    bc: tuple = ((0.0, 0.0, 0.0, 0.0),) * 4  # Dirichlet primitive (rho,u,v,p) per side
+    hole: tuple = (0.0, 0.0, -1.0)  # (xc, yc, R): blank points closer than R; R<=0: none
+
+    @property
+    def npts(self):
+        return self.n1 * self.n2
+
+
+@dataclass
+class Params:
+    d: int = 5
+    C0: int = 27
+    c_policy: int = 0  # 0: C = C0 on every line; 1: smallest C >= C0 with N+C 7-smooth
+    gamma: float = GAMMA
+    alpha_f: float = 10.0
+    p_f: int = 14
+    cfl: float = 0.5
+    n_f: int = 5
+    n_v: int = 9
+    win_r: int = 9
+    loc: int = 7
+    R: tuple = (1.5, 1.0, 0.5, 0.0)
+    depth_cap: int = 64
+
+
+@dataclass
+class Workload:
+    name: str
+    patches: list
+    params: Params
+    freestream: tuple  # primitive (rho, u, v, p)
+    init: str  # 'sod' or 'freestream'
+    steps: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def offsets(self):
+        off = [0]
+        for p in self.patches:
+            off.append(off[-1] + p.npts)
+        return off
+
+    @property
+    def total_points(self):
+        return self.offsets[-1]
+
+
+def sod128(n=128):
+    left, right = (1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1)
+    p = PatchDesc(AFFINE, n, n, (0.0, 1.0, 0.0, 1.0), (DIRICHLET, DIRICHLET, SLIPWALL, SLIPWALL),
+                  bc=(left, right, left, left))
+    return Workload("sod128" if n == 128 else f"sod{n}", [p], Params(d=5, C0=27, c_policy=0),
+                    freestream=left, init="sod", steps=100, extra={"left": left, "right": right, "x_split": 0.5})
+
+
+def _cart_array(nx, ny, x0, x1, y0, y1, nper, overlap, fs, hole, sizes=None):
+    """nx*ny affine patches tiling [x0,x1]x[y0,y1].
+
+    Uniform case (sizes None): every patch has nper points per side on one global
+    grid; neighbours share `overlap` grid lines. Seeded case: sizes[i][j] = (n1, n2)
+    and neighbouring patches overlap by `overlap` points of the finer neighbour.
+    Outer sides: left/bottom/top Dirichlet free stream, right outflow.
+    """
+    patches = []
+    if sizes is None:
+        ntot = nx * nper - (nx - 1) * overlap
+        hx = (x1 - x0) / (ntot - 1)
+        mty = ny * nper - (ny - 1) * overlap
+        hy = (y1 - y0) / (mty - 1)
+    for j in range(ny):
+        for i in range(nx):
+            if sizes is None:
+                n1 = n2 = nper
+                a = x0 + i * (nper - overlap) * hx
+                b = a + (nper - 1) * hx
+                c = y0 + j * (nper - overlap) * hy
+                e = c + (nper - 1) * hy
+            else:
+                n1, n2 = sizes[j][i]
+                wx, wy = (x1 - x0) / nx, (y1 - y0) / ny
+                # overlap half-width on each internal side, in the finer neighbour's spacing
+                def half(nself, nnb, w):
+                    return 0.5 * overlap * w / (max(nself, nnb) - 1)
+                lx = half(n1, sizes[j][i - 1][0], wx) if i > 0 else 0.0
+                rx = half(n1, sizes[j][i + 1][0], wx) if i < nx - 1 else 0.0
+                ly = half(n2, sizes[j - 1][i][1], wy) if j > 0 else 0.0
+                ry = half(n2, sizes[j + 1][i][1], wy) if j < ny - 1 else 0.0
+                a, b = x0 + i * wx - lx, x0 + (i + 1) * wx + rx
+                c, e = y0 + j * wy - ly, y0 + (j + 1) * wy + ry
+            side = (DIRICHLET if i == 0 else INTERNAL, OUTFLOW if i == nx - 1 else INTERNAL,
+                    DIRICHLET if j == 0 else INTERNAL, DIRICHLET if j == ny - 1 else INTERNAL)
+            patches.append(PatchDesc(AFFINE, n1, n2, (a, b, c, e), side, bc=(fs,) * 4, hole=hole))
+    return patches
+
+
+def _ogrid(nth, nr, r0, r1, fs):
+    return PatchDesc(OGRID, nth, nr, (0.0, 0.0, r0, r1), (PERIODIC, PERIODIC, SLIPWALL, INTERNAL), bc=(fs,) * 4)
+
+
+def cyl_m3(scale=1.0):
+    fs = (1.4, 3.0, 0.0, 1.0)
+    nc = int(round(160 * scale))
+    og = _ogrid(int(round(512 * scale)), int(round(96 * scale)), 0.5, 1.5, fs)
+    cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, nc, 10, fs, hole=(0.0, 0.0, 1.0))
+    return Workload("cyl_m3" if scale == 1.0 else f"cyl_m3_x{scale}", [og] + cart,
+                    Params(d=5, C0=27, c_policy=1), freestream=fs, init="freestream", steps=2000)
+
+
+def cyl_m2_half():
+    a = math.radians(2.0)
+    fs = (1.4, 2.0 * math.cos(a), 2.0 * math.sin(a), 1.0)
+    og = _ogrid(256, 48, 0.5, 1.5, fs)
+    cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, 80, 10, fs, hole=(0.0, 0.0, 1.0))
+    return Workload("cyl_m2_half", [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs,
+                    init="freestream", steps=400, extra={"mach": 2.0, "alpha_deg": 2.0})
+
+
+def seeded_sizes(nx, ny, nmin, nmax, seed, x0, x1, y0, y1, taper):
+    rng = np.random.default_rng(seed)
+    u = rng.random((ny, nx, 2))
+    wx, wy = (x1 - x0) / nx, (y1 - y0) / ny
+    cx = x0 + (np.arange(nx) + 0.5) * wx
+    cy = y0 + (np.arange(ny) + 0.5) * wy
+    dc = np.hypot(cx[None, :], cy[:, None])
+    f = 1.0 - taper * dc / dc.max()
+    n = nmin + np.round((nmax - nmin) * u * f[:, :, None]).astype(int)
+    return [[(int(n[j, i, 0]), int(n[j, i, 1])) for i in range(nx)] for j in range(ny)]
+
+
+def cyl_m25_array(nx, nmin, nmax, seed, taper, nth, nr, name):
+    fs = (1.4, 25.0, 0.0, 1.0)
+    sizes = seeded_sizes(nx, nx, nmin, nmax, seed, -8.0, 16.0, -12.0, 12.0, taper)
+    og = _ogrid(nth, nr, 0.5, 1.5, fs)
+    cart = _cart_array(nx, nx, -8.0, 16.0, -12.0, 12.0, None, 19, fs, hole=(0.0, 0.0, 1.0), sizes=sizes)
+    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs, init="freestream", steps=200,
+                    extra={"taper": taper, "seed": seed})
+
+
+def cyl_m25_32():
+    """32x32 uneven affine patches + 1024x192 O-grid, Mach 25 (about 30M points)."""
+    return cyl_m25_array(32, 48, 384, 3, 0.6, 1024, 192, "cyl_m25_32")
+
+
+def cyl_m25_4096():
+    """64x64 uneven affine patches + O-grid, Mach 25 (about 64M points with the taper below)."""
+    return cyl_m25_array(64, 64, 512, 5, 0.95, 1024, 192, "cyl_m25_4096")
+
+
+def small_multipatch():
+    """A tiny O-grid + 2x2 affine array around a cylinder: the oracle finishes it in seconds."""
+    fs = (1.4, 3.0, 0.0, 1.0)
+    og = _ogrid(128, 32, 0.5, 1.5, fs)
+    cart = _cart_array(2, 2, -2.5, 2.5, -2.5, 2.5, 64, 10, fs, hole=(0.0, 0.0, 0.85))
+    return Workload("small_multipatch", [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs,
+                    init="freestream", steps=20)
+
+
+WORKLOADS = {
+    "sod128": sod128,
+    "cyl_m3": cyl_m3,
+    "cyl_m2_half": cyl_m2_half,
+    "cyl_m25_32": cyl_m25_32,
+    "cyl_m25_4096": cyl_m25_4096,
+    "small_multipatch": small_multipatch,
+}
+
+
+# ---------------------------------------------------------------- grids (geometry only)
+
+def patch_xy(p: PatchDesc):
+    """Physical coordinates (x, y), each shape (n2, n1), of a patch's grid points."""
+    i = np.arange(p.n1)
+    j = np.arange(p.n2)
+    if p.kind == AFFINE:
+        x0, x1, y0, y1 = p.geom
+        x = x0 + (x1 - x0) * i / (p.n1 - 1)
+        y = y0 + (y1 - y0) * j / (p.n2 - 1)
+        return np.broadcast_to(x[None, :], (p.n2, p.n1)).copy(), np.broadcast_to(y[:, None], (p.n2, p.n1)).copy()
+    xc, yc, r0, r1 = p.geom
+    th = 2.0 * np.pi * i / p.n1
+    r = r0 + (r1 - r0) * j / (p.n2 - 1)
+    return xc + r[:, None] * np.cos(th)[None, :], yc + r[:, None] * np.sin(th)[None, :]
+
+
+def prim_to_cons(rho, u, v, p, gamma=GAMMA):
+    """Initial-condition construction from primitive states (eq. perfect_gas)."""
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def initial_state(w: Workload):
+    """List of per-patch conserved states, each (4, n2, n1), for the workload's IC.
+
+    Blanked points get the free-stream state (they never change)."""
+    out = []
+    for p in w.patches:
+        x, y = patch_xy(p)
+        if w.init == "sod":
+            L, R = w.extra["left"], w.extra["right"]
+            left = x < w.extra["x_split"]
+            prim = [np.where(left, L[k], R[k]) for k in range(4)]
+        else:
+            prim = [np.full(x.shape, w.freestream[k]) for k in range(4)]
+        out.append(prim_to_cons(*prim, gamma=w.params.gamma))
+    return out
+
+
+def flatten(per_patch):
+    """[4][P_tot] flat SoA layout: per patch, row-major (n2, n1), q1 fastest."""
+    return np.concatenate([a.reshape(a.shape[0], -1) for a in per_patch], axis=1)
+
+
+def unflatten(flat, w: Workload):
+    off = w.offsets
+    return [flat[:, off[k]:off[k + 1]].reshape(flat.shape[0], p.n2, p.n1) for k, p in enumerate(w.patches)]
+
+
+def random_smooth_state(w: Workload, seed, amp=0.05):
+    """Seeded smooth perturbation of the free stream (for RHS parity tests)."""
+    rng = np.random.default_rng(seed)
+    fs = w.freestream
+    out = []
+    kx, ky, ph = rng.uniform(0.5, 2.0, 4), rng.uniform(0.5, 2.0, 4), rng.uniform(0, 2 * np.pi, 4)
+    for p in w.patches:
+        x, y = patch_xy(p)
+        prim = []
+        for c in range(4):
+            base = fs[c] if c in (0, 3) else fs[c]
+            pert = amp * np.sin(kx[c] * x + ph[c]) * np.cos(ky[c] * y + 0.3 * ph[c])
+            prim.append(base * (1.0 + pert) if c in (0, 3) else base + amp * 3 * pert)
+        out.append(prim_to_cons(*prim, gamma=w.params.gamma))
+    return out

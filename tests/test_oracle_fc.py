@@ -1,0 +1,109 @@
+"""Pins of the oracle's FC-Gram continuation, derivative and filter (Sec. 2.2, Sec. 4.3)."""
+import numpy as np
+import pytest
+
+from oracle import fc
+
+
+def test_dft_matches_closed_forms():
+    L = 37
+    j = np.arange(L)
+    delta = np.zeros(L)
+    delta[0] = 1.0
+    assert np.allclose(fc.dft(delta), np.ones(L), atol=1e-14)
+    for m in (0, 1, 5, 36):
+        X = fc.dft(np.exp(2j * np.pi * m * j / L))
+        ref = np.zeros(L, complex)
+        ref[m] = L
+        assert np.abs(X - ref).max() < 1e-12
+    x = np.random.default_rng(0).normal(size=L)
+    assert np.abs(fc.idft(fc.dft(x)) - x).max() < 5e-14
+
+
+@pytest.mark.parametrize("d", [5, 2])
+def test_gram_basis_orthogonal_and_polynomial(d):
+    for C in (27, 40, 71):
+        Q, AL, AR = fc.load_tables(d, C)
+        assert AL.shape == (C, d) and AR.shape == (C, d)
+        assert np.abs(Q.T @ Q - np.eye(d)).max() < 1e-14
+        # columns of Q span the polynomials of degree < d on t = 0..d-1
+        V = np.vander(np.arange(d, dtype=float), d, increasing=True)
+        assert np.abs(Q @ (Q.T @ V) - V).max() < 1e-12 * np.abs(V).max()
+
+
+@pytest.mark.parametrize("C", [27, 33, 40, 55, 71])
+@pytest.mark.parametrize("N", [32, 100, 400])
+def test_fc_derivative_polynomials_below_d(N, C):
+    # Polynomial exactness of the Gram basis (Sec. 2.2): tolerance grows with N
+    # (derivative amplification ~ pi N) from the tables' ~1e-14 continuation accuracy.
+    d = 5
+    x = np.linspace(0.0, 1.0, N)
+    h = 1.0 / (N - 1)
+    for deg in range(d):
+        F = (x - 0.3) ** deg
+        dF = deg * (x - 0.3) ** (deg - 1) if deg else 0 * x
+        D = fc.fc_derivative(F, h, d, C)
+        assert np.abs(D - dF).max() <= 1.5e-13 * N * max(1.0, np.abs(dF).max()), (deg, N, C)
+
+
+def test_fc_derivative_degree_d_is_not_exact():
+    # a planted check on the pin above: degree d is outside the exact class
+    N, d, C = 64, 5, 27
+    x = np.linspace(0.0, 1.0, N)
+    D = fc.fc_derivative(x ** 9, 1.0 / (N - 1), d, C)
+    assert np.abs(D - 9 * x ** 8).max() > 1e-8
+
+
+def test_fc_derivative_convergence_smooth_nonperiodic():
+    errs = []
+    for N in (50, 100, 200, 400):
+        x = np.linspace(0.0, 1.0, N)
+        F = np.exp(np.sin(3 * x))
+        D = fc.fc_derivative(F, 1.0 / (N - 1), 5, 27)
+        errs.append(np.abs(D - 3 * np.cos(3 * x) * F).max())
+    rates = [np.log2(errs[k] / errs[k + 1]) for k in range(3)]
+    assert min(rates) > 3.5, (errs, rates)  # order d-1 = 4 for d = 5
+    assert errs[-1] < 3e-8  # max |F'| is about 4.4
+
+
+def test_fc_derivative_on_other_intervals_scales():
+    # derivative on [a, b] with spacing h scales as 1/h (Sec. 2.2, re-scaling to [0,1])
+    N = 80
+    x = np.linspace(2.0, 5.0, N)
+    F = np.sin(x)
+    D = fc.fc_derivative(F, 3.0 / (N - 1), 5, 27)
+    assert np.abs(D - np.cos(x)).max() < 5e-7  # fourth-order error at h = 3/79
+
+
+def test_periodic_derivative_and_filter_closed_forms():
+    N = 64
+    x = np.arange(N) / N
+    F = np.sin(2 * np.pi * 3 * x) + 0.5 * np.cos(2 * np.pi * 7 * x)
+    dF = 2 * np.pi * 3 * np.cos(2 * np.pi * 3 * x) - 0.5 * 2 * np.pi * 7 * np.sin(2 * np.pi * 7 * x)
+    assert np.abs(fc.periodic_derivative(F, 1.0 / N) - dF).max() < 1e-11
+    # sigma(0) = 1, sigma(+-1) = exp(-alpha) (eq. filtering)
+    assert fc.sigma(0, 10, 10.0, 14) == 1.0
+    assert abs(fc.sigma(5, 10, 10.0, 14) - np.exp(-10.0)) < 1e-16
+    assert abs(fc.sigma(-5, 10, 10.0, 14) - np.exp(-10.0)) < 1e-16
+    # each Fourier mode k is multiplied by sigma(2k/N); the Nyquist mode by exp(-10)
+    ref = np.exp(-10 * (6 / N) ** 14) * np.sin(2 * np.pi * 3 * x) + 0.5 * np.exp(-10 * (14 / N) ** 14) * np.cos(2 * np.pi * 7 * x)
+    assert np.abs(fc.periodic_filter(F, 10.0, 14) - ref).max() < 1e-14
+    nyq = np.cos(np.pi * np.arange(N))
+    assert np.abs(fc.periodic_filter(nyq, 10.0, 14) - np.exp(-10.0) * nyq).max() < 1e-14
+
+
+def test_fc_filter_keeps_smooth_lines():
+    N = 120
+    x = np.linspace(0, 1, N)
+    F = 1.0 + 0.3 * x - 0.2 * x ** 2
+    G = fc.fc_filter(F, 5, 27, 10.0, 14)
+    assert np.abs(G - F).max() < 1e-11  # continuation high modes are tiny but not zero
+
+
+def test_choose_C_policies():
+    assert fc.choose_C(128, 27, 0) == 27
+    for N in range(10, 1100):
+        C = fc.choose_C(N, 27, 1)
+        assert 27 <= C <= 71 and fc.is_7smooth(N + C)
+        assert all(not fc.is_7smooth(N + c) for c in range(27, C))
+    assert fc.choose_C(160, 27, 1) == 29  # 189 = 3^3 7
