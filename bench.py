@@ -1,0 +1,336 @@
+"""Benchmark of the multi-patch FC-SDNN operator: Euler RHS point-updates/s.
+
+One step = one time step of Algorithm 1 on the workload (viscosity, filter, CFL
+time step, five SSPRK-4 stages each followed by the boundary overwrite and the
+inter-patch exchange), all patches batched (one launch per pass and length
+class), captured once as a CUDA graph and replayed. A point-update is one active
+(non-blanked) grid point receiving one RHS evaluation, so a step is 5 x active
+points point-updates.
+
+  python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
+
+N > 1 (torchrun): independent replicas, one per GPU (the operator's only
+cross-patch coupling is the per-stage exchange; this build does not shard it).
+--impl reference: the CPU oracle on the host cores, on a bounded sample of the
+same workload, same metric and unit.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Euler RHS point-updates/s"
+UNIT = "point-updates/s"
+DEFAULT_WORKLOAD = "cyl_m25_32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-patches", type=int, default=3)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle on a bounded sample
+def oracle_sample_workload(w, npatch):
+    """The affine patches nearest the cylinder plus the O-grid: a bounded sample of the workload."""
+    from paper_2506_16076_gb300 import workloads as W
+    import math
+    aff = [p for p in w.patches if p.kind == W.AFFINE]
+    og = [p for p in w.patches if p.kind == W.OGRID]
+
+    def dist(p):
+        x0, x1, y0, y1 = p.geom
+        return math.hypot(0.5 * (x0 + x1), 0.5 * (y0 + y1))
+    aff.sort(key=dist)
+    pts = og[:1] + aff[:npatch] if npatch > 0 else og[:1]
+    return W.Workload(w.name + "_sample", pts, w.params, w.freestream, w.init, w.steps, w.extra)
+
+
+def oracle_bench(workload, steps, warmup, npatch, budget_s=None):
+    """Time full oracle steps on the sample; returns (point-updates/s, sample description, seconds)."""
+    from oracle import solver as S
+    from paper_2506_16076_gb300 import workloads as W
+    w = W.WORKLOADS[workload]()
+    ws = oracle_sample_workload(w, npatch)
+    sv = S.Solver(ws)
+    st = W.initial_state(ws)
+    active = sum(int((~g.blank).sum()) for g in sv.geos)
+    for n in range(warmup):
+        st = sv.step(st, n)
+    t0 = time.perf_counter()
+    done = 0
+    for n in range(steps):
+        st = sv.step(st, warmup + n)
+        done += 1
+        if budget_s and time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    desc = (f"{len(ws.patches)} of {len(w.patches)} patches of {workload} (O-grid + nearest affine patches), "
+            f"{active} active points, {done} full steps, direct-DFT oracle")
+    return active * 5 * done / el, desc, el, done
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
+def run_oracle_subprocess(workload, steps, warmup, npatch, budget_s):
+    """Run the oracle in a fresh process (spawned before any GPU work of that process)."""
+    env = dict(os.environ)
+    n = str(os.cpu_count() or 1)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = n
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_bench(%r, %d, %d, %d, %r); print(json.dumps(r))" % (ROOT, workload, steps, warmup,
+                                                                                npatch, budget_s))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    v, desc, el, done = json.loads(out.stdout.strip().splitlines()[-1])
+    return v, desc, el, done, int(n)
+
+
+# ---------------------------------------------------------------- clocks sampler
+class Clocks:
+    def __init__(self):
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms",
+                                          "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self, dev):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9 or f[0] != str(dev):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        pass
+    return p
+
+
+def main_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_16076_gb300 import fcsdnn, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU baseline runs first, in its own process, before this process touches the GPU
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, desc, el, done, cores = run_oracle_subprocess(args.workload, 2, 0, args.sample_patches, 30.0)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc + f", {el:.1f} s"}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": f"failed: {ex}"}
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = W.WORKLOADS[args.workload]()
+    t0 = time.perf_counter()
+    ctx = fcsdnn.Context(w)
+    init_s = time.perf_counter() - t0
+    e0 = torch.from_numpy(W.flatten(W.initial_state(w))).to(dev)
+    e = e0.clone()
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    mu = torch.zeros(ctx.P, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    GRAPH, FILTER, PERPATCH = fcsdnn.STEP_GRAPH, fcsdnn.STEP_FILTER, fcsdnn.STEP_PER_PATCH
+
+    def steps(k, flags, start):
+        for n in range(start, start + k):
+            ctx.rk_step(e, dt, mu, flags | (FILTER if n >= 1 else 0))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        steps(args.warmup, GRAPH, 0)
+        n0 = args.warmup
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks()
+        clocks.start()
+        l0 = ctx.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        steps(args.steps, GRAPH, n0)
+        ev1.record(stream)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches = ctx.launch_count() - l0
+        ms = ev0.elapsed_time(ev1)
+        ck = clocks.stop(local)
+        n0 += args.steps
+        status = ctx.sync_status(e)
+
+        # per-patch schedule on the same GPU (baseline of the batched launch), same step count
+        k_pp = max(1, min(args.steps, 3))
+        ev0.record(stream)
+        steps(k_pp, PERPATCH, n0)
+        ev1.record(stream)
+        stream.synchronize()
+        ms_pp = ev0.elapsed_time(ev1) / k_pp
+        n0 += k_pp
+
+        # per-kernel durations, live, with CUDA events on the launching stream
+        ctx.profile_reset()
+        ctx.profile(True)
+        steps(2, 0, n0)
+        ctx.profile(False)
+        prof = ctx.profile_read()
+        n0 += 2
+
+        # end to end through the public API with host buffers: H2D of the state, step, D2H of the result
+        host = e.cpu().pin_memory()
+        host_out = torch.empty_like(host).pin_memory()
+        k_e2e = max(1, min(args.steps, 5))
+        ev0.record(stream)
+        for n in range(n0, n0 + k_e2e):
+            e.copy_(host, non_blocking=True)
+            ctx.rk_step(e, dt, mu, GRAPH | FILTER)
+            host_out.copy_(e, non_blocking=True)
+        ev1.record(stream)
+        stream.synchronize()
+        ms_e2e = ev0.elapsed_time(ev1) / k_e2e
+
+    t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, ms_e2e = t[0].item(), t[1].item()
+    pu_step = 5 * ctx.active
+    value = world * pu_step * args.steps / (ms / 1e3)
+    e2e = world * pu_step / (ms_e2e / 1e3)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (FP64 pipe)
+    pk = peaks()
+    dom = max((k for k in prof if k in ("cart_q1", "cart_q2", "filter_q1", "filter_q2")),
+              key=lambda k: prof[k][0], default=None)
+    roof = None
+    if dom:
+        flops, nbytes, nl, npts = ctx.pass_stats(dom)
+        tot_ms, cnt = prof[dom]
+        avg_s = tot_ms / 1e3 / max(cnt, 1)
+        per_launch_flops = flops / max(cnt // 2 if dom.startswith("cart") else cnt // 2, 1)
+        # one pass launch group covers all its length classes; flops above are per full pass
+        groups = cnt
+        passes = 2 * (5 if dom.startswith("cart") else 1)  # profiled 2 steps
+        avg_pass_s = tot_ms / 1e3 / passes
+        sm_max = pk.get("sm_max_mhz", 2070.0)
+        fp64_peak = 152 * sm_max * 1e6 * 4 / 1e12  # 2 FP64 FMA lanes / clk / SM on GB300, TFLOP/s
+        ach = flops / avg_pass_s / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                "frac": round(ach / fp64_peak, 4), "traffic": None, "kernel": f"k_{dom}",
+                "pass_ms": round(avg_pass_s * 1e3, 3), "launches_per_pass": groups // passes,
+                "hbm_GBps": round(nbytes / avg_pass_s / 1e9, 1),
+                "hbm_frac_of_measured": round(nbytes / avg_pass_s / 1e9 / pk.get("hbm_gbs", 6787.9), 4),
+                "peak_note": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flops x max SM clock (probe measured 1.199 TF/s)"}
+        _ = per_launch_flops
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "points": ctx.P, "active_points": ctx.active,
+                   "patches": len(w.patches), "schedule": "batched, one launch per pass and length class, CUDA graph",
+                   "l2": "inputs larger than L2 (state %.2f GB)" % (32 * ctx.P / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU", "init_s": round(init_s, 2)},
+        "per_patch": {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
+                      "batched_speedup": ms_pp / (ms / args.steps)},
+        "kernels_ms_per_step": {k: round(v[0] / 2, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P, "d2h_bytes_per_step": 32 * ctx.P},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "state_status": int(status),
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    v, desc, el, done, cores = run_oracle_subprocess(args.workload, args.steps, args.warmup, args.sample_patches,
+                                                     None)
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
+           "ms_per_step": el / max(done, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

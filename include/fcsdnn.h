@@ -1,0 +1,173 @@
+/*
+ * fcsdnn.h -- C ABI of the GB300 multi-patch FC-SDNN spatial operator.
+ *
+ * The library evaluates, on one GPU in FP64, the spatial operator of the
+ * multi-patch FC-SDNN scheme of Bruno & Leibovici ("General-domain FC-based
+ * shock-dynamics solver I", arXiv 2506.16076) and advances it in time:
+ *   - FC-Gram continued spectral derivatives along every grid line
+ *     (Sec. 2.2, eqs. continuation and fc_der),
+ *   - 2-D Euler fluxes and the artificial-viscosity divergence in the
+ *     curvilinear form (Sec. 2.1, 2.3, 3.3, eq. general_curvilinear),
+ *   - SDNN-driven viscosity with the smoothing-blending operator (Sec. 5),
+ *   - inter-patch interpolation and boundary overwrite (Sec. 3.4, 4.2),
+ *   - the per-step spectral filter, the CFL time step and SSPRK-4 (Sec. 4, Alg. 1).
+ *
+ * Conventions
+ *   State layout: structure of arrays e[4][P] in FP64 (rho, rho u, rho v, E),
+ *   P = fc_state_size(); patch k occupies points [off_k, off_k + n1*n2) in
+ *   row-major (n2, n1) order, q1 fastest; off_k from fc_patch_offset().
+ *   Pointers named *_dev are device pointers owned by the caller, 16-byte
+ *   aligned. Host pointers (descriptors, tables, weights) are read during the
+ *   call only. Every call that takes a stream is asynchronous on that stream
+ *   (a cudaStream_t passed as void*, NULL = legacy default stream); device-side
+ *   errors (non-finite state, bounded-wait timeout) are raised into a device
+ *   flag that fc_sync_status() reads back. No call throws; every call returns
+ *   an fc_status and fc_last_error() describes the last failure of a context.
+ */
+#ifndef FCSDNN_H
+#define FCSDNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_ctx fc_ctx;
+
+typedef enum {
+  FC_OK = 0,
+  FC_ERR_INVALID = 1,       /* bad argument or descriptor */
+  FC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  FC_ERR_DONOR = 3,         /* donor-receiver condition violated (Sec. 3.4, Remark overlap_cond) */
+  FC_ERR_OVERLAP = 4,       /* a line too short for FC has points that are not receivers */
+  FC_ERR_NONFINITE = 5,     /* NaN/Inf or non-positive density/pressure detected on the device */
+  FC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  FC_ERR_UNIMPLEMENTED = 7,
+  FC_ERR_OOM = 8            /* device allocation failed */
+} fc_status;
+
+/* patch kinds (Sec. 3.1): affine box (C/I-type), annulus around an obstacle with a periodic angle */
+enum { FC_PATCH_AFFINE = 0, FC_PATCH_OGRID = 1 };
+/* side types, side order (q1=0, q1=1, q2=0, q2=1) (Sec. 3.4 internal/external sides, Sec. 4.2) */
+enum { FC_SIDE_INTERNAL = 0, FC_SIDE_DIRICHLET = 1, FC_SIDE_SLIPWALL = 2, FC_SIDE_OUTFLOW = 3, FC_SIDE_PERIODIC = 4 };
+
+/* One patch (Sec. 3.1-3.2). AFFINE: geom = (x0, x1, y0, y1), q1 -> x, q2 -> y.
+ * OGRID: geom = (xc, yc, r0, r1), q1 -> angle (periodic, n1 points), q2 -> radius.
+ * bc[s] = primitive (rho, u, v, p) imposed on side s when it is DIRICHLET.
+ * hole = (xc, yc, R): points with distance < R are blanked (R <= 0: none). */
+typedef struct {
+  int kind;
+  int n1, n2;
+  double geom[4];
+  int side[4];
+  double bc[4][4];
+  double hole[3];
+} fc_patch_desc;
+
+/* Method parameters. Defaults of the paper: gamma 1.4 (Sec. 2.1), alpha_f 10,
+ * p_f 14 (Sec. 4.3.1), CFL 0.5 (Sec. 6), n_f 5, n_v 9 (Sec. 3.4), window
+ * w_{0,9} (win_r 9, Sec. 5.2), 7x7 localisation (loc 7), R = (1.5,1,0.5,0) (Sec. 5.1).
+ * fc_tables: host array, [0]=d, [1]=Cmin, [2]=Cmax, then for C = Cmin..Cmax the
+ *   blocks Q (d x d), A_l (C x d), A_r (C x d), row-major (eq. continuation).
+ * c_policy 0: C = C0 on every line; 1: smallest C >= C0 with N + C 7-smooth.
+ * sdnn_w: host FP32 weights of the 7-16-16-4 classifier: W1[16][7], b1[16],
+ *   W2[16][16], b2[16], W3[4][16], b3[4] (sdnn_len = 420).
+ * depth_cap: cap of the index distance used to rank donors. */
+typedef struct {
+  int d, C0, c_policy;
+  double gamma, alpha_f;
+  int p_f;
+  double cfl;
+  int n_f, n_v, win_r, loc;
+  double R[4];
+  int depth_cap;
+  const double *fc_tables;
+  int fc_tables_len;
+  const float *sdnn_w;
+  int sdnn_len;
+} fc_params;
+
+/* fc_rk_step flags */
+enum {
+  FC_STEP_FILTER = 1,      /* apply the per-step spectral filter (Sec. 4.3.1) */
+  FC_STEP_FROZEN_MU = 2,   /* use mu_dev as given instead of computing it (Sec. 5) */
+  FC_STEP_PER_PATCH = 4,   /* one launch per patch and pass (baseline schedule) */
+  FC_STEP_FIXED_DT = 8,    /* use *dt_dev as the step instead of eq. CFL */
+  FC_STEP_GRAPH = 16       /* capture the step once and replay it as a CUDA graph */
+};
+
+/* Build a context: patch grids, metrics, fringes, donors and interpolation
+ * weights (Sec. 3, Alg. 1 line 2), FFT plans per continued length, viscosity
+ * windows and normalisers (eq. multipatch_W_norm). Checks the donor-receiver
+ * condition (FC_ERR_DONOR). Allocates all device workspaces. */
+fc_status fc_init_patches(fc_ctx **out, const fc_patch_desc *patches, int npatch, const fc_params *prm, void *stream);
+
+/* Number of points P (state has 4*P doubles) and per-patch offsets. */
+size_t fc_state_size(const fc_ctx *ctx);
+fc_status fc_patch_offset(const fc_ctx *ctx, int patch, size_t *offset);
+/* Number of non-blanked points (the points that receive an update). */
+size_t fc_active_points(const fc_ctx *ctx);
+
+/* rhs_dev = L[e_dev] (eq. semi-discrete) with viscosity mu_dev (P doubles);
+ * mu_dev NULL: mu is computed from e_dev (Sec. 5). L = 0 on blanked points
+ * and on lines too short for FC. */
+fc_status fc_rhs(fc_ctx *ctx, const double *e_dev, double *rhs_dev, const double *mu_dev, void *stream);
+
+/* mu_dev = Lambda[mu^[e_dev]] (eqs. V2D_unscaled, Lambda, viscosity);
+ * tau_dev (nullable, P int32): the smoothness class on generating points, 0 elsewhere. */
+fc_status fc_viscosity(fc_ctx *ctx, const double *e_dev, double *mu_dev, int32_t *tau_dev, void *stream);
+
+/* In-place per-step filter of rho, rho u, rho v, theta with E rebuilt (Sec. 4.3.1). */
+fc_status fc_filter(fc_ctx *ctx, double *e_dev, void *stream);
+
+/* In-place boundary overwrite followed by the inter-patch exchange (Sec. 4.2, Sec. 3.4.1). */
+fc_status fc_project(fc_ctx *ctx, double *e_dev, void *stream);
+
+/* *dt_dev = eq. (CFL) for state e_dev and viscosity mu_dev (device scalar). */
+fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, double *dt_dev, void *stream);
+
+/* One time step of Algorithm 1 in place on e_dev: project, viscosity (unless
+ * FROZEN_MU), filter (if FILTER), project, dt (unless FIXED_DT; written to
+ * *dt_dev), then five SSPRK-4 stages, each followed by the boundary overwrite
+ * and the exchange. mu_dev: P doubles, written (or read with FROZEN_MU). */
+fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
+
+/* Discrete adjoint of fc_rk_step with mu and dt frozen (no filter):
+ * lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev at the step that starts from e_n_dev. */
+fc_status fc_adjoint_step(fc_ctx *ctx, const double *e_n_dev, const double *mu_dev, const double *dt_dev,
+                          const double *lam_np1_dev, double *lam_n_dev, void *stream);
+
+/* Reads the device error flag (synchronises the stream): FC_OK, FC_ERR_NONFINITE or FC_ERR_TIMEOUT.
+ * check_state != 0 also scans e_dev (may be NULL otherwise) for NaN/Inf and rho, p <= 0. */
+fc_status fc_sync_status(fc_ctx *ctx, const double *e_dev, int check_state, void *stream);
+
+/* Number of kernel launches issued by this context so far (instrumentation). */
+uint64_t fc_launch_count(const fc_ctx *ctx);
+
+/* Kernel timing instrumentation. When enabled, every launch group of a call made
+ * outside graph capture is bracketed by CUDA events on the call's stream.
+ * fc_profile_read() synchronises the device, folds the recorded pairs into
+ * per-group totals and returns the number of groups (-1 on error); fc_profile_get()
+ * returns group k: its name (owned by the context), total milliseconds and launches. */
+fc_status fc_profile_enable(fc_ctx *ctx, int enable);
+int fc_profile_read(fc_ctx *ctx);
+fc_status fc_profile_get(const fc_ctx *ctx, int k, const char **name, double *ms, int *launches);
+fc_status fc_profile_reset(fc_ctx *ctx);
+
+/* Algorithmic work of one launch of a line pass ("cart_q1", "cart_q2", "filter_q1",
+ * "filter_q2"): FP64 flops by the conventional FFT count (5 L log2 L per complex
+ * transform) plus continuation, multiplier and pointwise work; compulsory HBM
+ * bytes; number of lines and points. Used to place a measured duration on the
+ * FP64 and HBM rooflines. */
+fc_status fc_pass_stats(const fc_ctx *ctx, const char *pass, double *flops, double *bytes, long long *lines,
+                        long long *points);
+
+const char *fc_last_error(const fc_ctx *ctx);
+void fc_destroy(fc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -74,11 +74,16 @@ def choose_C(N, C0, policy):
 def continuation(F, d, C):
     """Eq. (continuation): the C appended values of the FC-Gram continued vector.
 
-    F: (..., N) real. Returns (..., C)."""
+    F: (..., N) real. Returns (..., C). The matrices A_l, A_r of an accurate d = 5
+    continuation have entries of order 1e4 whose contributions cancel, so the
+    product is evaluated in extended precision and rounded once to FP64 (same
+    formula, smaller evaluation error)."""
     Q, AL, AR = load_tables(d, C)
-    Fl = F[..., :d]
-    Fr = F[..., -d:]
-    return (Fl @ Q) @ AL.T + (Fr @ Q) @ AR.T  # = A_l Q^T F_l + A_r Q^T F_r, row-wise
+    ld = np.longdouble
+    Fl = F[..., :d].astype(ld)
+    Fr = F[..., -d:].astype(ld)
+    ext = (Fl @ Q.astype(ld)) @ AL.T.astype(ld) + (Fr @ Q.astype(ld)) @ AR.T.astype(ld)  # A_l Q^T F_l + A_r Q^T F_r
+    return ext.astype(np.float64)
 
 
 @functools.lru_cache(maxsize=None)

@@ -1,0 +1,1348 @@
+// Host runtime of the C ABI (include/fcsdnn.h): geometry processing at initialisation
+// (Sec. 3, Alg. 1 line 2), FFT plans, line job queues, device workspaces, and the
+// orchestration of the per-step passes (Alg. 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fc_internal.h"
+
+using namespace fcx;
+
+namespace {
+
+constexpr double PI = 3.141592653589793;
+constexpr double CONTAIN_TOL = 1e-9;
+
+// SSPRK(5,4), Shu-Osher form (Sec. 4.1: the SSPRK-4 scheme the paper cites)
+constexpr double A20 = 0.444370493651235, A21 = 0.555629506348765, B1 = 0.391752226571890, B2 = 0.368410593050371;
+constexpr double A30 = 0.620101851488403, A32 = 0.379898148511597, B3 = 0.251891774271694;
+constexpr double A40 = 0.178079954393132, A43 = 0.821920045606868, B4 = 0.544974750228521;
+constexpr double A52 = 0.517231671970585, A53 = 0.096059710526147, B53 = 0.063692468666290;
+constexpr double A54 = 0.386708617503269, B54 = 0.226007483236906;
+
+struct Seg {
+  int line, a, n;
+  bool periodic;
+};
+
+struct HPatch {
+  fc_patch_desc d;
+  long long off = 0, gbase = -1;
+  int n1 = 0, n2 = 0;
+  bool periodic1 = false;
+  double h1 = 0, h2 = 0;       // parameter spacings
+  double hhat = 0, htil = 0;   // largest / smallest distance between index-adjacent points
+  std::vector<double> x, y;    // physical coordinates (n2*n1)
+  std::vector<uint8_t> blank, recv, gen, nodiff;
+  std::vector<int> depth;
+  std::vector<Seg> seg1, seg2;
+  double bx0, bx1, by0, by1;   // bounding box
+};
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+inline long long rnd_half_up(double t) { return (long long)std::floor(t + 0.5); }
+inline double pymod(double a, double n) { return a - n * std::floor(a / n); }
+
+}  // namespace
+
+struct fc_ctx {
+  std::string err;
+  fc_params prm{};
+  std::vector<double> fctab;  // copy of the packed tables
+  std::vector<float> sdnn;
+  int d = 5, Cmin = 0, Cmax = -1;
+  std::vector<HPatch> hp;
+  long long P = 0, Pg = 0, active = 0;
+  uint64_t launches = 0;
+
+  // device tables
+  std::vector<void*> allocs;
+  DevTables T{};
+  Plan* d_plans = nullptr;
+  double2* d_tw = nullptr;
+  double* d_rp = nullptr;
+  uint32_t* d_info = nullptr;
+  PatchDev* d_patches = nullptr;
+  double* d_J = nullptr;
+  float* d_sdnn = nullptr;
+  double* d_R = nullptr;
+  double* d_wtab = nullptr;
+
+  // job queues: [pass] -> batched order (length-descending, split by length class) and per-patch ranges
+  struct Queue {
+    Job* d = nullptr;
+    int n = 0;
+    std::vector<std::pair<int, int>> classes;   // (begin, Lmax) ranges of the batched order, end implied
+    std::vector<int> class_end;
+    Job* dpp = nullptr;                          // per-patch order
+    std::vector<int> pbeg, pend, plmax;
+  };
+  Queue q_cart1, q_cart2, q_gen1, q_gen2, q_filt1, q_filt2;
+  int* d_fix = nullptr;
+  int nfix = 0;
+  int* d_fcopy1 = nullptr;
+  int nfcopy1 = 0;
+  int* d_fcopy2 = nullptr;
+  int nfcopy2 = 0;
+  BcPt* d_bc = nullptr;
+  int nbc = 0;
+  Recv* d_recv = nullptr;
+  int nrecv = 0;
+  int* d_cross_dst = nullptr;
+  int* d_cross_ptr = nullptr;
+  int* d_cross_src = nullptr;
+  int ncross = 0;
+  double* d_den = nullptr;
+
+  // workspaces
+  double *d_B1 = nullptr, *d_B2 = nullptr, *d_B3 = nullptr, *d_R1 = nullptr, *d_G = nullptr;
+  double *d_phi = nullptr, *d_S = nullptr, *d_muhat = nullptr, *d_num = nullptr, *d_tmp = nullptr, *d_mu = nullptr;
+  double* d_dt = nullptr;
+  unsigned long long* d_pmax = nullptr;
+  int* d_flag = nullptr;
+
+  // kernel timing instrumentation (events around each launch group)
+  bool prof = false;
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+    int launches;
+  };
+  std::vector<ProfRec> prec;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  std::vector<std::string> pnames;
+  std::vector<double> pms;
+  std::vector<int> pcount;
+
+  cudaEvent_t ev() {
+    if (evused == evpool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      evpool.push_back(e);
+    }
+    return evpool[evused++];
+  }
+
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+  int gflags = -1;
+  uint64_t glaunches = 0;
+  cudaStream_t gstream = nullptr;
+
+  ~fc_ctx() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+  }
+
+  template <class T>
+  bool alloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+      *p = nullptr;
+      return false;
+    }
+    allocs.push_back(*p);
+    return true;
+  }
+  template <class T>
+  bool upload(T** p, const std::vector<T>& v) {
+    if (!alloc(p, v.size())) return false;
+    if (v.empty()) return true;
+    cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      err = std::string("cudaMemcpy failed: ") + cudaGetErrorString(e);
+      return false;
+    }
+    return true;
+  }
+};
+
+namespace {
+
+fc_status fail(fc_ctx* c, fc_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+fc_status cuda_check(fc_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, FC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return FC_OK;
+}
+
+// ---------------------------------------------------------------- geometry (Sec. 3)
+void grid_coords(HPatch& h) {
+  const fc_patch_desc& d = h.d;
+  h.x.resize((size_t)h.n1 * h.n2);
+  h.y.resize(h.x.size());
+  for (int j = 0; j < h.n2; ++j)
+    for (int i = 0; i < h.n1; ++i) {
+      const size_t k = (size_t)j * h.n1 + i;
+      if (d.kind == FC_PATCH_AFFINE) {
+        h.x[k] = d.geom[0] + (d.geom[1] - d.geom[0]) * i / (h.n1 - 1);
+        h.y[k] = d.geom[2] + (d.geom[3] - d.geom[2]) * j / (h.n2 - 1);
+      } else {
+        const double th = 2.0 * PI * i / h.n1;
+        const double r = d.geom[2] + (d.geom[3] - d.geom[2]) * j / (h.n2 - 1);
+        h.x[k] = d.geom[0] + r * std::cos(th);
+        h.y[k] = d.geom[1] + r * std::sin(th);
+      }
+    }
+  h.bx0 = *std::min_element(h.x.begin(), h.x.end());
+  h.bx1 = *std::max_element(h.x.begin(), h.x.end());
+  h.by0 = *std::min_element(h.y.begin(), h.y.end());
+  h.by1 = *std::max_element(h.y.begin(), h.y.end());
+}
+
+// fractional grid indices of a physical point (inverse of the patch map)
+inline void frac_index(const HPatch& h, double x, double y, double& s1, double& s2) {
+  const fc_patch_desc& d = h.d;
+  if (d.kind == FC_PATCH_AFFINE) {
+    s1 = (x - d.geom[0]) / (d.geom[1] - d.geom[0]) * (h.n1 - 1);
+    s2 = (y - d.geom[2]) / (d.geom[3] - d.geom[2]) * (h.n2 - 1);
+  } else {
+    const double th = pymod(std::atan2(y - d.geom[1], x - d.geom[0]), 2.0 * PI);
+    const double r = std::hypot(x - d.geom[0], y - d.geom[1]);
+    s1 = th / (2.0 * PI) * h.n1;
+    s2 = (r - d.geom[2]) / (d.geom[3] - d.geom[2]) * (h.n2 - 1);
+  }
+}
+
+inline void nearest(const HPatch& h, double s1, double s2, int& z1, int& z2) {
+  long long a = rnd_half_up(s1), b = rnd_half_up(s2);
+  if (h.periodic1) {
+    a %= h.n1;
+    if (a < 0) a += h.n1;
+  } else {
+    a = std::min<long long>(std::max<long long>(a, 0), h.n1 - 1);
+  }
+  b = std::min<long long>(std::max<long long>(b, 0), h.n2 - 1);
+  z1 = (int)a;
+  z2 = (int)b;
+}
+
+inline bool contains(const HPatch& h, double s1, double s2) {
+  if (!(s2 >= -CONTAIN_TOL && s2 <= h.n2 - 1 + CONTAIN_TOL)) return false;
+  if (!h.periodic1 && !(s1 >= -CONTAIN_TOL && s1 <= h.n1 - 1 + CONTAIN_TOL)) return false;
+  int z1, z2;
+  nearest(h, s1, s2, z1, z2);
+  return !h.blank[(size_t)z2 * h.n1 + z1];
+}
+
+void build_patch(HPatch& h, const fc_params& prm) {
+  const fc_patch_desc& d = h.d;
+  h.n1 = d.n1;
+  h.n2 = d.n2;
+  h.periodic1 = d.kind == FC_PATCH_OGRID;
+  h.h1 = h.periodic1 ? 1.0 / h.n1 : 1.0 / (h.n1 - 1);
+  h.h2 = 1.0 / (h.n2 - 1);
+  grid_coords(h);
+  if (d.kind == FC_PATCH_AFFINE) {
+    const double hx = (d.geom[1] - d.geom[0]) / (h.n1 - 1), hy = (d.geom[3] - d.geom[2]) / (h.n2 - 1);
+    h.hhat = std::max(hx, hy);
+    h.htil = std::min(hx, hy);
+  } else {
+    const double dr = (d.geom[3] - d.geom[2]) / (h.n2 - 1);
+    const double ch = 2.0 * std::sin(PI / h.n1);
+    h.hhat = std::max(dr, d.geom[3] * ch);
+    h.htil = std::min(dr, d.geom[2] * ch);
+  }
+  const size_t N = (size_t)h.n1 * h.n2;
+  h.blank.assign(N, 0);
+  if (d.kind == FC_PATCH_AFFINE && d.hole[2] > 0) {
+    const double R2 = d.hole[2] * d.hole[2];
+    for (size_t k = 0; k < N; ++k) {
+      const double dx = h.x[k] - d.hole[0], dy = h.y[k] - d.hole[1];
+      h.blank[k] = (dx * dx + dy * dy) < R2;
+    }
+  }
+  // internal-boundary points: points of internal sides, and non-blank points next to a blanked one
+  auto idx = [&](int i, int j) { return (size_t)j * h.n1 + i; };
+  std::vector<int> dep(N, prm.depth_cap);
+  std::vector<size_t> frontier;
+  for (int j = 0; j < h.n2; ++j)
+    for (int i = 0; i < h.n1; ++i) {
+      const size_t k = idx(i, j);
+      if (h.blank[k]) continue;
+      bool ib = (i == 0 && d.side[0] == FC_SIDE_INTERNAL) || (i == h.n1 - 1 && d.side[1] == FC_SIDE_INTERNAL) ||
+                (j == 0 && d.side[2] == FC_SIDE_INTERNAL) || (j == h.n2 - 1 && d.side[3] == FC_SIDE_INTERNAL);
+      for (int b = -1; b <= 1 && !ib; ++b)
+        for (int a = -1; a <= 1 && !ib; ++a) {
+          int ii = i + a, jj = j + b;
+          if (jj < 0 || jj >= h.n2) continue;
+          if (h.periodic1)
+            ii = (ii + h.n1) % h.n1;
+          else if (ii < 0 || ii >= h.n1)
+            continue;
+          if (h.blank[idx(ii, jj)]) ib = true;
+        }
+      if (ib) {
+        dep[k] = 0;
+        frontier.push_back(k);
+      }
+    }
+  // multi-source breadth-first search with 8-neighbour steps = max-index-norm distance (eq. fringe_region)
+  for (int lev = 1; lev < prm.depth_cap && !frontier.empty(); ++lev) {
+    std::vector<size_t> next;
+    for (size_t k : frontier) {
+      const int j = (int)(k / h.n1), i = (int)(k % h.n1);
+      for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) {
+          int ii = i + a, jj = j + b;
+          if (jj < 0 || jj >= h.n2) continue;
+          if (h.periodic1)
+            ii = (ii + h.n1) % h.n1;
+          else if (ii < 0 || ii >= h.n1)
+            continue;
+          const size_t q = idx(ii, jj);
+          if (dep[q] > lev) {
+            dep[q] = lev;
+            next.push_back(q);
+          }
+        }
+    }
+    frontier.swap(next);
+  }
+  for (size_t k = 0; k < N; ++k)
+    if (h.blank[k]) dep[k] = 0;
+  h.depth = dep;
+  h.recv.assign(N, 0);
+  h.gen.assign(N, 0);
+  for (size_t k = 0; k < N; ++k) {
+    if (h.blank[k]) continue;
+    h.recv[k] = dep[k] < prm.n_f;
+    h.gen[k] = dep[k] >= prm.n_v;
+  }
+  // segments: maximal runs of non-blank points along grid lines
+  h.seg1.clear();
+  h.seg2.clear();
+  for (int j = 0; j < h.n2; ++j) {
+    if (h.periodic1) {
+      h.seg1.push_back({j, 0, h.n1, true});
+      continue;
+    }
+    int a = -1;
+    for (int i = 0; i <= h.n1; ++i) {
+      const bool on = i < h.n1 && !h.blank[idx(i, j)];
+      if (on && a < 0) a = i;
+      if (!on && a >= 0) {
+        h.seg1.push_back({j, a, i - a, false});
+        a = -1;
+      }
+    }
+  }
+  for (int i = 0; i < h.n1; ++i) {
+    int a = -1;
+    for (int j = 0; j <= h.n2; ++j) {
+      const bool on = j < h.n2 && !h.blank[idx(i, j)];
+      if (on && a < 0) a = j;
+      if (!on && a >= 0) {
+        h.seg2.push_back({i, a, j - a, false});
+        a = -1;
+      }
+    }
+  }
+  h.nodiff = h.blank;
+  for (const Seg& s : h.seg1)
+    if (!s.periodic && s.n < 2 * prm.d)
+      for (int t = 0; t < s.n; ++t) h.nodiff[idx(s.a + t, s.line)] = 1;
+  for (const Seg& s : h.seg2)
+    if (s.n < 2 * prm.d)
+      for (int t = 0; t < s.n; ++t) h.nodiff[idx(s.line, s.a + t)] = 1;
+}
+
+// ---------------------------------------------------------------- FFT plans and continuation tables
+std::vector<int> factorize(int L) {
+  std::vector<int> f;
+  int m = L;
+  for (int r : {8, 4, 2, 3, 5, 7})
+    while (m % r == 0) {
+      f.push_back(r);
+      m /= r;
+    }
+  for (int p = 11; m > 1; p += 2)
+    while (m % p == 0) {
+      f.push_back(p);
+      m /= p;
+    }
+  return f;
+}
+
+bool smooth7(int n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- context build
+namespace {
+
+struct Builder {
+  fc_ctx* c;
+  std::map<int, int> plan_of_L;
+  std::vector<Plan> plans;
+  std::vector<double2> tw;
+  std::vector<double> rp;
+  std::map<int, int> fcm_of_C;
+
+  int plan(int L) {
+    auto it = plan_of_L.find(L);
+    if (it != plan_of_L.end()) return it->second;
+    Plan p{};
+    p.L = L;
+    std::vector<int> f = factorize(L);
+    p.nst = (int)f.size();
+    for (int s = 0; s < p.nst; ++s) p.rad[s] = f[s];
+    p.tw = (int)tw.size();
+    for (int e = 0; e < L; ++e) {
+      const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
+      double2 w;
+      w.x = (double)cosl(ang);
+      w.y = (double)sinl(ang);
+      tw.push_back(w);
+    }
+    p.sig = (int)rp.size();
+    const fc_params& prm = c->prm;
+    for (int t = 0; t < L; ++t) {
+      long double k = (2 * t <= L) ? t : t - L;
+      if (2 * t == L) k = L / 2.0L;
+      const long double z = 2.0L * k / (long double)L;
+      rp.push_back((double)(expl(-(long double)prm.alpha_f * powl(z, prm.p_f)) / (long double)L));
+    }
+    plans.push_back(p);
+    plan_of_L[L] = (int)plans.size() - 1;
+    return (int)plans.size() - 1;
+  }
+
+  // combined continuation matrices ML = A_l Q^T, MR = A_r Q^T for C points
+  int fcm(int C) {
+    auto it = fcm_of_C.find(C);
+    if (it != fcm_of_C.end()) return it->second;
+    const int d = c->d;
+    const double* base = c->fctab.data() + 3;
+    for (int cc = c->Cmin; cc < C; ++cc) base += d * d + 2 * cc * d;
+    const double* Q = base;
+    const double* AL = Q + d * d;
+    const double* AR = AL + C * d;
+    const int off = (int)rp.size();
+    // ML = A_l Q^T and MR = A_r Q^T (rows k, columns i), then uL = ML 1, vL = ML tau_l,
+    // uR = MR 1, vR = MR tau_r with tau_l = i, tau_r = i - (d - 1) (detrended evaluation)
+    std::vector<long double> M[2];
+    for (int which = 0; which < 2; ++which) {
+      const double* A = which ? AR : AL;
+      M[which].assign((size_t)C * d, 0.0L);
+      for (int k = 0; k < C; ++k)
+        for (int i = 0; i < d; ++i) {
+          long double s = 0;
+          for (int j = 0; j < d; ++j) s += (long double)A[k * d + j] * (long double)Q[i * d + j];
+          M[which][(size_t)k * d + i] = s;
+        }
+      for (long double v : M[which]) rp.push_back((double)v);
+    }
+    for (int which = 0; which < 2; ++which)
+      for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < C; ++k) {
+          long double s = 0;
+          for (int i = 0; i < d; ++i) {
+            const long double tau = which == 0 ? (long double)i : (long double)(i - (d - 1));
+            s += M[which][(size_t)k * d + i] * (pass == 0 ? 1.0L : tau);
+          }
+          rp.push_back((double)s);
+        }
+    fcm_of_C[C] = off;
+    return off;
+  }
+
+  int choose_C(int N) {
+    const fc_params& prm = c->prm;
+    if (prm.c_policy == 0) return prm.C0;
+    int C = prm.C0;
+    while (!smooth7(N + C)) ++C;
+    return C;
+  }
+};
+
+void make_queue(fc_ctx* c, fc_ctx::Queue& q, std::vector<Job>& jobs, const std::vector<Plan>& plans, int npatch,
+                bool& ok) {
+  // per-patch order: stable by patch
+  std::vector<Job> pp = jobs;
+  std::stable_sort(pp.begin(), pp.end(), [](const Job& a, const Job& b) { return a.patch < b.patch; });
+  q.pbeg.assign(npatch, 0);
+  q.pend.assign(npatch, 0);
+  q.plmax.assign(npatch, 0);
+  for (int k = 0; k < (int)pp.size(); ++k) {
+    const int p = pp[k].patch;
+    if (q.pend[p] == 0) q.pbeg[p] = k;
+    q.pend[p] = k + 1;
+    q.plmax[p] = std::max(q.plmax[p], plans[pp[k].plan].L);
+  }
+  // batched order: longest continued length first, split in power-of-two length classes
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [&](const Job& a, const Job& b) { return plans[a.plan].L > plans[b.plan].L; });
+  q.n = (int)jobs.size();
+  q.classes.clear();
+  q.class_end.clear();
+  int k = 0;
+  while (k < q.n) {
+    const int Lmax = plans[jobs[k].plan].L;
+    int cls = 1;
+    while (cls < Lmax) cls <<= 1;
+    int e = k;
+    while (e < q.n && plans[jobs[e].plan].L > cls / 2) ++e;
+    q.classes.push_back({k, Lmax});
+    q.class_end.push_back(e);
+    k = e;
+  }
+  ok = ok && c->upload(&q.d, jobs) && c->upload(&q.dpp, pp);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- API
+extern "C" {
+
+fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch, const fc_params* prm, void* stream) {
+  if (!out || !patches || npatch <= 0 || !prm) return FC_ERR_INVALID;
+  *out = nullptr;
+  fc_ctx* c = new fc_ctx();
+  c->prm = *prm;
+  if (!prm->fc_tables || prm->fc_tables_len < 3) {
+    fprintf(stderr, "fc_init_patches: missing FC tables\n");
+    delete c;
+    return FC_ERR_INVALID;
+  }
+  c->fctab.assign(prm->fc_tables, prm->fc_tables + prm->fc_tables_len);
+  c->d = (int)c->fctab[0];
+  c->Cmin = (int)c->fctab[1];
+  c->Cmax = (int)c->fctab[2];
+  auto bad = [&](const std::string& m) {
+    fprintf(stderr, "fc_init_patches: %s\n", m.c_str());
+    delete c;
+    return FC_ERR_INVALID;
+  };
+  if (c->d != prm->d) return bad("table order d differs from params.d");
+  {
+    size_t need = 3;
+    for (int C = c->Cmin; C <= c->Cmax; ++C) need += (size_t)c->d * c->d + 2 * (size_t)C * c->d;
+    if (need != (size_t)prm->fc_tables_len) return bad("FC table length mismatch");
+  }
+  if (!prm->sdnn_w || prm->sdnn_len != SDNN_H * 7 + SDNN_H + SDNN_H * SDNN_H + SDNN_H + 4 * SDNN_H + 4)
+    return bad("SDNN weights missing or of the wrong size");
+  if (prm->win_r < 1 || prm->win_r > 32 || prm->n_f < 1 || prm->n_v < 1 || prm->depth_cap < 2) return bad("bad params");
+  c->sdnn.assign(prm->sdnn_w, prm->sdnn_w + prm->sdnn_len);
+  cudaStream_t st = (cudaStream_t)stream;
+  (void)st;
+
+  // ---- host geometry
+  c->hp.resize(npatch);
+  long long off = 0, goff = 0;
+  for (int p = 0; p < npatch; ++p) {
+    HPatch& h = c->hp[p];
+    h.d = patches[p];
+    if (h.d.n1 < 2 || h.d.n2 < 2 || (h.d.kind != FC_PATCH_AFFINE && h.d.kind != FC_PATCH_OGRID))
+      return bad("bad patch descriptor " + std::to_string(p));
+    build_patch(h, *prm);
+    h.off = off;
+    off += (long long)h.n1 * h.n2;
+    if (h.d.kind == FC_PATCH_OGRID) {
+      h.gbase = goff;
+      goff += (long long)h.n1 * h.n2;
+    }
+  }
+  c->P = off;
+  c->Pg = goff;
+  if (c->P >= (1LL << 31)) return bad("more than 2^31 points");
+  c->active = 0;
+  for (auto& h : c->hp)
+    for (auto b : h.blank) c->active += !b;
+
+  // ---- exchange: donors, stencils, weights (Sec. 3.4.1)
+  std::vector<Recv> recv;
+  {
+    static const int OFFS[5] = {0, -1, 1, -2, 2};
+    std::vector<std::pair<int, int>> cands;
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) cands.push_back({a, b});
+    std::stable_sort(cands.begin(), cands.end(), [](const std::pair<int, int>& u, const std::pair<int, int>& v) {
+      const int su = std::abs(OFFS[u.first]) + std::abs(OFFS[u.second]);
+      const int sv = std::abs(OFFS[v.first]) + std::abs(OFFS[v.second]);
+      if (su != sv) return su < sv;
+      if (u.first != v.first) return u.first < v.first;
+      return u.second < v.second;
+    });
+    long long missing = 0;
+    for (int p = 0; p < npatch; ++p) {
+      const HPatch& h = c->hp[p];
+      std::vector<int> near;
+      for (int q = 0; q < npatch; ++q) {
+        const HPatch& g = c->hp[q];
+        if (q != p && !(h.bx1 < g.bx0 || g.bx1 < h.bx0 || h.by1 < g.by0 || g.by1 < h.by0)) near.push_back(q);
+      }
+      for (int j = 0; j < h.n2; ++j)
+        for (int i = 0; i < h.n1; ++i) {
+          const size_t k = (size_t)j * h.n1 + i;
+          if (!h.recv[k]) continue;
+          const double x = h.x[k], y = h.y[k];
+          int best = -1, bdep = -1, ba1 = 0, ba2 = 0;
+          double bt1 = 0, bt2 = 0;
+          for (int q : near) {
+            const HPatch& g = c->hp[q];
+            double s1, s2;
+            frac_index(g, x, y, s1, s2);
+            if (!contains(g, s1, s2)) continue;
+            const long long c1 = rnd_half_up(s1), c2 = rnd_half_up(s2);
+            bool found = false;
+            long long a1 = 0, a2 = 0;
+            for (auto& cd : cands) {
+              const long long b1 = c1 - 1 + OFFS[cd.first], b2 = c2 - 1 + OFFS[cd.second];
+              if (b2 < 0 || b2 > g.n2 - 3) continue;
+              if (!g.periodic1 && (b1 < 0 || b1 > g.n1 - 3)) continue;
+              bool ok = true;
+              for (int m2 = 0; m2 < 3 && ok; ++m2)
+                for (int m1 = 0; m1 < 3 && ok; ++m1) {
+                  long long i1 = b1 + m1;
+                  if (g.periodic1) i1 = ((i1 % g.n1) + g.n1) % g.n1;
+                  const size_t kk = (size_t)(b2 + m2) * g.n1 + i1;
+                  if (g.blank[kk] || g.recv[kk]) ok = false;
+                }
+              if (ok) {
+                a1 = b1;
+                a2 = b2;
+                found = true;
+                break;
+              }
+            }
+            if (!found) continue;
+            int z1, z2;
+            nearest(g, s1, s2, z1, z2);
+            const int dp = g.depth[(size_t)z2 * g.n1 + z1];
+            if (dp > bdep) {
+              bdep = dp;
+              best = q;
+              ba1 = (int)a1;
+              ba2 = (int)a2;
+              bt1 = g.periodic1 ? pymod(s1 - a1 + 0.5 * g.n1, (double)g.n1) - 0.5 * g.n1 : s1 - a1;
+              bt2 = s2 - a2;
+            }
+          }
+          if (best < 0) {
+            ++missing;
+            continue;
+          }
+          const HPatch& g = c->hp[best];
+          Recv r{};
+          r.dst = (int)(h.off + (long long)k);
+          for (int m2 = 0; m2 < 3; ++m2)
+            for (int m1 = 0; m1 < 3; ++m1) {
+              long long i1 = ba1 + m1;
+              if (g.periodic1) i1 = ((i1 % g.n1) + g.n1) % g.n1;
+              r.src[3 * m2 + m1] = (int)(g.off + (long long)(ba2 + m2) * g.n1 + i1);
+            }
+          auto lag = [](double t, double* w) {
+            w[0] = 0.5 * (t - 1.0) * (t - 2.0);
+            w[1] = t * (2.0 - t);
+            w[2] = 0.5 * t * (t - 1.0);
+          };
+          lag(bt1, r.w1);
+          lag(bt2, r.w2);
+          recv.push_back(r);
+        }
+    }
+    if (missing) {
+      c->err = std::to_string(missing) + " receiver points have no valid donor (donor-receiver condition)";
+      fprintf(stderr, "fc_init_patches: %s\n", c->err.c_str());
+      delete c;
+      return FC_ERR_DONOR;
+    }
+  }
+  // short segments must consist of receivers only
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    for (size_t k = 0; k < h.nodiff.size(); ++k)
+      if (h.nodiff[k] && !h.blank[k] && !h.recv[k]) {
+        c->err = "patch " + std::to_string(p) + " has a line too short for FC containing non-receiver points";
+        fprintf(stderr, "fc_init_patches: %s\n", c->err.c_str());
+        delete c;
+        return FC_ERR_OVERLAP;
+      }
+  }
+
+  // ---- boundary overwrite lists (Sec. 4.2): slip then Dirichlet; Dirichlet wins at corners
+  std::vector<BcPt> bcs;
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    std::map<size_t, BcPt> m;
+    auto side_pts = [&](int s, std::vector<size_t>& v) {
+      v.clear();
+      if (s < 2) {
+        const int i = s == 0 ? 0 : h.n1 - 1;
+        for (int j = 0; j < h.n2; ++j) v.push_back((size_t)j * h.n1 + i);
+      } else {
+        const int j = s == 2 ? 0 : h.n2 - 1;
+        for (int i = 0; i < h.n1; ++i) v.push_back((size_t)j * h.n1 + i);
+      }
+    };
+    std::vector<size_t> pts;
+    for (int s = 0; s < 4; ++s) {
+      if (h.d.side[s] != FC_SIDE_SLIPWALL) continue;
+      side_pts(s, pts);
+      for (size_t k : pts) {
+        if (h.blank[k]) continue;
+        BcPt& b = m[k];
+        b.idx = (int)(h.off + (long long)k);
+        if (h.d.kind == FC_PATCH_AFFINE) {
+          b.mode |= (s < 2) ? 1 : 2;
+        } else {
+          const double dx = h.x[k] - h.d.geom[0], dy = h.y[k] - h.d.geom[1];
+          const double r = std::hypot(dx, dy);
+          b.mode |= 4;
+          b.nx = dx / r;
+          b.ny = dy / r;
+        }
+      }
+    }
+    for (int s = 0; s < 4; ++s) {
+      if (h.d.side[s] != FC_SIDE_DIRICHLET) continue;
+      side_pts(s, pts);
+      const double* q = h.d.bc[s];
+      const double rho = q[0], u = q[1], v = q[2], pr = q[3];
+      const double val[4] = {rho, rho * u, rho * v, pr / (prm->gamma - 1.0) + 0.5 * rho * (u * u + v * v)};
+      for (size_t k : pts) {
+        if (h.blank[k]) continue;
+        BcPt& b = m[k];
+        b.idx = (int)(h.off + (long long)k);
+        b.mode |= 8;
+        for (int cc = 0; cc < 4; ++cc) b.val[cc] = val[cc];
+      }
+    }
+    for (auto& kv : m) bcs.push_back(kv.second);
+  }
+
+  // ---- per-point flags and viscosity windows
+  std::vector<uint32_t> info((size_t)c->P);
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    std::vector<uint8_t> w1((size_t)h.n1 * h.n2, 7), w2(w1.size(), 7);
+    for (const Seg& s : h.seg1) {
+      if (!s.periodic && s.n < 7) continue;
+      for (int t = 0; t < s.n; ++t) {
+        const int i = s.a + t;
+        const int start = s.periodic ? i - 3 : std::min(std::max(i - 3, s.a), s.a + s.n - 7);
+        w1[(size_t)s.line * h.n1 + i] = (uint8_t)(i - start);
+      }
+    }
+    for (const Seg& s : h.seg2) {
+      if (s.n < 7) continue;
+      for (int t = 0; t < s.n; ++t) {
+        const int j = s.a + t;
+        const int start = std::min(std::max(j - 3, s.a), s.a + s.n - 7);
+        w2[(size_t)j * h.n1 + s.line] = (uint8_t)(j - start);
+      }
+    }
+    for (size_t k = 0; k < w1.size(); ++k) {
+      uint32_t f = ((uint32_t)p << PT_PATCH_SHIFT) | ((uint32_t)w1[k] << PT_W1_SHIFT) | ((uint32_t)w2[k] << PT_W2_SHIFT);
+      if (h.blank[k]) f |= PT_BLANK;
+      if (h.nodiff[k]) f |= PT_NODIFF;
+      if (h.gen[k]) f |= PT_GEN;
+      info[(size_t)h.off + k] = f;
+    }
+  }
+
+  // ---- line jobs
+  Builder B{c};
+  std::vector<Job> jc1, jc2, jg1, jg2, jf1, jf2;
+  std::vector<uint8_t> cov2((size_t)c->P, 0), fcov1((size_t)c->P, 0), fcov2((size_t)c->P, 0);
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    const bool aff = h.d.kind == FC_PATCH_AFFINE;
+    const double sx = aff ? (h.n1 - 1) / (h.d.geom[1] - h.d.geom[0]) : 1.0 / h.h1;
+    const double sy = aff ? (h.n2 - 1) / (h.d.geom[3] - h.d.geom[2]) : 1.0 / h.h2;
+    for (const Seg& s : h.seg1) {
+      if (!s.periodic && s.n < 2 * prm->d) continue;
+      Job J{};
+      J.base = h.off + (long long)s.line * h.n1 + s.a;
+      J.stride = 1;
+      J.n = s.n;
+      J.patch = p;
+      J.scale = sx;
+      if (s.periodic) {
+        J.C = 0;
+        J.fcm = -1;
+        J.plan = B.plan(s.n);
+      } else {
+        J.C = B.choose_C(s.n);
+        if (J.C < c->Cmin || J.C > c->Cmax) return bad("continuation length outside the FC tables");
+        J.fcm = B.fcm(J.C);
+        J.plan = B.plan(s.n + J.C);
+      }
+      J.gbase = aff ? -1 : h.gbase + (long long)s.line * h.n1 + s.a;
+      (aff ? jc1 : jg1).push_back(J);
+      jf1.push_back(J);
+      for (int t = 0; t < s.n; ++t) fcov1[(size_t)J.base + t] = 1;
+    }
+    for (const Seg& s : h.seg2) {
+      if (s.n < 2 * prm->d) continue;
+      Job J{};
+      J.base = h.off + (long long)s.a * h.n1 + s.line;
+      J.stride = h.n1;
+      J.n = s.n;
+      J.patch = p;
+      J.scale = sy;
+      J.C = B.choose_C(s.n);
+      if (J.C < c->Cmin || J.C > c->Cmax) return bad("continuation length outside the FC tables");
+      J.fcm = B.fcm(J.C);
+      J.plan = B.plan(s.n + J.C);
+      J.gbase = aff ? -1 : h.gbase + (long long)s.a * h.n1 + s.line;
+      (aff ? jc2 : jg2).push_back(J);
+      jf2.push_back(J);
+      for (int t = 0; t < s.n; ++t) {
+        cov2[(size_t)J.base + (size_t)t * h.n1] = 1;
+        fcov2[(size_t)J.base + (size_t)t * h.n1] = 1;
+      }
+    }
+    if (!aff)  // curvilinear patches: every point is finished by its q1 line in pass C
+      for (long long k = 0; k < (long long)h.n1 * h.n2; ++k) cov2[(size_t)(h.off + k)] = 1;
+  }
+  std::vector<int> fix, fc1, fc2;
+  for (long long k = 0; k < c->P; ++k) {
+    if (!cov2[k]) fix.push_back((int)k);
+    if (!(info[k] & PT_BLANK)) {
+      if (!fcov1[k]) fc1.push_back((int)k);
+      if (!fcov2[k]) fc2.push_back((int)k);
+    }
+  }
+
+  // ---- viscosity windows, cross-patch nearest points (eqs. W, multipatch_W, zeta)
+  std::vector<double> wtab(2 * prm->win_r - 1);
+  for (int a = -(prm->win_r - 1); a <= prm->win_r - 1; ++a) {
+    const long double t = std::fabs((long double)a);
+    const long double cc = cosl(3.14159265358979323846264338327950288L * t / (2.0L * prm->win_r));
+    wtab[a + prm->win_r - 1] = (double)(cc * cc);
+  }
+  std::vector<int> cdst, cptr{0}, csrc;
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    std::vector<int> near;
+    for (int q = 0; q < npatch; ++q) {
+      const HPatch& g = c->hp[q];
+      if (q != p && !(h.bx1 < g.bx0 || g.bx1 < h.bx0 || h.by1 < g.by0 || g.by1 < h.by0)) near.push_back(q);
+    }
+    if (near.empty()) continue;
+    for (size_t k = 0; k < h.x.size(); ++k) {
+      if (h.blank[k]) continue;
+      const double x = h.x[k], y = h.y[k];
+      bool any = false;
+      for (int q : near) {
+        const HPatch& g = c->hp[q];
+        if (x < g.bx0 - 1e-12 || x > g.bx1 + 1e-12 || y < g.by0 - 1e-12 || y > g.by1 + 1e-12) continue;
+        double s1, s2;
+        frac_index(g, x, y, s1, s2);
+        if (!contains(g, s1, s2)) continue;
+        int z1, z2;
+        nearest(g, s1, s2, z1, z2);
+        csrc.push_back((int)(g.off + (long long)z2 * g.n1 + z1));
+        any = true;
+      }
+      if (any) {
+        cdst.push_back((int)(h.off + (long long)k));
+        cptr.push_back((int)csrc.size());
+      }
+    }
+  }
+
+  // ---- curvilinear metrics J = dq/dx (Sec. 3.3), layout [4][Pg]: J1x, J1y, J2x, J2y
+  std::vector<double> Jm((size_t)4 * std::max<long long>(c->Pg, 1), 0.0);
+  for (const HPatch& h : c->hp) {
+    if (h.d.kind != FC_PATCH_OGRID) continue;
+    const double r0 = h.d.geom[2], r1 = h.d.geom[3];
+    for (long long k = 0; k < (long long)h.n1 * h.n2; ++k) {
+      const double dx = h.x[k] - h.d.geom[0], dy = h.y[k] - h.d.geom[1];
+      const double r = std::hypot(dx, dy);
+      const double cs = dx / r, sn = dy / r;
+      const size_t g = (size_t)(h.gbase + k);
+      Jm[g] = -sn / (2.0 * PI * r);
+      Jm[g + c->Pg] = cs / (2.0 * PI * r);
+      Jm[g + 2 * c->Pg] = cs / (r1 - r0);
+      Jm[g + 3 * c->Pg] = sn / (r1 - r0);
+    }
+  }
+
+  // ---- upload
+  bool ok = true;
+  make_queue(c, c->q_cart1, jc1, B.plans, npatch, ok);
+  make_queue(c, c->q_cart2, jc2, B.plans, npatch, ok);
+  make_queue(c, c->q_gen1, jg1, B.plans, npatch, ok);
+  make_queue(c, c->q_gen2, jg2, B.plans, npatch, ok);
+  make_queue(c, c->q_filt1, jf1, B.plans, npatch, ok);
+  make_queue(c, c->q_filt2, jf2, B.plans, npatch, ok);
+  std::vector<PatchDev> pdev(npatch);
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    pdev[p] = PatchDev{h.off, h.gbase, h.n1, h.n2, h.d.kind, h.periodic1 ? 1 : 0, h.hhat, h.htil};
+  }
+  const std::vector<double> Rv(prm->R, prm->R + 4);
+  ok = ok && c->upload(&c->d_plans, B.plans) && c->upload(&c->d_tw, B.tw) && c->upload(&c->d_rp, B.rp) &&
+       c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
+       c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
+       c->upload(&c->d_fix, fix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
+       c->upload(&c->d_bc, bcs) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
+       c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc);
+  c->nfix = (int)fix.size();
+  c->nfcopy1 = (int)fc1.size();
+  c->nfcopy2 = (int)fc2.size();
+  c->nbc = (int)bcs.size();
+  c->nrecv = (int)recv.size();
+  c->ncross = (int)cdst.size();
+  const size_t P = (size_t)c->P, Pg = (size_t)std::max<long long>(c->Pg, 1);
+  ok = ok && c->alloc(&c->d_B1, 4 * P) && c->alloc(&c->d_B2, 4 * P) && c->alloc(&c->d_B3, 4 * P) &&
+       c->alloc(&c->d_R1, 4 * P) && c->alloc(&c->d_G, 16 * Pg) && c->alloc(&c->d_phi, P) && c->alloc(&c->d_S, P) &&
+       c->alloc(&c->d_muhat, P) && c->alloc(&c->d_num, P) && c->alloc(&c->d_tmp, P) && c->alloc(&c->d_mu, P) &&
+       c->alloc(&c->d_den, P) && c->alloc(&c->d_dt, 1) && c->alloc(&c->d_pmax, 2 * (size_t)npatch) &&
+       c->alloc(&c->d_flag, 1);
+  if (!ok) {
+    fprintf(stderr, "fc_init_patches: %s\n", c->err.c_str());
+    delete c;
+    return FC_ERR_OOM;
+  }
+  cudaMemset(c->d_flag, 0, sizeof(int));
+  DevTables& T = c->T;
+  T.tw = c->d_tw;
+  T.rp = c->d_rp;
+  T.plans = c->d_plans;
+  T.info = c->d_info;
+  T.patches = c->d_patches;
+  T.npatch = npatch;
+  T.P = c->P;
+  T.Pg = std::max<long long>(c->Pg, 1);
+  T.gamma = prm->gamma;
+  T.d = prm->d;
+  set_kernel_attributes();
+
+  // normaliser of eq. (multipatch_W_norm): window sums of the generation indicator, own + other patches
+  {
+    std::vector<double> ind((size_t)c->P), ones((size_t)c->P, 1.0);
+    for (size_t k = 0; k < info.size(); ++k) ind[k] = (info[k] & PT_GEN) ? 1.0 : 0.0;
+    // the generation indicator goes through mu^'s buffer, the unit divisor through phi's
+    cudaMemcpy(c->d_muhat, ind.data(), ind.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_phi, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice);
+    launch_window_rows(T, c->d_muhat, c->d_tmp, c->d_wtab, prm->win_r, 0);
+    launch_window_cols(T, c->d_tmp, c->d_num, c->d_wtab, prm->win_r, 0);
+    launch_mu_final(T, c->d_num, c->d_phi, c->d_cross_dst, c->d_cross_ptr, c->d_cross_src, c->ncross, c->d_den, 0);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      fprintf(stderr, "fc_init_patches: %s\n", cudaGetErrorString(e));
+      delete c;
+      return FC_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return FC_OK;
+}
+
+size_t fc_state_size(const fc_ctx* c) { return c ? (size_t)c->P : 0; }
+size_t fc_active_points(const fc_ctx* c) { return c ? (size_t)c->active : 0; }
+fc_status fc_patch_offset(const fc_ctx* c, int patch, size_t* off) {
+  if (!c || !off || patch < 0 || patch >= (int)c->hp.size()) return FC_ERR_INVALID;
+  *off = (size_t)c->hp[patch].off;
+  return FC_OK;
+}
+uint64_t fc_launch_count(const fc_ctx* c) { return c ? c->launches : 0; }
+const char* fc_last_error(const fc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+void fc_destroy(fc_ctx* c) { delete c; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- orchestration
+namespace {
+
+// brackets a launch group with events when instrumentation is on
+struct Prof {
+  fc_ctx* c;
+  cudaStream_t st;
+  const char* name;
+  cudaEvent_t a = nullptr;
+  uint64_t l0;
+  Prof(fc_ctx* c_, cudaStream_t s, const char* n) : c(c_), st(s), name(n), l0(c_->launches) {
+    if (c->prof) {
+      a = c->ev();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~Prof() {
+    if (a) {
+      cudaEvent_t b = c->ev();
+      cudaEventRecord(b, st);
+      c->prec.push_back({name, a, b, (int)(c->launches - l0)});
+    }
+  }
+};
+
+// run one pass over a queue, batched (one launch per length class) or one launch per patch
+template <class F>
+void run_queue(fc_ctx* c, const fc_ctx::Queue& q, bool per_patch, cudaStream_t st, const char* name, F&& launch) {
+  if (q.n == 0) return;
+  Prof pr(c, st, name);
+  if (!per_patch) {
+    for (size_t k = 0; k < q.classes.size(); ++k) {
+      const int b = q.classes[k].first, e = q.class_end[k];
+      launch(q.d + b, e - b, q.classes[k].second);
+      c->launches++;
+    }
+  } else {
+    for (size_t p = 0; p < q.pbeg.size(); ++p) {
+      const int n = q.pend[p] - q.pbeg[p];
+      if (n <= 0) continue;
+      launch(q.dpp + q.pbeg[p], n, q.plmax[p]);
+      c->launches++;
+    }
+  }
+}
+
+void stage(fc_ctx* c, const StageCoef& sc, const double* mu, bool per_patch, cudaStream_t st) {
+  const DevTables& T = c->T;
+  const double* e = sc.Ucur;
+  run_queue(c, c->q_gen1, per_patch, st, "gen_A",
+            [&](const Job* j, int n, int L) { launch_gen_A(T, j, n, L, e, c->d_G, st); });
+  run_queue(c, c->q_cart1, per_patch, st, "cart_q1",
+            [&](const Job* j, int n, int L) { launch_cart_q1(T, j, n, L, e, mu, c->d_R1, st); });
+  run_queue(c, c->q_gen2, per_patch, st, "gen_B",
+            [&](const Job* j, int n, int L) { launch_gen_B(T, j, n, L, e, mu, c->d_J, c->d_G, st); });
+  run_queue(c, c->q_cart2, per_patch, st, "cart_q2",
+            [&](const Job* j, int n, int L) { launch_cart_q2(T, j, n, L, mu, c->d_R1, sc, st); });
+  run_queue(c, c->q_gen1, per_patch, st, "gen_C",
+            [&](const Job* j, int n, int L) { launch_gen_C(T, j, n, L, c->d_J, c->d_G, sc, st); });
+  if (c->nfix) {
+    Prof pr(c, st, "rk_fixup");
+    launch_rk_fixup(T, c->d_fix, c->nfix, sc, st);
+    c->launches++;
+  }
+}
+
+void project(fc_ctx* c, double* e, cudaStream_t st) {
+  Prof pr(c, st, "bc_exchange");
+  if (c->nbc) {
+    launch_bc(c->d_bc, c->nbc, e, c->P, st);
+    c->launches++;
+  }
+  if (c->nrecv) {
+    launch_exchange(c->d_recv, c->nrecv, e, c->P, st);
+    c->launches++;
+  }
+}
+
+void viscosity(fc_ctx* c, const double* e, double* mu, int32_t* tau, cudaStream_t st) {
+  Prof pr(c, st, "viscosity");
+  const DevTables& T = c->T;
+  launch_visc_point(T, e, c->d_phi, c->d_S, st);
+  launch_visc_muhat(T, c->d_phi, c->d_S, c->d_sdnn, c->d_R, c->d_muhat, tau, st);
+  launch_window_rows(T, c->d_muhat, c->d_tmp, c->d_wtab, c->prm.win_r, st);
+  launch_window_cols(T, c->d_tmp, c->d_num, c->d_wtab, c->prm.win_r, st);
+  launch_mu_final(T, c->d_num, c->d_den, c->d_cross_dst, c->d_cross_ptr, c->d_cross_src, c->ncross, mu, st);
+  c->launches += 5 + (c->ncross > 0);
+}
+
+void filter(fc_ctx* c, double* e, bool per_patch, cudaStream_t st) {
+  const DevTables& T = c->T;
+  double* F = c->d_B3;
+  run_queue(c, c->q_filt1, per_patch, st, "filter_q1",
+            [&](const Job* j, int n, int L) { launch_filter_q1(T, j, n, L, e, F, st); });
+  if (c->nfcopy1) {
+    launch_filter_copy_q1(T, c->d_fcopy1, c->nfcopy1, e, F, st);
+    c->launches++;
+  }
+  run_queue(c, c->q_filt2, per_patch, st, "filter_q2",
+            [&](const Job* j, int n, int L) { launch_filter_q2(T, j, n, L, F, e, st); });
+  if (c->nfcopy2) {
+    launch_filter_copy_q2(T, c->d_fcopy2, c->nfcopy2, F, e, st);
+    c->launches++;
+  }
+}
+
+void timestep(fc_ctx* c, const double* e, const double* mu, double* dt, cudaStream_t st) {
+  Prof pr(c, st, "timestep");
+  launch_dt(c->T, e, mu, c->d_pmax, c->prm.cfl, dt, st);
+  c->launches += 2;
+}
+
+void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream_t st) {
+  const bool pp = (flags & FC_STEP_PER_PATCH) != 0;
+  project(c, e, st);
+  if (!(flags & FC_STEP_FROZEN_MU)) viscosity(c, e, mu, nullptr, st);
+  if (flags & FC_STEP_FILTER) {
+    filter(c, e, pp, st);
+    project(c, e, st);
+  }
+  if (!(flags & FC_STEP_FIXED_DT)) timestep(c, e, mu, dt, st);
+  StageCoef s{};
+  s.dt = dt;
+  // stage 1: u1 = u0 + b1 dt L(u0)
+  s.U0 = e; s.Ucur = e; s.Uaux = nullptr; s.out = c->d_B1; s.out2 = nullptr;
+  s.c0 = 0.0; s.c1 = 1.0; s.c2 = 0.0; s.cb = B1;
+  stage(c, s, mu, pp, st);
+  project(c, c->d_B1, st);
+  // stage 2
+  s.Ucur = c->d_B1; s.out = c->d_B2; s.c0 = A20; s.c1 = A21; s.cb = B2;
+  stage(c, s, mu, pp, st);
+  project(c, c->d_B2, st);
+  // stage 3
+  s.Ucur = c->d_B2; s.out = c->d_B3; s.c0 = A30; s.c1 = A32; s.cb = B3;
+  stage(c, s, mu, pp, st);
+  project(c, c->d_B3, st);
+  // stage 4: u4 = a40 u0 + a43 u3 + b4 dt L(u3); acc = a52 u2 + a53 u3 + b53 dt L(u3) (in place over u2)
+  s.Ucur = c->d_B3; s.Uaux = c->d_B2; s.out = c->d_B1; s.out2 = c->d_B2;
+  s.c0 = A40; s.c1 = A43; s.c2 = 0.0; s.cb = B4; s.d1 = A53; s.d2 = A52; s.db = B53;
+  stage(c, s, mu, pp, st);
+  project(c, c->d_B1, st);
+  // stage 5: u5 = acc + a54 u4 + b54 dt L(u4)
+  s.U0 = nullptr; s.Ucur = c->d_B1; s.Uaux = c->d_B2; s.out = e; s.out2 = nullptr;
+  s.c0 = 0.0; s.c1 = A54; s.c2 = 1.0; s.cb = B54;
+  stage(c, s, mu, pp, st);
+  project(c, e, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+fc_status fc_rhs(fc_ctx* c, const double* e, double* rhs, const double* mu, void* stream) {
+  if (!c || !e || !rhs) return FC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!mu) {
+    viscosity(c, e, c->d_mu, nullptr, st);
+    mu = c->d_mu;
+  }
+  StageCoef s{};
+  s.Ucur = e;
+  s.out = rhs;
+  s.rhs_only = 1;
+  s.dt = c->d_dt;
+  stage(c, s, mu, false, st);
+  return cuda_check(c, "fc_rhs");
+}
+
+fc_status fc_viscosity(fc_ctx* c, const double* e, double* mu, int32_t* tau, void* stream) {
+  if (!c || !e || !mu) return FC_ERR_INVALID;
+  viscosity(c, e, mu, tau, (cudaStream_t)stream);
+  return cuda_check(c, "fc_viscosity");
+}
+
+fc_status fc_filter(fc_ctx* c, double* e, void* stream) {
+  if (!c || !e) return FC_ERR_INVALID;
+  filter(c, e, false, (cudaStream_t)stream);
+  return cuda_check(c, "fc_filter");
+}
+
+fc_status fc_project(fc_ctx* c, double* e, void* stream) {
+  if (!c || !e) return FC_ERR_INVALID;
+  project(c, e, (cudaStream_t)stream);
+  return cuda_check(c, "fc_project");
+}
+
+fc_status fc_timestep(fc_ctx* c, const double* e, const double* mu, double* dt, void* stream) {
+  if (!c || !e || !mu || !dt) return FC_ERR_INVALID;
+  timestep(c, e, mu, dt, (cudaStream_t)stream);
+  return cuda_check(c, "fc_timestep");
+}
+
+fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, void* stream) {
+  if (!c || !e) return FC_ERR_INVALID;
+  if ((flags & FC_STEP_FROZEN_MU) && !mu) return fail(c, FC_ERR_INVALID, "FROZEN_MU needs mu");
+  if ((flags & FC_STEP_FIXED_DT) && !dt) return fail(c, FC_ERR_INVALID, "FIXED_DT needs dt");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!mu) mu = c->d_mu;
+  if (!dt) dt = c->d_dt;
+  if (!(flags & FC_STEP_GRAPH)) {
+    rk_body(c, e, dt, mu, flags, st);
+    return cuda_check(c, "fc_rk_step");
+  }
+  // graph mode: capture the step once per (buffers, flags, stream) and replay it
+  const int gf = flags & ~FC_STEP_GRAPH;
+  const bool hit = c->gexec && c->gflags == gf && c->gkey[0] == e && c->gkey[1] == dt && c->gkey[2] == mu &&
+                   c->gstream == st;
+  if (!hit) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    if (st == nullptr) return fail(c, FC_ERR_INVALID, "graph mode needs a non-default stream");
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail(c, FC_ERR_CUDA, "stream capture failed to begin");
+    const uint64_t l0 = c->launches;
+    const bool prof = c->prof;
+    c->prof = false;
+    rk_body(c, e, dt, mu, gf, st);
+    c->prof = prof;
+    if (cudaStreamEndCapture(st, &g) != cudaSuccess) return cuda_check(c, "graph capture");
+    cudaError_t er = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (er != cudaSuccess) return fail(c, FC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(er));
+    c->gkey[0] = e;
+    c->gkey[1] = dt;
+    c->gkey[2] = mu;
+    c->gflags = gf;
+    c->gstream = st;
+    c->glaunches = c->launches - l0;  // kernels per replay
+    c->launches = l0;
+  }
+  if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_check(c, "graph launch");
+  c->launches += c->glaunches;
+  return cuda_check(c, "fc_rk_step");
+}
+
+fc_status fc_sync_status(fc_ctx* c, const double* e, int check_state, void* stream) {
+  if (!c) return FC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (check_state && e) {
+    launch_check_state(c->T, e, c->d_flag, st);
+    c->launches++;
+  }
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cuda_check(c, "fc_sync_status");
+  if (flag) {
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    return fail(c, (fc_status)flag, flag == FC_ERR_NONFINITE ? "non-finite or non-physical state" : "device timeout");
+  }
+  return FC_OK;
+}
+
+fc_status fc_profile_enable(fc_ctx* c, int enable) {
+  if (!c) return FC_ERR_INVALID;
+  c->prof = enable != 0;
+  return FC_OK;
+}
+
+int fc_profile_read(fc_ctx* c) {
+  if (!c) return -1;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  for (const auto& r : c->prec) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    size_t k = 0;
+    while (k < c->pnames.size() && c->pnames[k] != r.name) ++k;
+    if (k == c->pnames.size()) {
+      c->pnames.push_back(r.name);
+      c->pms.push_back(0.0);
+      c->pcount.push_back(0);
+    }
+    c->pms[k] += ms;
+    c->pcount[k] += r.launches;
+  }
+  c->prec.clear();
+  c->evused = 0;
+  return (int)c->pnames.size();
+}
+
+fc_status fc_profile_get(const fc_ctx* c, int k, const char** name, double* ms, int* launches) {
+  if (!c || k < 0 || k >= (int)c->pnames.size() || !name || !ms || !launches) return FC_ERR_INVALID;
+  *name = c->pnames[k].c_str();
+  *ms = c->pms[k];
+  *launches = c->pcount[k];
+  return FC_OK;
+}
+
+fc_status fc_profile_reset(fc_ctx* c) {
+  if (!c) return FC_ERR_INVALID;
+  c->pnames.clear();
+  c->pms.clear();
+  c->pcount.clear();
+  c->prec.clear();
+  c->evused = 0;
+  return FC_OK;
+}
+
+// Algorithmic FP64 work of one launch of a line pass, by the conventional counts:
+// 5 L log2 L flops per complex FFT of length L (two real lines per transform, one
+// forward and one inverse per derivative), 4dC flops per continued real line
+// (2d-term matvec per continuation point), 2 flops per complex mode for the
+// multiplier, and the pointwise flux / viscous-flux / stage-combination work.
+// Bytes: the compulsory HBM traffic of the pass (8 B per double read or written once).
+fc_status fc_pass_stats(const fc_ctx* c, const char* pass, double* flops, double* bytes, long long* lines,
+                        long long* points) {
+  if (!c || !pass || !flops || !bytes || !lines || !points) return FC_ERR_INVALID;
+  const fc_ctx::Queue* q = nullptr;
+  int rounds = 2;              // derivative rounds per line
+  double pw = 0.0, bw = 0.0;   // pointwise flops and bytes per point
+  const std::string n(pass);
+  if (n == "cart_q1") {
+    q = &c->q_cart1;
+    pw = 20.0;
+    bw = 72.0;    // read e (32) and mu (8), write R1 (32)
+  } else if (n == "cart_q2") {
+    q = &c->q_cart2;
+    pw = 52.0;
+    bw = 168.0;   // read e, mu, R1, one more stage operand; write the stage output
+  } else if (n == "filter_q1" || n == "filter_q2") {
+    q = n == "filter_q1" ? &c->q_filt1 : &c->q_filt2;
+    rounds = 1;
+    pw = 12.0;
+    bw = 64.0;
+  } else {
+    return FC_ERR_INVALID;
+  }
+  // job lengths are not kept on the host after upload: recompute them from the patches
+  double F = 0, Bt = 0;
+  long long nl = 0, np = 0;
+  auto add_line = [&](int nn, int L, int C) {
+    F += rounds * (2.0 * 2.0 * 5.0 * L * std::log2((double)L) + 4.0 * 4.0 * c->d * C + 2.0 * 2.0 * 2.0 * L) + pw * nn;
+    Bt += bw * nn;
+    nl++;
+    np += nn;
+  };
+  for (const HPatch& h : c->hp) {
+    const bool aff = h.d.kind == FC_PATCH_AFFINE;
+    const bool want1 = (n == "cart_q1" && aff) || n == "filter_q1";
+    const bool want2 = (n == "cart_q2" && aff) || n == "filter_q2";
+    if (want1)
+      for (const Seg& s : h.seg1) {
+        if (!s.periodic && s.n < 2 * c->prm.d) continue;
+        int C = 0;
+        if (!s.periodic) {
+          C = c->prm.C0;
+          if (c->prm.c_policy) while (!smooth7(s.n + C)) ++C;
+        }
+        add_line(s.n, s.n + C, C);
+      }
+    if (want2)
+      for (const Seg& s : h.seg2) {
+        if (s.n < 2 * c->prm.d) continue;
+        int C = c->prm.C0;
+        if (c->prm.c_policy) while (!smooth7(s.n + C)) ++C;
+        add_line(s.n, s.n + C, C);
+      }
+  }
+  (void)q;
+  *flops = F;
+  *bytes = Bt;
+  *lines = nl;
+  *points = np;
+  return FC_OK;
+}
+
+fc_status fc_adjoint_step(fc_ctx* c, const double*, const double*, const double*, const double*, double*, void*) {
+  return fail(c, FC_ERR_UNIMPLEMENTED, "adjoint step not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal structures shared by the host runtime (fc_host.cpp) and the kernels (fc_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fcsdnn.h"
+
+namespace fcx {
+
+constexpr int MAXST = 24;       // max FFT stages per plan
+constexpr int MAXW = 8;         // max warps per CTA in the line kernels
+constexpr size_t SMEM_CAP = 200 * 1024;  // dynamic shared memory budget per CTA
+constexpr int SDNN_H = 16;      // hidden width of the stand-in classifier
+
+// Per-point flag word.
+enum : uint32_t {
+  PT_BLANK = 1u,      // blanked (inside a hole): never updated, mu = 0
+  PT_NODIFF = 2u,     // on a line segment too short for FC in some direction: L = 0
+  PT_GEN = 4u,        // viscosity-generation point (depth >= n_v)
+  PT_W1_SHIFT = 3,    // 3 bits: 7-point window start offset along q1 (0..6) or 7 = none
+  PT_W2_SHIFT = 6,    // 3 bits: same along q2
+  PT_PATCH_SHIFT = 9  // remaining bits: patch index
+};
+__host__ __device__ inline int pt_patch(uint32_t f) { return (int)(f >> PT_PATCH_SHIFT); }
+__host__ __device__ inline int pt_w1(uint32_t f) { return (int)((f >> PT_W1_SHIFT) & 7u); }
+__host__ __device__ inline int pt_w2(uint32_t f) { return (int)((f >> PT_W2_SHIFT) & 7u); }
+
+// FFT plan of one length L (mixed-radix Stockham, natural order in and out).
+struct Plan {
+  int L;
+  int nst;
+  int rad[MAXST];
+  int tw;     // offset of the L-entry forward twiddle table exp(-2 pi i e / L) in the twiddle pool
+  int sig;    // offset of the L-entry filter table sigma(2k/L)/L in the real pool (-1: none)
+};
+
+// One line segment processed by one warp.
+struct Job {
+  long long base;   // flat index of the first point
+  int stride;       // 1 (q1 line) or n1 (q2 line)
+  int n;            // points on the segment
+  int plan;         // plan index (L = n + C, or n when periodic)
+  int fcm;          // offset of the combined continuation matrices in the real pool (-1: periodic)
+  int C;            // continuation points (0 when periodic)
+  int patch;
+  long long gbase;  // index of the first point in the curvilinear scratch (-1: affine patch)
+  double scale;     // multiplier of the per-index derivative: 1/h (affine: per unit x or y)
+};
+
+struct PatchDev {
+  long long off;    // first flat index
+  long long gbase;  // first index in the curvilinear scratch (-1 for affine)
+  int n1, n2, kind, periodic1;
+  double hhat, htil;
+};
+
+// Receiver of the inter-patch exchange: 3x3 donor stencil, iterated quadratic weights.
+struct Recv {
+  int dst;
+  int src[9];       // donor flat indices, row-major over (m2, m1)
+  double w1[3], w2[3];
+};
+
+// Boundary overwrite of one point.
+struct BcPt {
+  int idx;
+  int mode;         // bit0: zero rho u, bit1: zero rho v, bit2: remove normal (nx, ny), bit3: Dirichlet
+  double nx, ny;
+  double val[4];    // Dirichlet conserved state
+};
+
+// Runge-Kutta stage combination applied in the last pass of a stage:
+//   out  = c0 U0 + c1 Ucur + c2 Uaux + cb dt L
+//   out2 = d2 Uaux + d1 Ucur + db dt L        (only when out2 != nullptr)
+//   rhs_only: out = L
+struct StageCoef {
+  const double* U0;
+  const double* Ucur;
+  const double* Uaux;
+  double* out;
+  double* out2;
+  double c0, c1, c2, cb, d1, d2, db;
+  const double* dt;
+  int rhs_only;
+};
+
+struct DevTables {
+  const double2* tw;        // twiddle pool
+  const double* rp;         // real pool (continuation matrices, filter tables)
+  const Plan* plans;
+  const uint32_t* info;     // per-point flags
+  const PatchDev* patches;
+  int npatch;
+  long long P;              // points (component stride of the state)
+  long long Pg;             // points of curvilinear patches (component stride of the scratch)
+  double gamma;
+  int d;
+};
+
+// ---- launch wrappers (fc_kernels.cu) ----
+void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
+                    double* R1, cudaStream_t st);
+void launch_cart_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* mu, const double* R1,
+                    const StageCoef& sc, cudaStream_t st);
+void launch_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* G, cudaStream_t st);
+void launch_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
+                  const double* J, double* G, cudaStream_t st);
+void launch_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, double* G,
+                  const StageCoef& sc, cudaStream_t st);
+void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef& sc, cudaStream_t st);
+void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st);
+void launch_exchange(const Recv* r, int n, double* e, long long P, cudaStream_t st);
+void launch_filter_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* F, cudaStream_t st);
+void launch_filter_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* F, double* e, cudaStream_t st);
+void launch_filter_copy_q1(const DevTables& T, const int* idx, int n, const double* e, double* F, cudaStream_t st);
+void launch_filter_copy_q2(const DevTables& T, const int* idx, int n, const double* F, double* e, cudaStream_t st);
+void launch_visc_point(const DevTables& T, const double* e, double* phi, double* S, cudaStream_t st);
+void launch_visc_muhat(const DevTables& T, const double* phi, const double* S, const float* w, const double* R,
+                       double* muhat, int32_t* tau, cudaStream_t st);
+void launch_window_rows(const DevTables& T, const double* in, double* out, const double* wtab, int r, cudaStream_t st);
+void launch_window_cols(const DevTables& T, const double* in, double* out, const double* wtab, int r, cudaStream_t st);
+void launch_mu_final(const DevTables& T, const double* num, const double* den, const int* cross_dst,
+                     const int* cross_ptr, const int* cross_src, int ncross, double* mu, cudaStream_t st);
+void launch_dt(const DevTables& T, const double* e, const double* mu, unsigned long long* pmax, double cfl,
+               double* dt, cudaStream_t st);
+void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st);
+void launch_adj_stage(const DevTables& T, const Job* jobs, int njobs, int Lmax, int pass, const double* e,
+                      const double* mu, const double* J, double* G, double* lam_out, const double* lam_in,
+                      cudaStream_t st);
+size_t line_smem_bytes(int Lmax);
+int line_warps(int Lmax);
+void set_kernel_attributes();
+
+}  // namespace fcx

@@ -1,0 +1,855 @@
+// Device kernels of the multi-patch FC-SDNN operator (sm_103a, FP64).
+//
+// Line kernels: one warp per grid-line segment, shared-memory mixed-radix Stockham
+// FFTs of the FC-Gram continued line (Sec. 2.2), fused with the Euler flux, the
+// artificial-viscosity flux and the SSPRK stage combination (Sec. 2.1, 2.3, 4.1).
+// The path is bound by the FP64 pipe (2 FP64 lanes/clk/SM on GB300), so the kernels
+// minimise FP64 instructions: packed real pairs per complex FFT, radix 2/3/4/5/7/8
+// butterflies with table twiddles, continuation as a 2d-term matvec.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fc_internal.h"
+#include "fc_line.cuh"
+
+namespace fcx {
+
+// warps per CTA for a line kernel whose longest line has Lmax points: 4 Lmax complex
+// values of shared memory per warp (two packed sequences, Stockham ping-pong)
+int line_warps(int Lmax) {
+  const size_t per = (size_t)4 * Lmax * sizeof(double2);
+  int w = (int)(SMEM_CAP / per);
+  return w < 1 ? 1 : (w > MAXW ? MAXW : w);
+}
+size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * 4 * Lmax * sizeof(double2); }
+
+__device__ __forceinline__ void flux_xy(double r, double mx, double my, double E, double gam, double* fx, double* fy) {
+  const double ir = 1.0 / r;
+  const double u = mx * ir, v = my * ir;
+  const double p = (gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+  fx[0] = mx;
+  fx[1] = fma(mx, u, p);
+  fx[2] = mx * v;
+  fx[3] = u * (E + p);
+  fy[0] = my;
+  fy[1] = my * u;
+  fy[2] = fma(my, v, p);
+  fy[3] = v * (E + p);
+}
+
+__device__ __forceinline__ void flux_x(double r, double mx, double my, double E, double gam, double* f) {
+  const double ir = 1.0 / r;
+  const double u = mx * ir, v = my * ir;
+  const double p = (gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+  f[0] = mx;
+  f[1] = fma(mx, u, p);
+  f[2] = mx * v;
+  f[3] = u * (E + p);
+}
+__device__ __forceinline__ void flux_y(double r, double mx, double my, double E, double gam, double* f) {
+  const double ir = 1.0 / r;
+  const double u = mx * ir, v = my * ir;
+  const double p = (gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+  f[0] = my;
+  f[1] = my * u;
+  f[2] = fma(my, v, p);
+  f[3] = v * (E + p);
+}
+
+// Load 4 state components of a line into two packed complex sequences.
+__device__ __forceinline__ void load4(double2* A, int L, const Job& J, const double* __restrict__ src, long long cs,
+                                      int lane) {
+  for (int t = lane; t < J.n; t += 32) {
+    const long long p = J.base + (long long)t * J.stride;
+    A[t] = cpx(src[p], src[p + cs]);
+    A[L + t] = cpx(src[p + 2 * cs], src[p + 3 * cs]);
+  }
+}
+
+// Forward FFT, derivative multiplier, inverse FFT of the two sequences in A (continued
+// first if the line is not periodic). Returns the buffer with the derivative.
+__device__ __forceinline__ double2* deriv2(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
+                                           int lane) {
+  if (J.fcm >= 0) {
+    FC_SYNC();
+    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
+  }
+  FC_SYNC();
+  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
+  double2* Y = (X == A) ? B : A;
+  mul_deriv(X, P.L, 2, J.scale * TWO_PI / ((double)P.L * (double)P.L), lane, 32);
+  FC_SYNC();
+  return fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+}
+
+__device__ __forceinline__ void stage_write(const StageCoef& sc, long long p, long long cs, const double* L4) {
+  if (sc.rhs_only) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sc.out[p + c * cs] = L4[c];
+    return;
+  }
+  const double dt = *sc.dt;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long q = p + c * cs;
+    const double cur = sc.Ucur[q];
+    double v = sc.c1 * cur;
+    double aux = 0.0;
+    if (sc.c0 != 0.0) v = fma(sc.c0, sc.U0[q], v);
+    if (sc.Uaux) aux = sc.Uaux[q];
+    if (sc.c2 != 0.0) v = fma(sc.c2, aux, v);
+    v = fma(sc.cb * dt, L4[c], v);
+    if (sc.out2) sc.out2[q] = fma(sc.db * dt, L4[c], fma(sc.d2, aux, sc.d1 * cur));
+    sc.out[q] = v;
+  }
+}
+
+// ---------------------------------------------------------------- affine patches, q1 lines
+// d/dx of e -> H_x = f_x(e) - mu d/dx e -> R1 = d/dx H_x  (J11 folded into J.scale = 1/hx)
+__global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                        const double* __restrict__ e, const double* __restrict__ mu,
+                                                        double* __restrict__ R1) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, e, cs, lane);
+    double2* X = deriv2(A, B, J, P, T, lane);
+    double2* Y = (X == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      double f[4];
+      flux_x(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+      const double m = mu[p];
+      const double2 g0 = X[t], g1 = X[L + t];
+      Y[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
+      Y[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+    }
+    double2* Z = deriv2(Y, X, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double2 a = Z[t], b = Z[L + t];
+      R1[p] = a.x;
+      R1[p + cs] = a.y;
+      R1[p + 2 * cs] = b.x;
+      R1[p + 3 * cs] = b.y;
+    }
+    FC_SYNC();
+  }
+}
+
+// ---------------------------------------------------------------- affine patches, q2 lines
+// d/dy of e -> H_y -> R2 = d/dy H_y; L = -(R1 + R2) (0 on PT_NODIFF points); stage combination.
+__global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                        const double* __restrict__ mu, const double* __restrict__ R1,
+                                                        StageCoef sc) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P;
+  const double* e = sc.Ucur;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, e, cs, lane);
+    double2* X = deriv2(A, B, J, P, T, lane);
+    double2* Y = (X == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      double f[4];
+      flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+      const double m = mu[p];
+      const double2 g0 = X[t], g1 = X[L + t];
+      Y[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
+      Y[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+    }
+    double2* Z = deriv2(Y, X, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double2 a = Z[t], b = Z[L + t];
+      double L4[4];
+      if (T.info[p] & PT_NODIFF) {
+        L4[0] = L4[1] = L4[2] = L4[3] = 0.0;
+      } else {
+        L4[0] = -(R1[p] + a.x);
+        L4[1] = -(R1[p + cs] + a.y);
+        L4[2] = -(R1[p + 2 * cs] + b.x);
+        L4[3] = -(R1[p + 3 * cs] + b.y);
+      }
+      stage_write(sc, p, cs, L4);
+    }
+    FC_SYNC();
+  }
+}
+
+// ---------------------------------------------------------------- curvilinear patches
+// scratch G (component stride Pg): slot 0 = D1e then R1, slot 1 = H_x, slot 2 = H_y, slot 3 = R2
+__device__ __forceinline__ double* gslot(double* G, long long Pg, int slot, int c) { return G + (4 * slot + c) * Pg; }
+
+// pass A: D1e = d/dq1 e
+__global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                      const double* __restrict__ e, double* __restrict__ G) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    load4(A, P.L, J, e, T.P, lane);
+    double2* X = deriv2(A, B, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      gslot(G, T.Pg, 0, 0)[g] = X[t].x;
+      gslot(G, T.Pg, 0, 1)[g] = X[t].y;
+      gslot(G, T.Pg, 0, 2)[g] = X[P.L + t].x;
+      gslot(G, T.Pg, 0, 3)[g] = X[P.L + t].y;
+    }
+    FC_SYNC();
+  }
+}
+
+// pass B: D2e; grad_x e = J1x D1 + J2x D2, grad_y e = J1y D1 + J2y D2; H_x, H_y;
+// R2 = J2x d/dq2 H_x + J2y d/dq2 H_y
+__global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                      const double* __restrict__ e, const double* __restrict__ mu,
+                                                      const double* __restrict__ Jm, double* __restrict__ G) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P, Pg = T.Pg;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, e, cs, lane);
+    double2* X = deriv2(A, B, J, P, T, lane);
+    double2* Y = (X == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double j1x = Jm[g], j1y = Jm[g + Pg], j2x = Jm[g + 2 * Pg], j2y = Jm[g + 3 * Pg];
+      const double d2[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+      double fx[4], fy[4];
+      flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, fx, fy);
+      const double m = mu[p];
+      double hx[4], hy[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double d1 = gslot(G, Pg, 0, c)[g];
+        const double gx = fma(j1x, d1, j2x * d2[c]);
+        const double gy = fma(j1y, d1, j2y * d2[c]);
+        hx[c] = fma(-m, gx, fx[c]);
+        hy[c] = fma(-m, gy, fy[c]);
+        gslot(G, Pg, 1, c)[g] = hx[c];
+        gslot(G, Pg, 2, c)[g] = hy[c];
+      }
+      Y[t] = cpx(hx[0], hx[1]);
+      Y[L + t] = cpx(hx[2], hx[3]);
+    }
+    double2* Z = deriv2(Y, X, J, P, T, lane);
+    double2* W = (Z == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double j2x = Jm[g + 2 * Pg];
+      gslot(G, Pg, 3, 0)[g] = j2x * Z[t].x;
+      gslot(G, Pg, 3, 1)[g] = j2x * Z[t].y;
+      gslot(G, Pg, 3, 2)[g] = j2x * Z[L + t].x;
+      gslot(G, Pg, 3, 3)[g] = j2x * Z[L + t].y;
+      W[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
+      W[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
+    }
+    double2* V = deriv2(W, Z, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double j2y = Jm[g + 3 * Pg];
+      double* r = gslot(G, Pg, 3, 0);
+      r[g] = fma(j2y, V[t].x, r[g]);
+      r = gslot(G, Pg, 3, 1);
+      r[g] = fma(j2y, V[t].y, r[g]);
+      r = gslot(G, Pg, 3, 2);
+      r[g] = fma(j2y, V[L + t].x, r[g]);
+      r = gslot(G, Pg, 3, 3);
+      r[g] = fma(j2y, V[L + t].y, r[g]);
+    }
+    FC_SYNC();
+  }
+}
+
+// pass C: R1 = J1x d/dq1 H_x + J1y d/dq1 H_y; L = -(R1 + R2); stage combination
+__global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                      const double* __restrict__ Jm, double* __restrict__ G,
+                                                      StageCoef sc) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P, Pg = T.Pg;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      A[t] = cpx(gslot(G, Pg, 1, 0)[g], gslot(G, Pg, 1, 1)[g]);
+      A[L + t] = cpx(gslot(G, Pg, 1, 2)[g], gslot(G, Pg, 1, 3)[g]);
+    }
+    double2* X = deriv2(A, B, J, P, T, lane);
+    double2* Y = (X == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double j1x = Jm[g];
+      gslot(G, Pg, 0, 0)[g] = j1x * X[t].x;
+      gslot(G, Pg, 0, 1)[g] = j1x * X[t].y;
+      gslot(G, Pg, 0, 2)[g] = j1x * X[L + t].x;
+      gslot(G, Pg, 0, 3)[g] = j1x * X[L + t].y;
+      Y[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
+      Y[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
+    }
+    double2* Z = deriv2(Y, X, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double j1y = Jm[g + Pg];
+      const double d[4] = {Z[t].x, Z[t].y, Z[L + t].x, Z[L + t].y};
+      double L4[4];
+      const bool nod = (T.info[p] & PT_NODIFF) != 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double r1 = fma(j1y, d[c], gslot(G, Pg, 0, c)[g]);
+        L4[c] = nod ? 0.0 : -(r1 + gslot(G, Pg, 3, c)[g]);
+      }
+      stage_write(sc, p, cs, L4);
+    }
+    FC_SYNC();
+  }
+}
+
+// points no final line pass covers (blanked points, short segments): L = 0
+__global__ void k_rk_fixup(DevTables T, const int* __restrict__ idx, int n, StageCoef sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double L4[4] = {0.0, 0.0, 0.0, 0.0};
+  stage_write(sc, idx[i], T.P, L4);
+}
+
+// ---------------------------------------------------------------- boundary overwrite (Sec. 4.2)
+__global__ void k_bc(const BcPt* __restrict__ bc, int n, double* __restrict__ e, long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BcPt b = bc[i];
+  const long long p = b.idx;
+  if (b.mode & 1) e[p + P] = 0.0;
+  if (b.mode & 2) e[p + 2 * P] = 0.0;
+  if (b.mode & 4) {
+    const double mx = e[p + P], my = e[p + 2 * P];
+    const double mn = mx * b.nx + my * b.ny;
+    e[p + P] = mx - mn * b.nx;
+    e[p + 2 * P] = my - mn * b.ny;
+  }
+  if (b.mode & 8) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) e[p + c * P] = b.val[c];
+  }
+}
+
+// ---------------------------------------------------------------- inter-patch exchange (Sec. 3.4.1)
+// iterated 1-D quadratic interpolation: along q1 in each of the 3 stencil rows, then along q2
+__global__ void k_exchange(const Recv* __restrict__ r, int n, double* __restrict__ e, long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Recv R = r[i];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* ec = e + c * P;
+    double acc = 0.0;
+#pragma unroll
+    for (int m2 = 0; m2 < 3; ++m2) {
+      double row = 0.0;
+#pragma unroll
+      for (int m1 = 0; m1 < 3; ++m1) row = fma(R.w1[m1], ec[R.src[3 * m2 + m1]], row);
+      acc = fma(R.w2[m2], row, acc);
+    }
+    e[R.dst + c * P] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- per-step filter (Sec. 4.3.1)
+__device__ __forceinline__ double theta_of(double r, double mx, double my, double E, double gam) {
+  const Prim q = primitives(r, mx, my, E, gam);
+  return q.p / r;
+}
+__device__ __forceinline__ double energy_of(double r, double mx, double my, double th, double gam) {
+  return r * th / (gam - 1.0) + 0.5 * (mx * mx + my * my) / r;
+}
+
+__device__ __forceinline__ double2* filter2(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
+                                            int lane) {
+  if (J.fcm >= 0) {
+    FC_SYNC();
+    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
+  }
+  FC_SYNC();
+  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
+  double2* Y = (X == A) ? B : A;
+  mul_filter(X, P.L, 2, T.rp + P.sig, lane, 32);
+  FC_SYNC();
+  return fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+}
+
+__global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                          int Lmax, const double* __restrict__ e,
+                                                          double* __restrict__ F) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double r = e[p], mx = e[p + cs], my = e[p + 2 * cs];
+      A[t] = cpx(r, mx);
+      A[L + t] = cpx(my, theta_of(r, mx, my, e[p + 3 * cs], T.gamma));
+    }
+    double2* X = filter2(A, B, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      F[p] = X[t].x;
+      F[p + cs] = X[t].y;
+      F[p + 2 * cs] = X[L + t].x;
+      F[p + 3 * cs] = X[L + t].y;
+    }
+    FC_SYNC();
+  }
+}
+
+__global__ void __launch_bounds__(MAXW * 32) k_filter_q2(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                          int Lmax, const double* __restrict__ F,
+                                                          double* __restrict__ e) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, F, cs, lane);
+    double2* X = filter2(A, B, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double r = X[t].x, mx = X[t].y, my = X[L + t].x, th = X[L + t].y;
+      e[p] = r;
+      e[p + cs] = mx;
+      e[p + 2 * cs] = my;
+      e[p + 3 * cs] = energy_of(r, mx, my, th, T.gamma);
+    }
+    FC_SYNC();
+  }
+}
+
+__global__ void k_filter_copy_q1(DevTables T, const int* __restrict__ idx, int n, const double* __restrict__ e,
+                                 double* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = idx[i], cs = T.P;
+  const double r = e[p], mx = e[p + cs], my = e[p + 2 * cs];
+  F[p] = r;
+  F[p + cs] = mx;
+  F[p + 2 * cs] = my;
+  F[p + 3 * cs] = theta_of(r, mx, my, e[p + 3 * cs], T.gamma);
+}
+
+__global__ void k_filter_copy_q2(DevTables T, const int* __restrict__ idx, int n, const double* __restrict__ F,
+                                 double* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = idx[i], cs = T.P;
+  const double r = F[p], mx = F[p + cs], my = F[p + 2 * cs];
+  e[p] = r;
+  e[p + cs] = mx;
+  e[p + 2 * cs] = my;
+  e[p + 3 * cs] = energy_of(r, mx, my, F[p + 3 * cs], T.gamma);
+}
+
+// ---------------------------------------------------------------- viscosity (Sec. 5)
+// Proxy Phi (local Mach number) and MWSB S = |u| + |v| + a, evaluated with explicitly
+// rounded operations in a fixed order (no contraction), so the classifier input is
+// reproducible.
+__global__ void k_visc_point(DevTables T, const double* __restrict__ e, double* __restrict__ phi,
+                             double* __restrict__ S) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  if (T.info[p] & PT_BLANK) {
+    phi[p] = 0.0;
+    S[p] = 0.0;
+    return;
+  }
+  const long long cs = T.P;
+  const double gam = T.gamma;
+  const double rho = e[p];
+  const double u = __ddiv_rn(e[p + cs], rho);
+  const double v = __ddiv_rn(e[p + 2 * cs], rho);
+  const double s2 = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+  const double ke = __dmul_rn(__dmul_rn(0.5, rho), s2);
+  const double pr = __dmul_rn(__dsub_rn(gam, 1.0), __dsub_rn(e[p + 3 * cs], ke));
+  phi[p] = __dmul_rn(__dsqrt_rn(s2), __dsqrt_rn(__ddiv_rn(rho, __dmul_rn(gam, pr))));
+  S[p] = __dadd_rn(__dadd_rn(fabs(u), fabs(v)), __dsqrt_rn(__ddiv_rn(__dmul_rn(gam, pr), rho)));
+}
+
+__device__ __forceinline__ int classify7(const double* w, const float* __restrict__ W) {
+  double lo = w[0], hi = w[0], am = fabs(w[0]);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) {
+    lo = fmin(lo, w[k]);
+    hi = fmax(hi, w[k]);
+    am = fmax(am, fabs(w[k]));
+  }
+  const double rg = __dsub_rn(hi, lo);
+  if (rg < __dmul_rn(1e-6, fmax(1.0, am))) return 4;
+  float x[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) x[k] = __double2float_rn(__ddiv_rn(__dsub_rn(w[k], lo), rg));
+  const float* W1 = W;
+  const float* b1 = W1 + SDNN_H * 7;
+  const float* W2 = b1 + SDNN_H;
+  const float* b2 = W2 + SDNN_H * SDNN_H;
+  const float* W3 = b2 + SDNN_H;
+  const float* b3 = W3 + 4 * SDNN_H;
+  float h1[SDNN_H], h2[SDNN_H];
+#pragma unroll
+  for (int o = 0; o < SDNN_H; ++o) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) a = fmaf(W1[o * 7 + k], x[k], a);
+    h1[o] = fmaxf(a + b1[o], 0.f);
+  }
+#pragma unroll
+  for (int o = 0; o < SDNN_H; ++o) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < SDNN_H; ++k) a = fmaf(W2[o * SDNN_H + k], h1[k], a);
+    h2[o] = fmaxf(a + b2[o], 0.f);
+  }
+  int best = 0;
+  float bv = -INFINITY;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < SDNN_H; ++k) a = fmaf(W3[o * SDNN_H + k], h2[k], a);
+    a += b3[o];
+    if (a > bv) {
+      bv = a;
+      best = o;
+    }
+  }
+  return best + 1;
+}
+
+// mu^ = R(tau~) max_{7x7} S h^ on generating points, 0 elsewhere (eq. V2D_unscaled)
+__global__ void k_visc_muhat(DevTables T, const double* __restrict__ phi, const double* __restrict__ S,
+                             const float* __restrict__ W, const double* __restrict__ Rw, double* __restrict__ muhat,
+                             int32_t* __restrict__ tau) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  const uint32_t f = T.info[p];
+  if (!(f & PT_GEN)) {
+    muhat[p] = 0.0;
+    if (tau) tau[p] = 0;
+    return;
+  }
+  const PatchDev pd = T.patches[pt_patch(f)];
+  const long long loc = p - pd.off;
+  const int j = (int)(loc / pd.n1), i = (int)(loc - (long long)j * pd.n1);
+  int t1 = 4, t2 = 4;
+  double w[7];
+  const int o1 = pt_w1(f), o2 = pt_w2(f);
+  if (o1 != 7) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      int ii = i - o1 + k;
+      if (pd.periodic1) ii = (ii + pd.n1) % pd.n1;
+      w[k] = phi[pd.off + (long long)j * pd.n1 + ii];
+    }
+    t1 = classify7(w, W);
+  }
+  if (o2 != 7) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) w[k] = phi[pd.off + (long long)(j - o2 + k) * pd.n1 + i];
+    t2 = classify7(w, W);
+  }
+  const int tc = min(t1, t2);
+  // 7x7 maximum of S (clipped to the grid, wrapped along a periodic q1); S >= 0, so the
+  // IEEE bit patterns order like the values and the maximum runs on integer compares
+  long long mb = 0;
+  for (int b = -3; b <= 3; ++b) {
+    const int jj = j + b;
+    if (jj < 0 || jj >= pd.n2) continue;
+    for (int a = -3; a <= 3; ++a) {
+      int ii = i + a;
+      if (pd.periodic1) {
+        ii = (ii + pd.n1) % pd.n1;
+      } else if (ii < 0 || ii >= pd.n1) {
+        continue;
+      }
+      const long long bits = __double_as_longlong(S[pd.off + (long long)jj * pd.n1 + ii]);
+      mb = bits > mb ? bits : mb;
+    }
+  }
+  muhat[p] = __dmul_rn(__dmul_rn(Rw[tc - 1], __longlong_as_double(mb)), pd.hhat);
+  if (tau) tau[p] = tc;
+}
+
+// separable window sums of eq. (Lambda): rows (q1) then columns (q2), zero outside, wrapped if periodic
+__global__ void k_window_rows(DevTables T, const double* __restrict__ in, double* __restrict__ out,
+                              const double* __restrict__ wtab, int r) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  const PatchDev pd = T.patches[pt_patch(T.info[p])];
+  const long long loc = p - pd.off;
+  const int j = (int)(loc / pd.n1), i = (int)(loc - (long long)j * pd.n1);
+  const double* row = in + pd.off + (long long)j * pd.n1;
+  double acc = 0.0;
+  for (int a = -(r - 1); a <= r - 1; ++a) {
+    int ii = i + a;
+    if (pd.periodic1) {
+      ii = (ii + pd.n1) % pd.n1;
+    } else if (ii < 0 || ii >= pd.n1) {
+      continue;
+    }
+    acc = fma(wtab[a + r - 1], row[ii], acc);
+  }
+  out[p] = acc;
+}
+
+__global__ void k_window_cols(DevTables T, const double* __restrict__ in, double* __restrict__ out,
+                              const double* __restrict__ wtab, int r) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  const PatchDev pd = T.patches[pt_patch(T.info[p])];
+  const long long loc = p - pd.off;
+  const int j = (int)(loc / pd.n1), i = (int)(loc - (long long)j * pd.n1);
+  double acc = 0.0;
+  for (int b = -(r - 1); b <= r - 1; ++b) {
+    const int jj = j + b;
+    if (jj < 0 || jj >= pd.n2) continue;
+    acc = fma(wtab[b + r - 1], in[pd.off + (long long)jj * pd.n1 + i], acc);
+  }
+  out[p] = acc;
+}
+
+// mu = (own window sum + window sums of the other patches at their nearest points) / normaliser
+__global__ void k_mu_own(DevTables T, const double* __restrict__ num, const double* __restrict__ den,
+                         double* __restrict__ mu) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  const double d = den[p];
+  mu[p] = ((T.info[p] & PT_BLANK) || !(d > 0.0)) ? 0.0 : num[p] / d;
+}
+__global__ void k_mu_cross(const double* __restrict__ num, const double* __restrict__ den, const int* __restrict__ dst,
+                           const int* __restrict__ ptr, const int* __restrict__ src, int n, double* __restrict__ mu) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = dst[i];
+  double s = num[p];
+  for (int k = ptr[i]; k < ptr[i + 1]; ++k) s += num[src[k]];
+  const double d = den[p];
+  mu[p] = d > 0.0 ? s / d : 0.0;
+}
+
+// ---------------------------------------------------------------- time step, eq. (CFL)
+__global__ void k_dt_reduce(DevTables T, const double* __restrict__ e, const double* __restrict__ mu,
+                            unsigned long long* __restrict__ pmax) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int patch = -1;
+  unsigned long long bs = 0, bm = 0;
+  if (p < T.P) {
+    const uint32_t f = T.info[p];
+    if (!(f & PT_BLANK)) {
+      patch = pt_patch(f);
+      const long long cs = T.P;
+      const double gam = T.gamma;
+      const double rho = e[p];
+      const double u = __ddiv_rn(e[p + cs], rho);
+      const double v = __ddiv_rn(e[p + 2 * cs], rho);
+      const double s2 = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+      const double pr = __dmul_rn(__dsub_rn(gam, 1.0), __dsub_rn(e[p + 3 * cs], __dmul_rn(__dmul_rn(0.5, rho), s2)));
+      const double Sv = __dadd_rn(__dadd_rn(fabs(u), fabs(v)), __dsqrt_rn(__ddiv_rn(__dmul_rn(gam, pr), rho)));
+      bs = (unsigned long long)__double_as_longlong(Sv);
+      bm = (unsigned long long)__double_as_longlong(mu[p]);
+      if (!(Sv >= 0.0)) bs = 0x7FF8000000000000ull;  // NaN: poison the patch maximum
+    }
+  }
+  const unsigned mask = __activemask();
+  const int p0 = __shfl_sync(mask, patch, 0);
+  if (__all_sync(mask, patch == p0) && p0 >= 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long s2 = __shfl_down_sync(mask, bs, o);
+      const unsigned long long m2 = __shfl_down_sync(mask, bm, o);
+      bs = s2 > bs ? s2 : bs;
+      bm = m2 > bm ? m2 : bm;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(pmax + 2 * p0, bs);
+      atomicMax(pmax + 2 * p0 + 1, bm);
+    }
+  } else if (patch >= 0) {
+    atomicMax(pmax + 2 * patch, bs);
+    atomicMax(pmax + 2 * patch + 1, bm);
+  }
+}
+
+__global__ void k_dt_final(DevTables T, const unsigned long long* __restrict__ pmax, double cfl, double* dt) {
+  __shared__ double red[256];
+  double best = INFINITY;
+  for (int q = threadIdx.x; q < T.npatch; q += blockDim.x) {
+    const double Sm = __longlong_as_double((long long)pmax[2 * q]);
+    const double Mm = __longlong_as_double((long long)pmax[2 * q + 1]);
+    const double h = T.patches[q].htil;
+    const double v = __ddiv_rn(cfl, __dadd_rn(__ddiv_rn(Sm, h), __ddiv_rn(Mm, __dmul_rn(h, h))));
+    best = (v < best || v != v) ? v : best;
+  }
+  red[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = red[threadIdx.x + s];
+      if (o < red[threadIdx.x] || o != o) red[threadIdx.x] = o;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *dt = __ddiv_rn(red[0], 3.141592653589793);
+}
+
+// non-finite / non-physical state detector: raises *flag, never traps
+__global__ void k_check_state(DevTables T, const double* __restrict__ e, int* flag) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= T.P) return;
+  if (T.info[p] & PT_BLANK) return;
+  const long long cs = T.P;
+  const double r = e[p], mx = e[p + cs], my = e[p + 2 * cs], E = e[p + 3 * cs];
+  const Prim q = primitives(r, mx, my, E, T.gamma);
+  const bool ok = isfinite(r) && isfinite(mx) && isfinite(my) && isfinite(E) && r > 0.0 && q.p > 0.0;
+  if (!ok) atomicExch(flag, (int)FC_ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------- launch wrappers
+static inline int grid_lines(int njobs, int Lmax) {
+  const int w = line_warps(Lmax);
+  int g = (njobs + w - 1) / w;
+  return g < 1 ? 1 : g;
+}
+#define LINE_CFG(njobs, Lmax) grid_lines(njobs, Lmax), line_warps(Lmax) * 32, line_smem_bytes(Lmax), st
+static inline unsigned grid_pts(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
+                    double* R1, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_cart_q1<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, mu, R1);
+}
+void launch_cart_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* mu, const double* R1,
+                    const StageCoef& sc, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_cart_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, mu, R1, sc);
+}
+void launch_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* G,
+                  cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_gen_A<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, G);
+}
+void launch_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
+                  const double* J, double* G, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_gen_B<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, mu, J, G);
+}
+void launch_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, double* G,
+                  const StageCoef& sc, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_gen_C<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, G, sc);
+}
+void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef& sc, cudaStream_t st) {
+  if (n <= 0) return;
+  k_rk_fixup<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, sc);
+}
+void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st) {
+  if (n <= 0) return;
+  k_bc<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, e, P);
+}
+void launch_exchange(const Recv* r, int n, double* e, long long P, cudaStream_t st) {
+  if (n <= 0) return;
+  k_exchange<<<grid_pts(n, 256), 256, 0, st>>>(r, n, e, P);
+}
+void launch_filter_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* F,
+                      cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_filter_q1<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, F);
+}
+void launch_filter_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* F, double* e,
+                      cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_filter_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, F, e);
+}
+void launch_filter_copy_q1(const DevTables& T, const int* idx, int n, const double* e, double* F, cudaStream_t st) {
+  if (n <= 0) return;
+  k_filter_copy_q1<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, e, F);
+}
+void launch_filter_copy_q2(const DevTables& T, const int* idx, int n, const double* F, double* e, cudaStream_t st) {
+  if (n <= 0) return;
+  k_filter_copy_q2<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, F, e);
+}
+void launch_visc_point(const DevTables& T, const double* e, double* phi, double* S, cudaStream_t st) {
+  k_visc_point<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, phi, S);
+}
+void launch_visc_muhat(const DevTables& T, const double* phi, const double* S, const float* w, const double* R,
+                       double* muhat, int32_t* tau, cudaStream_t st) {
+  k_visc_muhat<<<grid_pts(T.P, 128), 128, 0, st>>>(T, phi, S, w, R, muhat, tau);
+}
+void launch_window_rows(const DevTables& T, const double* in, double* out, const double* wtab, int r,
+                        cudaStream_t st) {
+  k_window_rows<<<grid_pts(T.P, 256), 256, 0, st>>>(T, in, out, wtab, r);
+}
+void launch_window_cols(const DevTables& T, const double* in, double* out, const double* wtab, int r,
+                        cudaStream_t st) {
+  k_window_cols<<<grid_pts(T.P, 256), 256, 0, st>>>(T, in, out, wtab, r);
+}
+void launch_mu_final(const DevTables& T, const double* num, const double* den, const int* cross_dst,
+                     const int* cross_ptr, const int* cross_src, int ncross, double* mu, cudaStream_t st) {
+  k_mu_own<<<grid_pts(T.P, 256), 256, 0, st>>>(T, num, den, mu);
+  if (ncross > 0) k_mu_cross<<<grid_pts(ncross, 256), 256, 0, st>>>(num, den, cross_dst, cross_ptr, cross_src, ncross, mu);
+}
+void launch_dt(const DevTables& T, const double* e, const double* mu, unsigned long long* pmax, double cfl, double* dt,
+               cudaStream_t st) {
+  cudaMemsetAsync(pmax, 0, sizeof(unsigned long long) * 2 * T.npatch, st);
+  k_dt_reduce<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, mu, pmax);
+  k_dt_final<<<1, 256, 0, st>>>(T, pmax, cfl, dt);
+}
+void set_kernel_attributes() {
+  const int cap = (int)SMEM_CAP;
+  cudaFuncSetAttribute(k_cart_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_cart_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_gen_A, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_gen_B, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_filter_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_filter_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st) {
+  k_check_state<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, flag);
+}
+
+}  // namespace fcx

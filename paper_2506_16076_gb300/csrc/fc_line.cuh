@@ -1,0 +1,328 @@
+// Per-line building blocks of the FC derivative and filter: mixed-radix Stockham FFT
+// stages in shared memory, FC-Gram continuation, spectral multipliers.
+//
+// Every function takes (lane, nl): lane index and lane count of the group that
+// processes the line (a warp: nl = 32). Work is split with strided loops and all
+// cross-lane exchange goes through shared memory separated by FC_SYNC(), so the
+// functions have no intra-warp register dependencies.
+#pragma once
+#include <math.h>
+
+#include "fc_internal.h"
+
+#ifdef __CUDA_ARCH__
+#define FC_SYNC() __syncwarp()
+#else
+#define FC_SYNC() \
+  do {            \
+  } while (0)
+#endif
+#define FC_HD __host__ __device__ __forceinline__
+
+namespace fcx {
+
+constexpr double TWO_PI = 6.283185307179586;
+
+FC_HD double2 cpx(double x, double y) {
+  double2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+FC_HD double2 cadd(double2 a, double2 b) { return cpx(a.x + b.x, a.y + b.y); }
+FC_HD double2 csub(double2 a, double2 b) { return cpx(a.x - b.x, a.y - b.y); }
+FC_HD double2 cscl(double2 a, double s) { return cpx(a.x * s, a.y * s); }
+FC_HD double2 cmul(double2 a, double2 w) { return cpx(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x)); }
+// s i b with s = -1 (forward transform) or +1 (inverse transform)
+template <bool INV>
+FC_HD double2 mul_si(double2 b) {
+  return INV ? cpx(-b.y, b.x) : cpx(b.y, -b.x);
+}
+
+// ---- small DFTs: y_q = sum_m x_m exp(s 2 pi i q m / R) ----
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+  FC_HD static void run(double2* v) {
+    double2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+  FC_HD static void run(double2* v) {
+    double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    double2 c = cadd(v[1], v[3]), d = mul_si<INV>(csub(v[1], v[3]));
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, d);
+    v[3] = csub(b, d);
+  }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+  FC_HD static void run(double2* v) {
+    double2 e[4] = {v[0], v[2], v[4], v[6]};
+    double2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, INV>::run(e);
+    Dft<4, INV>::run(o);
+    const double r = 0.7071067811865476;
+    const double s = INV ? 1.0 : -1.0;
+    double2 t1 = cpx(r * (o[1].x - s * o[1].y), r * (o[1].y + s * o[1].x));   // w8^1 o1
+    double2 t2 = mul_si<INV>(o[2]);                                            // w8^2 o2
+    double2 t3 = cpx(r * (-o[3].x - s * o[3].y), r * (-o[3].y + s * o[3].x));  // w8^3 o3
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
+  }
+};
+
+// odd R: pairs (x_m, x_{R-m}); y_q = x0 + sum_m cos(2 pi q m/R) a_m + s i sum_m sin(2 pi q m/R) b_m
+template <int R>
+struct OddConst;
+template <>
+struct OddConst<3> {
+  FC_HD static double c(int k) { return -0.5; }
+  FC_HD static double s(int k) { return 0.8660254037844387; }
+};
+template <>
+struct OddConst<5> {
+  FC_HD static double c(int k) { return k == 1 ? 0.30901699437494745 : -0.8090169943749473; }
+  FC_HD static double s(int k) { return k == 1 ? 0.9510565162951535 : 0.5877852522924732; }
+};
+template <>
+struct OddConst<7> {
+  FC_HD static double c(int k) {
+    return k == 1 ? 0.6234898018587336 : (k == 2 ? -0.22252093395631434 : -0.900968867902419);
+  }
+  FC_HD static double s(int k) {
+    return k == 1 ? 0.7818314824680298 : (k == 2 ? 0.9749279121818236 : 0.43388373911755823);
+  }
+};
+
+template <int R, bool INV>
+struct DftOdd {
+  FC_HD static void run(double2* v) {
+    constexpr int H = (R - 1) / 2;
+    double2 a[H], b[H];
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      a[m - 1] = cadd(v[m], v[R - m]);
+      b[m - 1] = csub(v[m], v[R - m]);
+    }
+    double2 x0 = v[0];
+    double2 y0 = x0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) y0 = cadd(y0, a[m]);
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      double2 t = x0, u = cpx(0.0, 0.0);
+#pragma unroll
+      for (int m = 1; m <= H; ++m) {
+        int km = (q * m) % R;  // angle index in 1..R-1
+        double cc, ss;
+        if (km <= H) {
+          cc = OddConst<R>::c(km);
+          ss = OddConst<R>::s(km);
+        } else {
+          cc = OddConst<R>::c(R - km);
+          ss = -OddConst<R>::s(R - km);
+        }
+        t = cpx(fma(cc, a[m - 1].x, t.x), fma(cc, a[m - 1].y, t.y));
+        u = cpx(fma(ss, b[m - 1].x, u.x), fma(ss, b[m - 1].y, u.y));
+      }
+      double2 iu = mul_si<INV>(u);
+      v[q] = cadd(t, iu);
+      v[R - q] = csub(t, iu);
+    }
+    v[0] = y0;
+  }
+};
+template <bool INV>
+struct Dft<3, INV> : DftOdd<3, INV> {};
+template <bool INV>
+struct Dft<5, INV> : DftOdd<5, INV> {};
+template <bool INV>
+struct Dft<7, INV> : DftOdd<7, INV> {};
+
+// ---- one Stockham stage of radix R over nseq sequences of length L (Ns = product of earlier radices)
+template <int R, bool INV>
+FC_HD void stage_r(const double2* __restrict__ in, double2* __restrict__ out, int L, int Ns, int nseq,
+                   const double2* __restrict__ tw, int lane, int nl) {
+  const int nb = L / R;
+  const int tws = L / (Ns * R);
+  for (int idx = lane; idx < nseq * nb; idx += nl) {
+    const int s = idx / nb;
+    const int j = idx - s * nb;
+    const double2* x = in + s * L;
+    double2* y = out + s * L;
+    const int k = j % Ns;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[j + r * nb];
+    if (k != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        double2 w = tw[r * k * tws];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    Dft<R, INV>::run(v);
+    const int base = j + (j / Ns) * Ns * (R - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[base + r * Ns] = v[r];
+  }
+}
+
+// generic radix (any prime R): one output element per iteration, O(R) work each
+template <bool INV>
+FC_HD void stage_gen(const double2* __restrict__ in, double2* __restrict__ out, int L, int Ns, int R, int nseq,
+                     const double2* __restrict__ tw, int lane, int nl) {
+  const int nb = L / R;
+  const int str = L / (Ns * R);
+  for (int idx = lane; idx < nseq * L; idx += nl) {
+    const int s = idx / L;
+    const int o = idx - s * L;
+    const int g = o / (Ns * R);
+    const int rem = o - g * Ns * R;
+    const int q = rem / Ns;
+    const int k = rem - q * Ns;
+    const int j = g * Ns + k;
+    const double2* x = in + s * L;
+    const int ph = (k + q * Ns) * str;  // < L
+    int e = 0;
+    double ax = 0.0, ay = 0.0;
+    for (int m = 0; m < R; ++m) {
+      double2 w = tw[e];
+      if (INV) w.y = -w.y;
+      const double2 xv = x[j + m * nb];
+      ax = fma(xv.x, w.x, fma(-xv.y, w.y, ax));
+      ay = fma(xv.x, w.y, fma(xv.y, w.x, ay));
+      e += ph;
+      if (e >= L) e -= L;
+    }
+    out[s * L + o] = cpx(ax, ay);
+  }
+}
+
+// Full transform of nseq sequences stored back to back in a (length L each); b is scratch
+// of the same size. Returns the buffer that holds the result (a or b).
+template <bool INV>
+FC_HD double2* fft_lines(double2* a, double2* b, const Plan& P, int nseq, const double2* twpool, int lane, int nl) {
+  const double2* tw = twpool + P.tw;
+  const int L = P.L;
+  int Ns = 1;
+  for (int st = 0; st < P.nst; ++st) {
+    const int R = P.rad[st];
+    switch (R) {
+      case 2: stage_r<2, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      case 3: stage_r<3, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      case 4: stage_r<4, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      case 5: stage_r<5, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      case 7: stage_r<7, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      case 8: stage_r<8, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
+      default: stage_gen<INV>(a, b, L, Ns, R, nseq, tw, lane, nl); break;
+    }
+    FC_SYNC();
+    double2* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// FC-Gram continuation (eq. continuation) of the nseq complex sequences in a: entries
+// [0, n) hold the data (two real lines packed as re/im); entries [n, n+C) receive
+//   ext = ML F_l + MR F_r,   ML = A_l Q^T, MR = A_r Q^T (C x d).
+// ML and MR have entries of order 1e4 (d = 5) whose contributions cancel, so the same
+// linear map is evaluated in detrended form: with F~_l = F_l - F_0 - (F_1 - F_0) tau_l
+// (tau_l = 0..d-1) and F~_r = F_r - F_{n-1} - (F_{n-1} - F_{n-2}) tau_r (tau_r = 1-d..0),
+//   ext = ML F~_l + MR F~_r + F_0 uL + (F_1 - F_0) vL + F_{n-1} uR + (F_{n-1} - F_{n-2}) vR
+// with uL = ML 1, vL = ML tau_l, uR = MR 1, vR = MR tau_r precomputed. The detrended
+// values are differences of nearby samples (exact or nearly so), so the large
+// coefficients multiply only second differences. Layout of M: ML, MR, uL, vL, uR, vR.
+FC_HD void continue_lines(double2* a, int L, int n, int C, int d, const double* __restrict__ M, int nseq, int lane,
+                          int nl) {
+  const double* ML = M;
+  const double* MR = M + C * d;
+  const double* uL = MR + C * d;
+  const double* vL = uL + C;
+  const double* uR = vL + C;
+  const double* vR = uR + C;
+  for (int idx = lane; idx < nseq * C; idx += nl) {
+    const int s = idx / C;
+    const int k = idx - s * C;
+    const double2* x = a + s * L;
+    const double2 f0 = x[0], f1 = x[1], fn = x[n - 1], fm = x[n - 2];
+    const double dlx = f1.x - f0.x, dly = f1.y - f0.y;
+    const double drx = fn.x - fm.x, dry = fn.y - fm.y;
+    double ex = 0.0, ey = 0.0;
+    for (int j = 2; j < d; ++j) {
+      const double ml = ML[k * d + j];
+      const double2 fl = x[j];
+      ex = fma(ml, (fl.x - f0.x) - (double)j * dlx, ex);
+      ey = fma(ml, (fl.y - f0.y) - (double)j * dly, ey);
+    }
+    for (int j = 0; j < d - 2; ++j) {
+      const double mr = MR[k * d + j];
+      const double2 fr = x[n - d + j];
+      const double t = (double)(d - 1 - j);
+      ex = fma(mr, (fr.x - fn.x) + t * drx, ex);
+      ey = fma(mr, (fr.y - fn.y) + t * dry, ey);
+    }
+    ex = fma(f0.x, uL[k], fma(dlx, vL[k], fma(fn.x, uR[k], fma(drx, vR[k], ex))));
+    ey = fma(f0.y, uL[k], fma(dly, vL[k], fma(fn.y, uR[k], fma(dry, vR[k], ey))));
+    a[s * L + n + k] = cpx(ex, ey);
+  }
+}
+
+// Z_k <- i m_k Z_k with m_k = fac * k, k the signed mode number; the Nyquist mode of an
+// even length gets 0 (eq. fc_der). fac includes the 1/L of the inverse transform.
+FC_HD void mul_deriv(double2* a, int L, int nseq, double fac, int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) {
+    const int s = idx / L;
+    const int t = idx - s * L;
+    int kk = (2 * t <= L) ? t : t - L;
+    if (2 * t == L) kk = 0;
+    const double m = fac * (double)kk;
+    const double2 z = a[idx];
+    a[idx] = cpx(-m * z.y, m * z.x);
+  }
+}
+
+// Z_k <- sig[k] Z_k (sig already divided by L) (eq. filtering)
+FC_HD void mul_filter(double2* a, int L, int nseq, const double* __restrict__ sig, int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) {
+    const int s = idx / L;
+    const int t = idx - s * L;
+    a[idx] = cscl(a[idx], sig[t]);
+  }
+}
+
+// ---- Euler physics (Sec. 2.1) ----
+struct Prim {
+  double rho, u, v, p;
+};
+FC_HD Prim primitives(double r, double mx, double my, double E, double gam) {
+  Prim q;
+  const double ir = 1.0 / r;
+  q.rho = r;
+  q.u = mx * ir;
+  q.v = my * ir;
+  q.p = (gam - 1.0) * (E - 0.5 * (mx * q.u + my * q.v));
+  return q;
+}
+
+}  // namespace fcx

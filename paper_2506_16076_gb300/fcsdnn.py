@@ -1,0 +1,251 @@
+"""Thin Python binding of the C ABI in include/fcsdnn.h (ctypes; marshalling only).
+
+Every step of the operator runs in the CUDA library; this module only packs
+descriptors, loads the method data files (FC-Gram tables, classifier weights),
+and passes device pointers of torch tensors and the current CUDA stream. It
+raises if the library is missing: there is no CPU path.
+"""
+import ctypes as C
+import functools
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_lib", "libfcsdnn.so")
+_lib = None
+
+FC_OK = 0
+STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID", 2: "FC_ERR_CUDA", 3: "FC_ERR_DONOR", 4: "FC_ERR_OVERLAP",
+          5: "FC_ERR_NONFINITE", 6: "FC_ERR_TIMEOUT", 7: "FC_ERR_UNIMPLEMENTED", 8: "FC_ERR_OOM"}
+STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4, 8, 16
+
+# every symbol include/fcsdnn.h declares
+EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
+           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_sync_status",
+           "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
+           "fc_pass_stats", "fc_last_error", "fc_destroy"]
+
+
+class FcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PatchDescC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("geom", C.c_double * 4),
+                ("side", C.c_int * 4), ("bc", (C.c_double * 4) * 4), ("hole", C.c_double * 3)]
+
+
+class ParamsC(C.Structure):
+    _fields_ = [("d", C.c_int), ("C0", C.c_int), ("c_policy", C.c_int), ("gamma", C.c_double),
+                ("alpha_f", C.c_double), ("p_f", C.c_int), ("cfl", C.c_double), ("n_f", C.c_int),
+                ("n_v", C.c_int), ("win_r", C.c_int), ("loc", C.c_int), ("R", C.c_double * 4),
+                ("depth_cap", C.c_int), ("fc_tables", C.POINTER(C.c_double)), ("fc_tables_len", C.c_int),
+                ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int)]
+
+
+def library_path():
+    return _LIBPATH
+
+
+def load():
+    """Load libfcsdnn.so (building it first if the sources are newer); raise if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        from . import build
+        build.build()
+    lib = C.CDLL(_LIBPATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "fc_init_patches": (C.c_int, [C.POINTER(vp), C.POINTER(PatchDescC), ip, C.POINTER(ParamsC), vp]),
+        "fc_state_size": (C.c_size_t, [vp]),
+        "fc_active_points": (C.c_size_t, [vp]),
+        "fc_patch_offset": (C.c_int, [vp, ip, C.POINTER(C.c_size_t)]),
+        "fc_rhs": (C.c_int, [vp, vp, vp, vp, vp]),
+        "fc_viscosity": (C.c_int, [vp, vp, vp, vp, vp]),
+        "fc_filter": (C.c_int, [vp, vp, vp]),
+        "fc_project": (C.c_int, [vp, vp, vp]),
+        "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
+        "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
+        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
+        "fc_sync_status": (C.c_int, [vp, vp, ip, vp]),
+        "fc_launch_count": (C.c_uint64, [vp]),
+        "fc_profile_enable": (C.c_int, [vp, ip]),
+        "fc_profile_read": (C.c_int, [vp]),
+        "fc_profile_get": (C.c_int, [vp, ip, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+        "fc_profile_reset": (C.c_int, [vp]),
+        "fc_pass_stats": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "fc_last_error": (C.c_char_p, [vp]),
+        "fc_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+@functools.lru_cache(maxsize=None)
+def fc_table_blob(d):
+    """Pack fc_tables_d{d}.txt as the fc_params.fc_tables array: d, Cmin, Cmax, then Q, A_l, A_r per C."""
+    path = os.path.join(_HERE, "data", f"fc_tables_d{d}.txt")
+    with open(path) as f:
+        lines = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    blocks, i = [], 0
+    while lines[i] != "end":
+        c = int(lines[i + 1].split()[1])
+        i += 2
+        rows = []
+        for name, nr in (("Q", d), ("AL", c), ("AR", c)):
+            assert lines[i] == name
+            rows += [float(v) for r in range(nr) for v in lines[i + 1 + r].split()]
+            i += 1 + nr
+        blocks.append((c, rows))
+    blocks.sort()
+    cs = [c for c, _ in blocks]
+    assert cs == list(range(cs[0], cs[-1] + 1))
+    out = [float(d), float(cs[0]), float(cs[-1])]
+    for _, rows in blocks:
+        out += rows
+    return np.array(out, dtype=np.float64)
+
+
+@functools.lru_cache(maxsize=None)
+def sdnn_blob():
+    """fc_params.sdnn_w: W1, b1, W2, b2, W3, b3 of the stand-in classifier (FP32)."""
+    path = os.path.join(_HERE, "data", "sdnn_standin.txt")
+    with open(path) as f:
+        lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    vals, i = [], 0
+    while i < len(lines):
+        r = int(lines[i][1])
+        vals += [float(v) for k in range(r) for v in lines[i + 1 + k]]
+        i += 1 + r
+    return np.array(vals, dtype=np.float32)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One fc_ctx: geometry and device workspaces of a workload."""
+
+    def __init__(self, workload: W.Workload):
+        lib = load()
+        self.lib = lib
+        self.w = workload
+        prm = workload.params
+        n = len(workload.patches)
+        descs = (PatchDescC * n)()
+        for k, p in enumerate(workload.patches):
+            dsc = descs[k]
+            dsc.kind, dsc.n1, dsc.n2 = p.kind, p.n1, p.n2
+            for m in range(4):
+                dsc.geom[m] = p.geom[m]
+                dsc.side[m] = p.side[m]
+                for q in range(4):
+                    dsc.bc[m][q] = p.bc[m][q]
+            for m in range(3):
+                dsc.hole[m] = p.hole[m]
+        self._tab = fc_table_blob(prm.d)
+        self._sd = sdnn_blob()
+        P = ParamsC()
+        P.d, P.C0, P.c_policy, P.gamma, P.alpha_f, P.p_f = prm.d, prm.C0, prm.c_policy, prm.gamma, prm.alpha_f, prm.p_f
+        P.cfl, P.n_f, P.n_v, P.win_r, P.loc, P.depth_cap = prm.cfl, prm.n_f, prm.n_v, prm.win_r, prm.loc, prm.depth_cap
+        for m in range(4):
+            P.R[m] = prm.R[m]
+        P.fc_tables = self._tab.ctypes.data_as(C.POINTER(C.c_double))
+        P.fc_tables_len = len(self._tab)
+        P.sdnn_w = self._sd.ctypes.data_as(C.POINTER(C.c_float))
+        P.sdnn_len = len(self._sd)
+        ctx = C.c_void_p()
+        st = lib.fc_init_patches(C.byref(ctx), descs, n, C.byref(P), None)
+        if st != FC_OK:
+            raise FcError(st, "fc_init_patches failed (see stderr)")
+        self.ctx = ctx
+        self.P = lib.fc_state_size(ctx)
+        self.active = lib.fc_active_points(ctx)
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            self.lib.fc_destroy(self.ctx)
+            self.ctx = None
+
+    def _check(self, st):
+        if st != FC_OK:
+            raise FcError(st, self.lib.fc_last_error(self.ctx).decode())
+
+    def offsets(self):
+        out = []
+        for k in range(len(self.w.patches)):
+            o = C.c_size_t()
+            self._check(self.lib.fc_patch_offset(self.ctx, k, C.byref(o)))
+            out.append(o.value)
+        return out
+
+    def rhs(self, e, out, mu=None):
+        self._check(self.lib.fc_rhs(self.ctx, _ptr(e), _ptr(out), _ptr(mu), _stream()))
+
+    def viscosity(self, e, mu, tau=None):
+        self._check(self.lib.fc_viscosity(self.ctx, _ptr(e), _ptr(mu), _ptr(tau), _stream()))
+
+    def filter(self, e):
+        self._check(self.lib.fc_filter(self.ctx, _ptr(e), _stream()))
+
+    def project(self, e):
+        self._check(self.lib.fc_project(self.ctx, _ptr(e), _stream()))
+
+    def timestep(self, e, mu, dt):
+        self._check(self.lib.fc_timestep(self.ctx, _ptr(e), _ptr(mu), _ptr(dt), _stream()))
+
+    def rk_step(self, e, dt, mu, flags=0):
+        self._check(self.lib.fc_rk_step(self.ctx, _ptr(e), _ptr(dt), _ptr(mu), int(flags), _stream()))
+
+    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n):
+        self._check(self.lib.fc_adjoint_step(self.ctx, _ptr(e_n), _ptr(mu), _ptr(dt), _ptr(lam_np1), _ptr(lam_n),
+                                             _stream()))
+
+    def sync_status(self, e=None, check_state=True):
+        return self.lib.fc_sync_status(self.ctx, _ptr(e), 1 if (check_state and e is not None) else 0, _stream())
+
+    def launch_count(self):
+        return int(self.lib.fc_launch_count(self.ctx))
+
+    def profile(self, enable=True):
+        self._check(self.lib.fc_profile_enable(self.ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """{group name: (total ms, launches)} of the instrumented calls since the last reset."""
+        n = self.lib.fc_profile_read(self.ctx)
+        if n < 0:
+            raise FcError(2, "fc_profile_read failed")
+        out = {}
+        for k in range(n):
+            nm, ms, cnt = C.c_char_p(), C.c_double(), C.c_int()
+            self._check(self.lib.fc_profile_get(self.ctx, k, C.byref(nm), C.byref(ms), C.byref(cnt)))
+            out[nm.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def pass_stats(self, name):
+        """(algorithmic FP64 flops, compulsory bytes, lines, points) of one launch of a line pass."""
+        f, b, nl, npt = C.c_double(), C.c_double(), C.c_longlong(), C.c_longlong()
+        self._check(self.lib.fc_pass_stats(self.ctx, name.encode(), C.byref(f), C.byref(b), C.byref(nl),
+                                           C.byref(npt)))
+        return f.value, b.value, nl.value, npt.value
+
+    def profile_reset(self):
+        self._check(self.lib.fc_profile_reset(self.ctx))

@@ -262,8 +262,8 @@ def random_smooth_state(w: Workload, seed, amp=0.05):
         x, y = patch_xy(p)
         prim = []
         for c in range(4):
-            base = fs[c] if c in (0, 3) else fs[c]
-            pert = amp * np.sin(kx[c] * x + ph[c]) * np.cos(ky[c] * y + 0.3 * ph[c])
-            prim.append(base * (1.0 + pert) if c in (0, 3) else base + amp * 3 * pert)
+            pert = np.sin(kx[c] * x + ph[c]) * np.cos(ky[c] * y + 0.3 * ph[c])
+            # density and pressure: relative perturbation; velocities: 3 amp (sound speed ~ 1)
+            prim.append(fs[c] * (1.0 + amp * pert) if c in (0, 3) else fs[c] + 3.0 * amp * pert)
         out.append(prim_to_cons(*prim, gamma=w.params.gamma))
     return out

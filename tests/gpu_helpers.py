@@ -1,0 +1,43 @@
+"""Helpers of the GPU parity tests: flat device state <-> oracle per-patch arrays, error measure."""
+import numpy as np
+import torch
+
+from paper_2506_16076_gb300 import workloads as W
+
+
+def to_dev(per_patch):
+    return torch.from_numpy(np.ascontiguousarray(W.flatten(per_patch))).cuda()
+
+
+def to_dev_scalar_field(per_patch):
+    return torch.from_numpy(np.ascontiguousarray(np.concatenate([a.ravel() for a in per_patch]))).cuda()
+
+
+def from_dev(t, w, ncomp=4):
+    a = t.detach().cpu().numpy()
+    if ncomp == 1:
+        a = a[None]
+    out = W.unflatten(a, w)
+    return [o[0] for o in out] if ncomp == 1 else out
+
+
+def rel_err(gpu, orc, mask=None):
+    """Per component max|gpu - orc| / max|orc| (over all patches), as a list of 4."""
+    errs = []
+    for c in range(gpu[0].shape[0]):
+        num = max(np.abs(np.where(m, g[c] - o[c], 0.0) if m is not None else g[c] - o[c]).max()
+                  for g, o, m in zip(gpu, orc, mask or [None] * len(gpu)))
+        den = max(np.abs(o[c]).max() for o in orc)
+        errs.append(num / max(den, 1e-300))
+    return errs
+
+
+def smooth_mu(w, seed, scale):
+    """Seeded smooth non-negative viscosity field (a frozen mu for RHS parity)."""
+    rng = np.random.default_rng(seed)
+    a, b, c = rng.uniform(1, 3, 3)
+    out = []
+    for p in w.patches:
+        x, y = W.patch_xy(p)
+        out.append(scale * (1.0 + np.sin(a * x) * np.cos(b * y + c)) ** 2)
+    return out
