@@ -134,10 +134,25 @@ fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, do
  * and the exchange. mu_dev: P doubles, written (or read with FROZEN_MU). */
 fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
 
-/* Discrete adjoint of fc_rk_step with mu and dt frozen (no filter):
- * lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev at the step that starts from e_n_dev. */
+/* Discrete adjoint of one fc_rk_step with mu and dt frozen and no filter (the
+ * smoothness classifier is not differentiable, so the viscosity of the forward step
+ * is held fixed): lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev for the step that
+ * starts from e_n_dev with viscosity mu_dev (P doubles) and step *dt_dev (device
+ * scalar). The stage states are recomputed from e_n_dev. Transposes: FC derivative
+ * (zero padding, negated spectral derivative, continuation folded back onto the
+ * 2d end points), flux Jacobians, viscous term with mu fixed, inter-patch exchange
+ * (donors gather the receivers' adjoint with the interpolation weights), boundary
+ * overwrite. gbc_dev (nullable, [4][P]) accumulates the adjoint that reaches the
+ * Dirichlet points, i.e. the sensitivity of the step result to the imposed states.
+ * The first call allocates 11 state-sized device buffers. */
 fc_status fc_adjoint_step(fc_ctx *ctx, const double *e_n_dev, const double *mu_dev, const double *dt_dev,
-                          const double *lam_np1_dev, double *lam_n_dev, void *stream);
+                          const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, void *stream);
+
+/* Wall-pressure drag functional J = sum over the wall ring of the first curvilinear
+ * patch with a slip wall of p n_x r0 dtheta (periodic trapezoid of the integral of
+ * wall pressure times n_x, n the outward body normal); J_dev: device scalar.
+ * dJde_dev (nullable, [4][P]): dJ/de, zero off the wall. */
+fc_status fc_drag(fc_ctx *ctx, const double *e_dev, double *J_dev, double *dJde_dev, void *stream);
 
 /* Reads the device error flag (synchronises the stream): FC_OK, FC_ERR_NONFINITE or FC_ERR_TIMEOUT.
  * check_state != 0 also scans e_dev (may be NULL otherwise) for NaN/Inf and rho, p <= 0. */

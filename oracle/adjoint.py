@@ -1,0 +1,242 @@
+"""Discrete adjoint of the semi-discrete operator and of one SSPRK-4 step (oracle).
+
+Test infrastructure only (see oracle/__init__.py).
+
+The forward map is the step of Algorithm 1 with the viscosity mu and the time
+step dt frozen (the smoothness classifier is not differentiable) and no filter:
+    u_0 = P(e_n),  u_i = P( sum_k alpha_ik u_k + beta_ik dt L(u_k) ),  e_{n+1} = u_5,
+with P the boundary overwrite followed by the inter-patch exchange (Sec. 4.2,
+Sec. 3.4.1) and L the operator of eq. (semi-discrete) in the curvilinear form of
+eq. (general_curvilinear):
+    L(u) = -N sum_k sum_i J_ki D_k( f_i(u) - mu sum_m J_mi D_m u ),
+N = zeroing on points where a derivative is undefined. Its linearisation
+transposes to
+    eta_i = -sum_k D_k^T (J_ki N lam),
+    L'(u)^T lam = sum_i A_i(u)^T eta_i - sum_m D_m^T ( mu sum_i J_mi eta_i ),
+A_i = d f_i / d e the flux Jacobians, D^T the transposed FC derivative
+(fc.fc_derivative_T). P^T: the exchange transpose scatters each receiver's
+adjoint to its donors with the Neville (Lagrange) weights and zeroes the
+receiver; the boundary transpose zeroes Dirichlet points (their adjoint is the
+sensitivity to the imposed state) and projects out the wall-normal momentum.
+"""
+import numpy as np
+
+from paper_2506_16076_gb300 import workloads as W
+from . import fc
+from .geometry import neville
+from .solver import SSP54_ALPHA, SSP54_BETA
+
+
+def flux_jacobians(e, gam):
+    """A_x, A_y with A[c][j] = d f_c / d e_j (eq. euler 2d equation), arrays (4, 4, ...)."""
+    rho, m, n, E = e
+    u, v = m / rho, n / rho
+    g1 = gam - 1.0
+    p = g1 * (E - 0.5 * rho * (u * u + v * v))
+    pr, pm, pn, pE = 0.5 * g1 * (u * u + v * v), -g1 * u, -g1 * v, g1 + 0 * u
+    H = (E + p) / rho
+    z, o = 0 * u, 1 + 0 * u
+    Ax = np.array([[z, o, z, z],
+                   [-u * u + pr, 2 * u + pm, pn, pE],
+                   [-u * v, v, u, z],
+                   [-u * H + u * pr, H + u * pm, u * pn, u * (1 + pE)]])
+    Ay = np.array([[z, z, o, z],
+                   [-u * v, v, u, z],
+                   [-v * v + pr, pm, 2 * v + pn, pE],
+                   [-v * H + v * pr, v * pm, H + v * pn, v * (1 + pE)]])
+    return Ax, Ay
+
+
+def d1T(sv, g, G):
+    out = np.zeros_like(G)
+    prm = sv.prm
+    for (j, a, n, per) in g.seg1:
+        if per:
+            out[..., j, a:a + n] = fc.periodic_derivative_T(G[..., j, a:a + n], g.h1)
+        elif n >= 2 * prm.d:
+            out[..., j, a:a + n] = fc.fc_derivative_T(G[..., j, a:a + n], g.h1, prm.d,
+                                                      fc.choose_C(n, prm.C0, prm.c_policy))
+    return out
+
+
+def d2T(sv, g, G):
+    out = np.zeros_like(G)
+    prm = sv.prm
+    for (i, a, n, per) in g.seg2:
+        if n >= 2 * prm.d:
+            out[..., a:a + n, i] = fc.fc_derivative_T(G[..., a:a + n, i], g.h2, prm.d,
+                                                      fc.choose_C(n, prm.C0, prm.c_policy))
+    return out
+
+
+def rhs_adjoint_patch(sv, g, u, mu, lam):
+    """L'(u)^T lam on one patch."""
+    J1x, J1y, J2x, J2y = g.J
+    lm = np.where(g.nodiff[None], 0.0, lam)
+    eta_x = -(d1T(sv, g, J1x * lm) + d2T(sv, g, J2x * lm))
+    eta_y = -(d1T(sv, g, J1y * lm) + d2T(sv, g, J2y * lm))
+    Ax, Ay = flux_jacobians(u, sv.prm.gamma)
+    out = np.einsum("cj...,c...->j...", Ax, eta_x) + np.einsum("cj...,c...->j...", Ay, eta_y)
+    out -= d1T(sv, g, mu * (J1x * eta_x + J1y * eta_y))
+    out -= d2T(sv, g, mu * (J2x * eta_x + J2y * eta_y))
+    return out
+
+
+def rhs_adjoint(sv, states, mus, lams):
+    return [rhs_adjoint_patch(sv, g, u, m, l) for g, u, m, l in zip(sv.geos, states, mus, lams)]
+
+
+def exchange_T(sv, lams):
+    """Transpose of the exchange: receiver adjoints scattered to donors, receivers zeroed."""
+    out = [l.copy() for l in lams]
+    nodes = (0.0, 1.0, 2.0)
+    for p, it in enumerate(sv.conn.items):
+        if len(it["j"]) == 0:
+            continue
+        lr = lams[p][:, it["j"], it["i"]]
+        for q in np.unique(it["donor"]):
+            sel = it["donor"] == q
+            h = sv.geos[q]
+            t1, t2 = it["t1"][sel], it["t2"][sel]
+            for m2 in range(3):
+                w2 = neville(nodes, [np.full_like(t2, float(k == m2)) for k in range(3)], t2)
+                for m1 in range(3):
+                    w1 = neville(nodes, [np.full_like(t1, float(k == m1)) for k in range(3)], t1)
+                    i1 = it["a1"][sel] + m1
+                    i1 = np.mod(i1, h.n1) if h.periodic1 else i1
+                    i2 = it["a2"][sel] + m2
+                    np.add.at(out[q], (slice(None), i2, i1), w2 * w1 * lr[:, sel])
+    for p, it in enumerate(sv.conn.items):
+        if len(it["j"]):
+            out[p][:, it["j"], it["i"]] = 0.0
+    return out
+
+
+def bc_T(sv, lams, gbc=None):
+    """Transpose of the boundary overwrite (slip then Dirichlet); gbc accumulates the
+    adjoint arriving at Dirichlet points (sensitivity to the imposed states)."""
+    from .solver import _side_slice
+    out = [l.copy() for l in lams]
+    for k, (g, lam) in enumerate(zip(sv.geos, out)):
+        side = g.desc.side
+        for s in range(4):
+            if side[s] != W.DIRICHLET:
+                continue
+            sl = _side_slice(s)
+            keep = g.blank[sl]
+            if gbc is not None:
+                gbc[k][(slice(None),) + sl] += np.where(keep, 0.0, lam[(slice(None),) + sl])
+            lam[(slice(None),) + sl] = np.where(keep, lam[(slice(None),) + sl], 0.0)
+        for s in range(4):
+            if side[s] != W.SLIPWALL:
+                continue
+            sl = _side_slice(s)
+            if g.kind == W.AFFINE:
+                comp = 1 if s < 2 else 2
+                lam[comp][sl] = np.where(g.blank[sl], lam[comp][sl], 0.0)
+            else:
+                c, sn = g.cos[sl], g.sin[sl]
+                mn = lam[1][sl] * c + lam[2][sl] * sn
+                lam[1][sl] = lam[1][sl] - mn * c
+                lam[2][sl] = lam[2][sl] - mn * sn
+    return out
+
+
+def project_T(sv, lams, gbc=None):
+    """P = exchange o bc  =>  P^T = bc^T o exchange^T."""
+    return bc_T(sv, exchange_T(sv, lams), gbc)
+
+
+def step_forward(sv, e_n, mu, dt):
+    """The differentiated step (mu, dt frozen, no filter); returns the stage states u_0..u_5."""
+    u = [sv.project([a.copy() for a in e_n])]
+    Ls = {}
+    for i in range(5):
+        new = []
+        for p in range(len(sv.geos)):
+            acc = np.zeros_like(u[0][p])
+            for k in range(i + 1):
+                if SSP54_ALPHA[i][k] != 0.0:
+                    acc = acc + SSP54_ALPHA[i][k] * u[k][p]
+                if SSP54_BETA[i][k] != 0.0:
+                    if k not in Ls:
+                        Ls[k] = sv.rhs(u[k], mu)
+                    acc = acc + SSP54_BETA[i][k] * dt * Ls[k][p]
+            new.append(acc)
+        u.append(sv.project(new))
+    return u
+
+
+def step_adjoint(sv, e_n, mu, dt, lam_np1):
+    """lam_n = (d e_{n+1}/d e_n)^T lam_{n+1} and the Dirichlet sensitivity of the step."""
+    u = step_forward(sv, e_n, mu, dt)
+    npch = len(sv.geos)
+    gbc = [np.zeros_like(a) for a in e_n]
+    lam_u = [[np.zeros_like(a) for a in e_n] for _ in range(6)]
+    psi = [[np.zeros_like(a) for a in e_n] for _ in range(6)]  # sum_i beta_ik lam_v_i
+    lam_u[5] = [l.copy() for l in lam_np1]
+    for i in range(5, 0, -1):
+        if any(np.any(x) for x in psi[i]):
+            add = rhs_adjoint(sv, u[i], mu, psi[i])
+            lam_u[i] = [a + dt * b for a, b in zip(lam_u[i], add)]
+        lam_v = project_T(sv, lam_u[i], gbc)
+        for k in range(i):
+            al, be = SSP54_ALPHA[i - 1][k], SSP54_BETA[i - 1][k]
+            for p in range(npch):
+                if al != 0.0:
+                    lam_u[k][p] = lam_u[k][p] + al * lam_v[p]
+                if be != 0.0:
+                    psi[k][p] = psi[k][p] + be * lam_v[p]
+    add = rhs_adjoint(sv, u[0], mu, psi[0])
+    lam_u[0] = [a + dt * b for a, b in zip(lam_u[0], add)]
+    lam_n = project_T(sv, lam_u[0], gbc)
+    return lam_n, gbc
+
+
+def step_jvp_complex(sv, e_n, mu, dt, v, h=1e-30):
+    """Directional derivative of the frozen step by the complex step: Im(step(e + i h v)) / h."""
+    z = [a + 1j * h * b for a, b in zip(e_n, v)]
+    out = step_forward(sv, z, mu, dt)[5]
+    return [np.imag(a) / h for a in out]
+
+
+def rhs_jvp_complex(sv, u, mu, v, h=1e-30):
+    z = [a + 1j * h * b for a, b in zip(u, v)]
+    return [np.imag(a) / h for a in sv.rhs(z, mu)]
+
+
+def project_jvp_complex(sv, u, v, h=1e-30):
+    z = [a + 1j * h * b for a, b in zip(u, v)]
+    return [np.imag(a) / h for a in sv.project(z)]
+
+
+def wall_drag(sv, states):
+    """J = sum over the wall ring of the first curvilinear patch of p n_x r0 dtheta
+    (periodic trapezoid of the integral of wall pressure times n_x, outward body normal)."""
+    from . import euler
+    for g, e in zip(sv.geos, states):
+        if g.kind == W.OGRID and g.desc.side[2] == W.SLIPWALL:
+            r0 = g.desc.geom[2]
+            p = euler.primitives(e[:, 0, :], sv.prm.gamma)[3]
+            return np.sum(p * g.cos[0]) * r0 * 2 * np.pi / g.n1
+    raise ValueError("no wall")
+
+
+def wall_drag_grad(sv, states):
+    """dJ/de for wall_drag (same layout as states)."""
+    from . import euler
+    out = [np.zeros_like(e) for e in states]
+    gam = sv.prm.gamma
+    for k, (g, e) in enumerate(zip(sv.geos, states)):
+        if g.kind == W.OGRID and g.desc.side[2] == W.SLIPWALL:
+            r0 = g.desc.geom[2]
+            rho, m, n, E = e[:, 0, :]
+            w = g.cos[0] * r0 * 2 * np.pi / g.n1
+            g1 = gam - 1.0
+            u, v = m / rho, n / rho
+            out[k][0, 0, :] = w * g1 * 0.5 * (u * u + v * v)
+            out[k][1, 0, :] = -w * g1 * u
+            out[k][2, 0, :] = -w * g1 * v
+            out[k][3, 0, :] = w * g1
+            return out
+    raise ValueError("no wall")

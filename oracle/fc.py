@@ -133,6 +133,18 @@ def spectral_filter(Fc, alpha, p):
     return idft(sigma(k, L, alpha, p) * dft(Fc)).real
 
 
+def _real_linear(op):
+    """Apply a real linear operator to complex data part by part (complex-step derivatives)."""
+    def wrapped(F, *a):
+        if np.iscomplexobj(F):
+            return op(F.real, *a) + 1j * op(F.imag, *a)
+        return op(F, *a)
+    wrapped.__doc__ = op.__doc__
+    wrapped.__name__ = op.__name__
+    return wrapped
+
+
+@_real_linear
 def fc_derivative(F, h, d, C):
     """FC derivative along the last axis of values on x_j = j h (Sec. 2.2).
 
@@ -142,17 +154,47 @@ def fc_derivative(F, h, d, C):
     return spectral_derivative(Fc, (N + C) * h)[..., :N]
 
 
+@_real_linear
 def periodic_derivative(F, h):
     """Fourier derivative of samples of a periodic function (no continuation), period N h."""
     N = F.shape[-1]
     return spectral_derivative(F, N * h)
 
 
+@_real_linear
 def fc_filter(F, d, C, alpha, p):
     N = F.shape[-1]
     Fc = np.concatenate([F, continuation(F, d, C)], axis=-1)
     return spectral_filter(Fc, alpha, p)[..., :N]
 
 
+@_real_linear
 def periodic_filter(F, alpha, p):
     return spectral_filter(F, alpha, p)
+
+
+@_real_linear
+def fc_derivative_T(G, h, d, C):
+    """Transpose of fc_derivative as a linear map R^N -> R^N.
+
+    fc_derivative = restrict o (spectral derivative on the period) o extend, with
+    extend = [I; M], M = continuation matrix (eq. continuation). The spectral
+    derivative is a real skew-symmetric circulant, so the transpose is
+    extend^T o (-spectral derivative) o zero-padding: the continuation part is folded
+    back onto the first and last d points with (A_l Q^T)^T and (A_r Q^T)^T."""
+    N = G.shape[-1]
+    L = N + C
+    Z = np.concatenate([G, np.zeros(G.shape[:-1] + (C,))], axis=-1)
+    W = -spectral_derivative(Z, L * h)
+    Q, AL, AR = load_tables(d, C)
+    out = W[..., :N].copy()
+    ext = W[..., N:]
+    out[..., :d] += (ext @ AL) @ Q.T  # (A_l Q^T)^T w
+    out[..., N - d:] += (ext @ AR) @ Q.T  # (A_r Q^T)^T w
+    return out
+
+
+@_real_linear
+def periodic_derivative_T(G, h):
+    """Transpose of the periodic Fourier derivative: its negative (skew-symmetric circulant)."""
+    return -periodic_derivative(G, h)

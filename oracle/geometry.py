@@ -277,7 +277,7 @@ class Connectivity:
         nodes = (0.0, 1.0, 2.0)
         new = []
         for p, it in enumerate(self.items):
-            vals = np.zeros((states[p].shape[0], len(it["j"])))
+            vals = np.zeros((states[p].shape[0], len(it["j"])), dtype=states[p].dtype)
             for q in np.unique(it["donor"]):
                 if q < 0:
                     continue

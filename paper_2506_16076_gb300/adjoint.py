@@ -1,0 +1,122 @@
+"""Checkpointed discrete adjoint of the time stepper and a torch.autograd.Function.
+
+The differentiated map is a sequence of fc_rk_step calls with the viscosity and
+the time step of each step frozen at their forward values (the smoothness
+classifier is not differentiable) and no filter. The forward run stores the
+state every K steps; the backward run recomputes each segment of K states from
+its checkpoint (fc_rk_step with FROZEN_MU | FIXED_DT, replaying the recorded
+mu and dt) and applies fc_adjoint_step backwards through the segment.
+
+Orchestration only: every step and adjoint step runs in the CUDA library.
+"""
+import math
+
+import torch
+
+from . import fcsdnn
+from . import workloads as W
+
+
+class Trajectory:
+    def __init__(self, K):
+        self.K = K
+        self.checkpoints = {}
+        self.mus = []
+        self.dts = []
+
+
+def forward(ctx, e0, nsteps, K, flags=0):
+    """Run nsteps steps from e0 (not modified); returns (e_N, Trajectory)."""
+    e = e0.clone()
+    tr = Trajectory(K)
+    tr.checkpoints[0] = e0.clone()
+    for n in range(nsteps):
+        mu = torch.empty(ctx.P, dtype=torch.float64, device=e.device)
+        dt = torch.zeros(1, dtype=torch.float64, device=e.device)
+        ctx.rk_step(e, dt, mu, flags & ~fcsdnn.STEP_FILTER)
+        tr.mus.append(mu)
+        tr.dts.append(dt)
+        if (n + 1) % K == 0 and n + 1 < nsteps:
+            tr.checkpoints[n + 1] = e.clone()
+    return e, tr
+
+
+def replay(ctx, tr, e0, n0, n1):
+    """States e_{n0}..e_{n1-1} recomputed from e_{n0} with the recorded mu and dt."""
+    out = [e0.clone()]
+    e = e0.clone()
+    for n in range(n0, n1 - 1):
+        ctx.rk_step(e, tr.dts[n], tr.mus[n], fcsdnn.STEP_FROZEN_MU | fcsdnn.STEP_FIXED_DT)
+        out.append(e.clone())
+    return out
+
+
+def backward(ctx, tr, lam_N):
+    """lam_0 = (d e_N / d e_0)^T lam_N and the accumulated Dirichlet sensitivity gbc."""
+    nsteps = len(tr.dts)
+    lam = lam_N.clone()
+    nxt = torch.empty_like(lam)
+    gbc = torch.zeros_like(lam)
+    starts = sorted(tr.checkpoints)
+    for si in range(len(starts) - 1, -1, -1):
+        n0 = starts[si]
+        n1 = starts[si + 1] if si + 1 < len(starts) else nsteps
+        states = replay(ctx, tr, tr.checkpoints[n0], n0, n1)
+        for n in range(n1 - 1, n0 - 1, -1):
+            ctx.adjoint_step(states[n - n0], tr.mus[n], tr.dts[n], lam, nxt, gbc)
+            lam, nxt = nxt, lam
+    return lam, gbc
+
+
+class FCSteps(torch.autograd.Function):
+    """e_N = steps(e_0): forward through fc_rk_step, backward through fc_adjoint_step."""
+
+    @staticmethod
+    def forward(fctx, e0, ctx, nsteps, K):
+        eN, tr = forward(ctx, e0, nsteps, K)
+        fctx.ctx, fctx.tr = ctx, tr
+        return eN
+
+    @staticmethod
+    def backward(fctx, grad):
+        lam0, gbc = backward(fctx.ctx, fctx.tr, grad.contiguous())
+        fctx.gbc = gbc
+        return lam0, None, None, None
+
+
+def drag(ctx, e):
+    J = torch.zeros(1, dtype=torch.float64, device=e.device)
+    g = torch.zeros_like(e)
+    ctx.drag(e, J, g)
+    return J, g
+
+
+def freestream_state_derivs(fs, gamma=W.GAMMA):
+    """d(conserved free stream)/d(Mach, angle, rho) for (rho, M cos a, M sin a, p) with sound speed
+    sqrt(gamma p / rho); returns 4-vectors (torch) for Mach and angle at fixed rho, p."""
+    rho, u, v, p = fs
+    M = math.hypot(u, v)
+    a = math.atan2(v, u)
+    c = math.sqrt(gamma * p / rho)
+    dM = torch.tensor([0.0, rho * c * math.cos(a), rho * c * math.sin(a), rho * c * c * M], dtype=torch.float64)
+    da = torch.tensor([0.0, -rho * c * M * math.sin(a), rho * c * M * math.cos(a), 0.0], dtype=torch.float64)
+    return dM, da
+
+
+def drag_gradients(w, ctx, e0, nsteps, K):
+    """J after nsteps from the free-stream state e0 and dJ/dMach, dJ/dangle, dJ/drho_0(x).
+
+    Mach and angle enter through the initial state and the Dirichlet free-stream
+    states; rho_0 perturbs the initial density at fixed velocity and pressure."""
+    eN, tr = forward(ctx, e0, nsteps, K)
+    J, dJde = drag(ctx, eN)
+    lam0, gbc = backward(ctx, tr, dJde)
+    dM, da = freestream_state_derivs(w.freestream, w.params.gamma)
+    dev = e0.device
+    tot = (lam0 + gbc).sum(dim=1).cpu()
+    dJdM = float(tot @ dM)
+    dJda = float(tot @ da)
+    rho = e0[0]
+    u, v = e0[1] / rho, e0[2] / rho
+    dJdrho = lam0[0] + lam0[1] * u + lam0[2] * v + lam0[3] * 0.5 * (u * u + v * v)
+    return J.item(), dJdM, dJda, dJdrho, tr

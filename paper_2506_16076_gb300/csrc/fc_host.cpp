@@ -113,6 +113,21 @@ struct fc_ctx {
   unsigned long long* d_pmax = nullptr;
   int* d_flag = nullptr;
 
+  // discrete adjoint: exchange transpose as a CSR over donor points, stage states, accumulators
+  int* d_dptr = nullptr;
+  int* d_dsrc = nullptr;
+  int* d_drecv = nullptr;
+  double* d_dw = nullptr;
+  int ndon = 0;
+  double* d_U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *d_A0 = nullptr, *d_A14 = nullptr, *d_A2 = nullptr, *d_A3 = nullptr, *d_PSa = nullptr, *d_PSb = nullptr;
+  bool adj_ready = false;
+  // wall ring for the drag functional
+  int* d_wall = nullptr;
+  double* d_wallw = nullptr;
+  double* d_wallc = nullptr;
+  int nwall = 0;
+
   // kernel timing instrumentation (events around each launch group)
   bool prof = false;
   struct ProfRec {
@@ -887,6 +902,40 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     }
   }
 
+  // ---- exchange transpose: for every donor point, the receivers it feeds and the weights
+  std::vector<int> dptr{0}, dsrc, drecv;
+  std::vector<double> dw;
+  {
+    std::vector<std::pair<int, std::pair<int, double>>> ent;
+    ent.reserve(recv.size() * 9);
+    for (const Recv& r : recv)
+      for (int m2 = 0; m2 < 3; ++m2)
+        for (int m1 = 0; m1 < 3; ++m1) ent.push_back({r.src[3 * m2 + m1], {r.dst, r.w1[m1] * r.w2[m2]}});
+    std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t k = 0; k < ent.size(); ++k) {
+      if (k == 0 || ent[k].first != ent[k - 1].first) {
+        if (k) dptr.push_back((int)drecv.size());
+        dsrc.push_back(ent[k].first);
+      }
+      drecv.push_back(ent[k].second.first);
+      dw.push_back(ent[k].second.second);
+    }
+    if (!ent.empty()) dptr.push_back((int)drecv.size());
+  }
+  // ---- wall ring of the first curvilinear patch with a slip wall at q2 = 0 (drag functional)
+  std::vector<int> wall;
+  std::vector<double> wallw, wallc;
+  for (const HPatch& h : c->hp) {
+    if (h.d.kind != FC_PATCH_OGRID || h.d.side[2] != FC_SIDE_SLIPWALL) continue;
+    for (int i = 0; i < h.n1; ++i) {
+      const double dx = h.x[i] - h.d.geom[0], dy = h.y[i] - h.d.geom[1];
+      wall.push_back((int)(h.off + i));
+      wallc.push_back(dx / std::hypot(dx, dy));
+      wallw.push_back(h.d.geom[2] * 2.0 * PI / h.n1);
+    }
+    break;
+  }
+
   // ---- upload
   bool ok = true;
   make_queue(c, c->q_cart1, jc1, B.plans, npatch, ok);
@@ -906,7 +955,11 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
        c->upload(&c->d_fix, fix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
        c->upload(&c->d_bc, bcs) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
-       c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc);
+       c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
+       c->upload(&c->d_dsrc, dsrc) && c->upload(&c->d_drecv, drecv) && c->upload(&c->d_dw, dw) &&
+       c->upload(&c->d_wall, wall) && c->upload(&c->d_wallw, wallw) && c->upload(&c->d_wallc, wallc);
+  c->ndon = (int)dsrc.size();
+  c->nwall = (int)wall.size();
   c->nfix = (int)fix.size();
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
@@ -1120,6 +1173,39 @@ void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream
   project(c, e, st);
 }
 
+void projectT(fc_ctx* c, double* lam, double* gbc, cudaStream_t st) {
+  Prof pr(c, st, "bc_exchange_T");
+  launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv, c->nrecv, lam, c->P, st);
+  launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->P, st);
+  c->launches += (c->ndon > 0) + (c->nrecv > 0) + (c->nbc > 0);
+}
+
+// acc += dt L'(u)^T psi
+void adj_stage(fc_ctx* c, const double* u, const double* mu, const double* psi, double* acc, const double* dt,
+               cudaStream_t st) {
+  const DevTables& T = c->T;
+  cudaMemsetAsync(c->d_R1, 0, sizeof(double) * 4 * (size_t)c->P, st);
+  run_queue(c, c->q_gen1, false, st, "adj_gen_A",
+            [&](const Job* j, int n, int L) { launch_adj_gen_A(T, j, n, L, c->d_J, psi, c->d_G, st); });
+  run_queue(c, c->q_cart1, false, st, "adj_cart_q1",
+            [&](const Job* j, int n, int L) { launch_adj_cart(T, j, n, L, 0, u, mu, psi, c->d_R1, acc, dt, st); });
+  run_queue(c, c->q_gen2, false, st, "adj_gen_B",
+            [&](const Job* j, int n, int L) { launch_adj_gen_B(T, j, n, L, c->d_J, u, mu, psi, c->d_G, st); });
+  run_queue(c, c->q_cart2, false, st, "adj_cart_q2",
+            [&](const Job* j, int n, int L) { launch_adj_cart(T, j, n, L, 1, u, mu, psi, c->d_R1, acc, dt, st); });
+  run_queue(c, c->q_gen1, false, st, "adj_gen_C",
+            [&](const Job* j, int n, int L) { launch_adj_gen_C(T, j, n, L, c->d_G, acc, dt, st); });
+  if (c->nfix) {
+    launch_adj_fixup(c->d_fix, c->nfix, c->d_R1, acc, c->P, dt, st);
+    c->launches++;
+  }
+}
+
+void axpby(fc_ctx* c, double a, const double* x, double b, double* y, cudaStream_t st) {
+  launch_axpby(4 * c->P, a, x, b, y, st);
+  c->launches++;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1208,6 +1294,16 @@ fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, vo
   if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_check(c, "graph launch");
   c->launches += c->glaunches;
   return cuda_check(c, "fc_rk_step");
+}
+
+fc_status fc_drag(fc_ctx* c, const double* e, double* J, double* dJde, void* stream) {
+  if (!c || !e || !J) return FC_ERR_INVALID;
+  if (c->nwall == 0) return fail(c, FC_ERR_INVALID, "no curvilinear patch with a slip wall");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dJde) cudaMemsetAsync(dJde, 0, sizeof(double) * 4 * (size_t)c->P, st);
+  launch_drag(c->d_wall, c->d_wallw, c->d_wallc, c->nwall, e, c->P, c->prm.gamma, J, dJde, st);
+  c->launches++;
+  return cuda_check(c, "fc_drag");
 }
 
 fc_status fc_sync_status(fc_ctx* c, const double* e, int check_state, void* stream) {
@@ -1341,8 +1437,68 @@ fc_status fc_pass_stats(const fc_ctx* c, const char* pass, double* flops, double
   return FC_OK;
 }
 
-fc_status fc_adjoint_step(fc_ctx* c, const double*, const double*, const double*, const double*, double*, void*) {
-  return fail(c, FC_ERR_UNIMPLEMENTED, "adjoint step not built yet");
+fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const double* dt, const double* lam_np1,
+                          double* lam_n, double* gbc, void* stream) {
+  if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!c->adj_ready) {
+    const size_t n4 = 4 * (size_t)c->P;
+    bool ok = true;
+    for (int k = 0; k < 5; ++k) ok = ok && c->alloc(&c->d_U[k], n4);
+    ok = ok && c->alloc(&c->d_A0, n4) && c->alloc(&c->d_A14, n4) && c->alloc(&c->d_A2, n4) &&
+         c->alloc(&c->d_A3, n4) && c->alloc(&c->d_PSa, n4) && c->alloc(&c->d_PSb, n4);
+    if (!ok) return FC_ERR_OOM;
+    c->adj_ready = true;
+  }
+  double** U = c->d_U;
+  // forward recompute of the stage states u_0..u_4 (mu, dt frozen, no filter)
+  cudaMemcpyAsync(U[0], e_n, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
+  project(c, U[0], st);
+  StageCoef s{};
+  s.dt = dt;
+  s.U0 = U[0];
+  const double c0[4] = {0.0, A20, A30, A40}, c1[4] = {1.0, A21, A32, A43}, cb[4] = {B1, B2, B3, B4};
+  for (int i = 0; i < 4; ++i) {
+    s.Ucur = U[i];
+    s.out = U[i + 1];
+    s.c0 = c0[i];
+    s.c1 = c1[i];
+    s.cb = cb[i];
+    stage(c, s, mu, false, st);
+    project(c, U[i + 1], st);
+  }
+  // reverse sweep (Shu-Osher coefficients, see the forward stages)
+  double *A0 = c->d_A0, *A14 = c->d_A14, *A2 = c->d_A2, *A3 = c->d_A3, *PSa = c->d_PSa, *PSb = c->d_PSb;
+  axpby(c, 1.0, lam_np1, 0.0, A14, st);
+  projectT(c, A14, gbc, st);  // lam_v5
+  axpby(c, A53, A14, 0.0, A3, st);
+  axpby(c, B53, A14, 0.0, PSb, st);
+  axpby(c, A52, A14, 0.0, A2, st);
+  axpby(c, B54, A14, 0.0, PSa, st);
+  axpby(c, A54, A14, 0.0, A14, st);  // lam_u4 (without its L' term)
+  adj_stage(c, U[4], mu, PSa, A14, dt, st);
+  projectT(c, A14, gbc, st);  // lam_v4
+  axpby(c, A40, A14, 0.0, A0, st);
+  axpby(c, A43, A14, 1.0, A3, st);
+  axpby(c, B4, A14, 1.0, PSb, st);
+  adj_stage(c, U[3], mu, PSb, A3, dt, st);
+  projectT(c, A3, gbc, st);  // lam_v3
+  axpby(c, A30, A3, 1.0, A0, st);
+  axpby(c, A32, A3, 1.0, A2, st);
+  axpby(c, B3, A3, 0.0, PSa, st);
+  adj_stage(c, U[2], mu, PSa, A2, dt, st);
+  projectT(c, A2, gbc, st);  // lam_v2
+  axpby(c, A20, A2, 1.0, A0, st);
+  axpby(c, A21, A2, 0.0, A14, st);
+  axpby(c, B2, A2, 0.0, PSb, st);
+  adj_stage(c, U[1], mu, PSb, A14, dt, st);
+  projectT(c, A14, gbc, st);  // lam_v1
+  axpby(c, 1.0, A14, 1.0, A0, st);
+  axpby(c, B1, A14, 0.0, PSa, st);
+  adj_stage(c, U[0], mu, PSa, A0, dt, st);
+  projectT(c, A0, gbc, st);
+  cudaMemcpyAsync(lam_n, A0, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
+  return cuda_check(c, "fc_adjoint_step");
 }
 
 }  // extern "C"

@@ -124,9 +124,22 @@ void launch_mu_final(const DevTables& T, const double* num, const double* den, c
 void launch_dt(const DevTables& T, const double* e, const double* mu, unsigned long long* pmax, double cfl,
                double* dt, cudaStream_t st);
 void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st);
-void launch_adj_stage(const DevTables& T, const Job* jobs, int njobs, int Lmax, int pass, const double* e,
-                      const double* mu, const double* J, double* G, double* lam_out, const double* lam_in,
+void launch_adj_cart(const DevTables& T, const Job* jobs, int njobs, int Lmax, int dir, const double* u,
+                     const double* mu, const double* psi, double* R1, double* acc, const double* dt, cudaStream_t st);
+void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* psi,
+                      double* G, cudaStream_t st);
+void launch_adj_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
+                      const double* mu, const double* psi, double* G, cudaStream_t st);
+void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* G, double* acc,
+                      const double* dt, cudaStream_t st);
+void launch_adj_fixup(const int* idx, int n, const double* R1, double* acc, long long P, const double* dt,
                       cudaStream_t st);
+void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const double* dw, int nd, const Recv* r,
+                       int nr, double* lam, long long P, cudaStream_t st);
+void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, cudaStream_t st);
+void launch_drag(const int* wall, const double* w, const double* nx, int n, const double* e, long long P, double gam,
+                 double* J, double* dJde, cudaStream_t st);
+void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 size_t line_smem_bytes(int Lmax);
 int line_warps(int Lmax);
 void set_kernel_attributes();

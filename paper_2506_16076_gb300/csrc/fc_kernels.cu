@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* _
 // ---------------------------------------------------------------- curvilinear patches
 // scratch G (component stride Pg): slot 0 = D1e then R1, slot 1 = H_x, slot 2 = H_y, slot 3 = R2
 __device__ __forceinline__ double* gslot(double* G, long long Pg, int slot, int c) { return G + (4 * slot + c) * Pg; }
+__device__ __forceinline__ const double* gslot(const double* G, long long Pg, int slot, int c) {
+  return G + (4 * slot + c) * Pg;
+}
 
 // pass A: D1e = d/dq1 e
 __global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
@@ -748,6 +751,375 @@ __global__ void k_check_state(DevTables T, const double* __restrict__ e, int* fl
   if (!ok) atomicExch(flag, (int)FC_ERR_NONFINITE);
 }
 
+// ---------------------------------------------------------------- discrete adjoint (mu, dt frozen)
+// Transposed FC derivative of the two packed sequences in A (data in [0, n)):
+// D^T = extend^T o (-spectral derivative) o zero padding; extend^T folds the C
+// continuation entries back onto the first and last d points with ML^T and MR^T.
+__device__ __forceinline__ double2* deriv2T(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
+                                            int lane) {
+  const int L = P.L, n = J.n, C = J.C, d = T.d;
+  for (int idx = lane; idx < 2 * C; idx += 32) {
+    const int s = idx / C, k = idx - s * C;
+    A[s * L + n + k] = cpx(0.0, 0.0);
+  }
+  FC_SYNC();
+  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
+  double2* Y = (X == A) ? B : A;
+  mul_deriv(X, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), lane, 32);
+  FC_SYNC();
+  X = fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+  if (J.fcm >= 0) {
+    const double* ML = T.rp + J.fcm;
+    const double* MR = ML + C * d;
+    double2 acc = cpx(0.0, 0.0);
+    int dst = -1;
+    if (lane < 4 * d) {  // 2 sequences x (d left + d right) end points
+      const int s = lane / (2 * d), q = lane - s * 2 * d;
+      const bool left = q < d;
+      const int j = left ? q : q - d;
+      const double* M = left ? ML : MR;
+      const double2* ext = X + s * L + n;
+      for (int k = 0; k < C; ++k) {
+        const double m = M[k * d + j];
+        acc.x = fma(m, ext[k].x, acc.x);
+        acc.y = fma(m, ext[k].y, acc.y);
+      }
+      dst = s * L + (left ? j : n - d + j);
+    }
+    FC_SYNC();
+    if (dst >= 0) X[dst] = cadd(X[dst], acc);
+    FC_SYNC();
+  }
+  return X;
+}
+
+// A^T eta for the x (dir 0) or y (dir 1) flux Jacobian at state e (eq. euler 2d equation)
+__device__ __forceinline__ void fluxT(int dir, double r, double mx, double my, double E, double gam, const double* eta,
+                                      double* out) {
+  const double ir = 1.0 / r;
+  const double u = mx * ir, v = my * ir;
+  const double g1 = gam - 1.0;
+  const double q2 = u * u + v * v;
+  const double p = g1 * (E - 0.5 * r * q2);
+  const double H = (E + p) * ir;
+  const double pr = 0.5 * g1 * q2, pm = -g1 * u, pn = -g1 * v, pE = g1;
+  if (dir == 0) {
+    // rows c = 0..3 of A_x, columns j: out_j = sum_c A[c][j] eta_c
+    out[0] = (-u * u + pr) * eta[1] + (-u * v) * eta[2] + (-u * H + u * pr) * eta[3];
+    out[1] = eta[0] + (2.0 * u + pm) * eta[1] + v * eta[2] + (H + u * pm) * eta[3];
+    out[2] = pn * eta[1] + u * eta[2] + u * pn * eta[3];
+    out[3] = pE * eta[1] + u * (1.0 + pE) * eta[3];
+  } else {
+    out[0] = (-u * v) * eta[1] + (-v * v + pr) * eta[2] + (-v * H + v * pr) * eta[3];
+    out[1] = v * eta[1] + pm * eta[2] + v * pm * eta[3];
+    out[2] = eta[0] + u * eta[1] + (2.0 * v + pn) * eta[2] + (H + v * pn) * eta[3];
+    out[3] = pE * eta[2] + v * (1.0 + pE) * eta[3];
+  }
+}
+
+__device__ __forceinline__ void load4_masked(double2* A, int L, const Job& J, const DevTables& T,
+                                             const double* __restrict__ src, int lane) {
+  const long long cs = T.P;
+  for (int t = lane; t < J.n; t += 32) {
+    const long long p = J.base + (long long)t * J.stride;
+    if (T.info[p] & PT_NODIFF) {
+      A[t] = cpx(0.0, 0.0);
+      A[L + t] = cpx(0.0, 0.0);
+    } else {
+      A[t] = cpx(src[p], src[p + cs]);
+      A[L + t] = cpx(src[p + 2 * cs], src[p + 3 * cs]);
+    }
+  }
+}
+
+// affine patches, pass 1 (q1 lines): R1 = A_x^T eta_x - D_x^T(mu eta_x), eta_x = -D_x^T (N psi)
+// pass 2 (q2 lines): acc += dt (R1 + A_y^T eta_y - D_y^T(mu eta_y))
+__global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                         int Lmax, int dir, const double* __restrict__ u,
+                                                         const double* __restrict__ mu, const double* __restrict__ psi,
+                                                         double* __restrict__ R1, double* __restrict__ acc,
+                                                         const double* __restrict__ dtp) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4_masked(A, L, J, T, psi, lane);
+    double2* X = deriv2T(A, B, J, P, T, lane);
+    double2* Y = (X == A) ? B : A;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double eta[4] = {-X[t].x, -X[t].y, -X[L + t].x, -X[L + t].y};
+      double r[4];
+      fluxT(dir, u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs], T.gamma, eta, r);
+      const double m = mu[p];
+      if (dir == 0) {
+        R1[p] = r[0];
+        R1[p + cs] = r[1];
+        R1[p + 2 * cs] = r[2];
+        R1[p + 3 * cs] = r[3];
+      } else {
+        // R1 + A_y^T eta_y so far, kept in the stage buffer until the last transform
+        R1[p] += r[0];
+        R1[p + cs] += r[1];
+        R1[p + 2 * cs] += r[2];
+        R1[p + 3 * cs] += r[3];
+      }
+      Y[t] = cpx(m * eta[0], m * eta[1]);
+      Y[L + t] = cpx(m * eta[2], m * eta[3]);
+    }
+    double2* Z = deriv2T(Y, X, J, P, T, lane);
+    const double dt = dir ? *dtp : 0.0;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double z[4] = {Z[t].x, Z[t].y, Z[L + t].x, Z[L + t].y};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double v = R1[p + c * cs] - z[c];
+        if (dir == 0)
+          R1[p + c * cs] = v;
+        else
+          acc[p + c * cs] = fma(dt, v, acc[p + c * cs]);
+      }
+    }
+    FC_SYNC();
+  }
+}
+
+// curvilinear patches. scratch G slots: 0 = S1x then eta_x, 1 = S1y, 2 = partial, 3 = g1
+// pass A (q1): S1x = D_1^T(J1x N psi), S1y = D_1^T(J1y N psi)
+__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                          int Lmax, const double* __restrict__ Jm,
+                                                          const double* __restrict__ psi, double* __restrict__ G) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P, Pg = T.Pg;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int which = 0; which < 2; ++which) {
+      for (int t = lane; t < J.n; t += 32) {
+        const long long p = J.base + (long long)t * J.stride;
+        const long long g = J.gbase + (long long)t * J.stride;
+        const double w = (T.info[p] & PT_NODIFF) ? 0.0 : Jm[g + which * Pg];
+        A[t] = cpx(w * psi[p], w * psi[p + cs]);
+        A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
+      }
+      double2* X = deriv2T(A, B, J, P, T, lane);
+      for (int t = lane; t < J.n; t += 32) {
+        const long long g = J.gbase + (long long)t * J.stride;
+        gslot(G, Pg, which, 0)[g] = X[t].x;
+        gslot(G, Pg, which, 1)[g] = X[t].y;
+        gslot(G, Pg, which, 2)[g] = X[L + t].x;
+        gslot(G, Pg, which, 3)[g] = X[L + t].y;
+      }
+      FC_SYNC();
+    }
+  }
+}
+
+// pass B (q2): eta_x = -(S1x + D_2^T(J2x N psi)), eta_y = -(S1y + D_2^T(J2y N psi));
+// partial = A_x^T eta_x + A_y^T eta_y - D_2^T(mu (J2x eta_x + J2y eta_y)); g1 = mu (J1x eta_x + J1y eta_y)
+__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                          int Lmax, const double* __restrict__ Jm,
+                                                          const double* __restrict__ u, const double* __restrict__ mu,
+                                                          const double* __restrict__ psi, double* __restrict__ G) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P, Pg = T.Pg;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int which = 0; which < 2; ++which) {
+      for (int t = lane; t < J.n; t += 32) {
+        const long long p = J.base + (long long)t * J.stride;
+        const long long g = J.gbase + (long long)t * J.stride;
+        const double w = (T.info[p] & PT_NODIFF) ? 0.0 : Jm[g + (2 + which) * Pg];
+        A[t] = cpx(w * psi[p], w * psi[p + cs]);
+        A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
+      }
+      double2* X = deriv2T(A, B, J, P, T, lane);
+      for (int t = lane; t < J.n; t += 32) {
+        const long long g = J.gbase + (long long)t * J.stride;
+        const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double* s = gslot(G, Pg, which, c);
+          s[g] = -(s[g] + x[c]);  // eta_x (which 0) or eta_y (which 1)
+        }
+      }
+      FC_SYNC();
+    }
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      double ex[4], ey[4], ax[4], ay[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        ex[c] = gslot(G, Pg, 0, c)[g];
+        ey[c] = gslot(G, Pg, 1, c)[g];
+      }
+      fluxT(0, u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs], T.gamma, ex, ax);
+      fluxT(1, u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs], T.gamma, ey, ay);
+      const double m = mu[p];
+      const double j1x = Jm[g], j1y = Jm[g + Pg], j2x = Jm[g + 2 * Pg], j2y = Jm[g + 3 * Pg];
+      double g2[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        gslot(G, Pg, 2, c)[g] = ax[c] + ay[c];
+        gslot(G, Pg, 3, c)[g] = m * fma(j1x, ex[c], j1y * ey[c]);
+        g2[c] = m * fma(j2x, ex[c], j2y * ey[c]);
+      }
+      A[t] = cpx(g2[0], g2[1]);
+      A[L + t] = cpx(g2[2], g2[3]);
+    }
+    double2* Z = deriv2T(A, B, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double z[4] = {Z[t].x, Z[t].y, Z[L + t].x, Z[L + t].y};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) gslot(G, Pg, 2, c)[g] -= z[c];
+    }
+    FC_SYNC();
+  }
+}
+
+// pass C (q1): acc += dt (partial - D_1^T(g1))
+__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                          int Lmax, const double* __restrict__ G,
+                                                          double* __restrict__ acc, const double* __restrict__ dtp) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * 4 * Lmax;
+  double2* B = A + 2 * Lmax;
+  const long long cs = T.P, Pg = T.Pg;
+  const double dt = *dtp;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      A[t] = cpx(gslot(G, Pg, 3, 0)[g], gslot(G, Pg, 3, 1)[g]);
+      A[L + t] = cpx(gslot(G, Pg, 3, 2)[g], gslot(G, Pg, 3, 3)[g]);
+    }
+    double2* X = deriv2T(A, B, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[p + c * cs] = fma(dt, gslot(G, Pg, 2, c)[g] - x[c], acc[p + c * cs]);
+    }
+    FC_SYNC();
+  }
+}
+
+// points no column pass finishes: acc += dt R1 (R1 is zero where no row pass wrote it)
+__global__ void k_adj_fixup(const int* __restrict__ idx, int n, const double* __restrict__ R1, double* __restrict__ acc,
+                            long long P, const double* __restrict__ dtp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double dt = *dtp;
+  const long long p = idx[i];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[p + c * P] = fma(dt, R1[p + c * P], acc[p + c * P]);
+}
+
+// exchange transpose: every donor gathers w * adjoint of the receivers it feeds (CSR by donor),
+// then the receivers are zeroed (they do not depend on their own previous value)
+__global__ void k_exchange_T(const int* __restrict__ dptr, const int* __restrict__ dsrc, const int* __restrict__ drecv,
+                             const double* __restrict__ dw, int nd, double* __restrict__ lam, long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const long long s = dsrc[i];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double a = lam[s + c * P];
+    for (int k = dptr[i]; k < dptr[i + 1]; ++k) a = fma(dw[k], lam[drecv[k] + c * P], a);
+    lam[s + c * P] = a;
+  }
+}
+__global__ void k_zero_points(const Recv* __restrict__ r, int n, double* __restrict__ lam, long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = r[i].dst;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) lam[p + c * P] = 0.0;
+}
+// boundary transpose: Dirichlet points hand their adjoint to gbc and are zeroed; slip walls
+// zero (affine) or project out (curvilinear) the wall-normal momentum adjoint
+__global__ void k_bc_T(const BcPt* __restrict__ bc, int n, double* __restrict__ lam, double* __restrict__ gbc,
+                       long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BcPt b = bc[i];
+  const long long p = b.idx;
+  if (b.mode & 8) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (gbc) gbc[p + c * P] += lam[p + c * P];
+      lam[p + c * P] = 0.0;
+    }
+    return;
+  }
+  if (b.mode & 1) lam[p + P] = 0.0;
+  if (b.mode & 2) lam[p + 2 * P] = 0.0;
+  if (b.mode & 4) {
+    const double mx = lam[p + P], my = lam[p + 2 * P];
+    const double mn = mx * b.nx + my * b.ny;
+    lam[p + P] = mx - mn * b.nx;
+    lam[p + 2 * P] = my - mn * b.ny;
+  }
+}
+// y = a x + b y over n doubles (b == 0: y = a x)
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
+// ---------------------------------------------------------------- wall drag functional
+// J = sum_i w_i n_x,i p_i over the wall ring (periodic trapezoid of the wall-pressure integral);
+// dJde (optional): its gradient at the wall points, zero elsewhere (caller zeroes it)
+__global__ void k_drag(const int* __restrict__ wall, const double* __restrict__ w, const double* __restrict__ nx, int n,
+                       const double* __restrict__ e, long long P, double gam, double* J, double* dJde) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long p = wall[i];
+    const double r = e[p], mx = e[p + P], my = e[p + 2 * P], E = e[p + 3 * P];
+    const double u = mx / r, v = my / r;
+    const double g1 = gam - 1.0;
+    const double pr = g1 * (E - 0.5 * r * (u * u + v * v));
+    const double wn = w[i] * nx[i];
+    acc += wn * pr;
+    if (dJde) {
+      dJde[p] = wn * 0.5 * g1 * (u * u + v * v);
+      dJde[p + P] = -wn * g1 * u;
+      dJde[p + 2 * P] = -wn * g1 * v;
+      dJde[p + 3 * P] = wn * g1;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *J = red[0];
+}
+
 // ---------------------------------------------------------------- launch wrappers
 static inline int grid_lines(int njobs, int Lmax) {
   const int w = line_warps(Lmax);
@@ -838,6 +1210,50 @@ void launch_dt(const DevTables& T, const double* e, const double* mu, unsigned l
   k_dt_reduce<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, mu, pmax);
   k_dt_final<<<1, 256, 0, st>>>(T, pmax, cfl, dt);
 }
+
+void launch_adj_cart(const DevTables& T, const Job* jobs, int njobs, int Lmax, int dir, const double* u,
+                     const double* mu, const double* psi, double* R1, double* acc, const double* dt, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_adj_cart<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, dir, u, mu, psi, R1, acc, dt);
+}
+void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* psi,
+                      double* G, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_adj_gen_A<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, psi, G);
+}
+void launch_adj_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
+                      const double* mu, const double* psi, double* G, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_adj_gen_B<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, u, mu, psi, G);
+}
+void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* G, double* acc,
+                      const double* dt, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_adj_gen_C<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, G, acc, dt);
+}
+void launch_adj_fixup(const int* idx, int n, const double* R1, double* acc, long long P, const double* dt,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  k_adj_fixup<<<grid_pts(n, 256), 256, 0, st>>>(idx, n, R1, acc, P, dt);
+}
+void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const double* dw, int nd, const Recv* r,
+                       int nr, double* lam, long long P, cudaStream_t st) {
+  if (nd > 0) k_exchange_T<<<grid_pts(nd, 256), 256, 0, st>>>(dptr, dsrc, drecv, dw, nd, lam, P);
+  if (nr > 0) k_zero_points<<<grid_pts(nr, 256), 256, 0, st>>>(r, nr, lam, P);
+}
+void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, cudaStream_t st) {
+  if (n <= 0) return;
+  k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, P);
+}
+void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  k_axpby<<<grid_pts(n, 256), 256, 0, st>>>(n, a, x, b, y);
+}
+
+void launch_drag(const int* wall, const double* w, const double* nx, int n, const double* e, long long P, double gam,
+                 double* J, double* dJde, cudaStream_t st) {
+  k_drag<<<1, 256, 0, st>>>(wall, w, nx, n, e, P, gam, J, dJde);
+}
+
 void set_kernel_attributes() {
   const int cap = (int)SMEM_CAP;
   cudaFuncSetAttribute(k_cart_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -847,6 +1263,10 @@ void set_kernel_attributes() {
   cudaFuncSetAttribute(k_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filter_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filter_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_adj_cart, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_adj_gen_A, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_adj_gen_B, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_adj_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st) {
   k_check_state<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, flag);

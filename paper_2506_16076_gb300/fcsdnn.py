@@ -24,7 +24,7 @@ STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4
 
 # every symbol include/fcsdnn.h declares
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
-           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_sync_status",
+           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_drag", "fc_sync_status",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
            "fc_pass_stats", "fc_last_error", "fc_destroy"]
 
@@ -73,7 +73,8 @@ def load():
         "fc_project": (C.c_int, [vp, vp, vp]),
         "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
-        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
+        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "fc_drag": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_sync_status": (C.c_int, [vp, vp, ip, vp]),
         "fc_launch_count": (C.c_uint64, [vp]),
         "fc_profile_enable": (C.c_int, [vp, ip]),
@@ -215,9 +216,12 @@ class Context:
     def rk_step(self, e, dt, mu, flags=0):
         self._check(self.lib.fc_rk_step(self.ctx, _ptr(e), _ptr(dt), _ptr(mu), int(flags), _stream()))
 
-    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n):
+    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None):
         self._check(self.lib.fc_adjoint_step(self.ctx, _ptr(e_n), _ptr(mu), _ptr(dt), _ptr(lam_np1), _ptr(lam_n),
-                                             _stream()))
+                                             _ptr(gbc), _stream()))
+
+    def drag(self, e, J, dJde=None):
+        self._check(self.lib.fc_drag(self.ctx, _ptr(e), _ptr(J), _ptr(dJde), _stream()))
 
     def sync_status(self, e=None, check_state=True):
         return self.lib.fc_sync_status(self.ctx, _ptr(e), 1 if (check_state and e is not None) else 0, _stream())

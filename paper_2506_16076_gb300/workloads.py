@@ -96,7 +96,7 @@ def _cart_array(nx, ny, x0, x1, y0, y1, nper, overlap, fs, hole, sizes=None):
 
     Uniform case (sizes None): every patch has nper points per side on one global
     grid; neighbours share `overlap` grid lines. Seeded case: sizes[i][j] = (n1, n2)
-    and neighbouring patches overlap by `overlap` points of the finer neighbour.
+    and neighbouring patches overlap by `overlap` points of the coarser neighbour.
     Outer sides: left/bottom/top Dirichlet free stream, right outflow.
     """
     patches = []
@@ -116,9 +116,10 @@ def _cart_array(nx, ny, x0, x1, y0, y1, nper, overlap, fs, hole, sizes=None):
             else:
                 n1, n2 = sizes[j][i]
                 wx, wy = (x1 - x0) / nx, (y1 - y0) / ny
-                # overlap half-width on each internal side, in the finer neighbour's spacing
+                # overlap half-width on each internal side: `overlap` points of the coarser
+                # neighbour, so both patches keep an (overlap)-point layer inside the other
                 def half(nself, nnb, w):
-                    return 0.5 * overlap * w / (max(nself, nnb) - 1)
+                    return 0.5 * overlap * w / (min(nself, nnb) - 1)
                 lx = half(n1, sizes[j][i - 1][0], wx) if i > 0 else 0.0
                 rx = half(n1, sizes[j][i + 1][0], wx) if i < nx - 1 else 0.0
                 ly = half(n2, sizes[j - 1][i][1], wy) if j > 0 else 0.0

@@ -21,14 +21,19 @@ def from_dev(t, w, ncomp=4):
     return [o[0] for o in out] if ncomp == 1 else out
 
 
-def rel_err(gpu, orc, mask=None):
-    """Per component max|gpu - orc| / max|orc| (over all patches), as a list of 4."""
+def rel_err(gpu, orc, mask=None, floor=1e-2):
+    """Per component max|gpu - orc| / max(max|orc_c|, floor * max_c' max|orc_c'|), as a list.
+
+    The floor keeps a component that is identically ~0 (e.g. the transverse momentum of
+    a planar shock tube) from turning rounding noise into an O(1) "relative" error."""
+    ncomp = gpu[0].shape[0]
+    scale = [max(np.abs(o[c]).max() for o in orc) for c in range(ncomp)]
+    top = max(scale)
     errs = []
-    for c in range(gpu[0].shape[0]):
+    for c in range(ncomp):
         num = max(np.abs(np.where(m, g[c] - o[c], 0.0) if m is not None else g[c] - o[c]).max()
                   for g, o, m in zip(gpu, orc, mask or [None] * len(gpu)))
-        den = max(np.abs(o[c]).max() for o in orc)
-        errs.append(num / max(den, 1e-300))
+        errs.append(num / max(scale[c], floor * top, 1e-300))
     return errs
 
 

@@ -2,7 +2,9 @@
 
 Tolerances (the operator's own targets): 1e-11 relative per RHS evaluation and
 per linear pass, 1e-8 relative after 100 steps, identical smoothness classes
-except at stated ties (oracle top-two FP32 logit margin below 1e-3).
+except at stated ties (oracle top-two FP32 logit margin below 1e-3). Relative
+errors are per component, against max(max|oracle component|, 1e-2 x the largest
+component scale) (see tests/gpu_helpers.rel_err).
 """
 import dataclasses
 
@@ -34,7 +36,7 @@ def case(request, gpu_lib):
 
 def test_rhs_parity_given_mu(case):
     w, ctx, sv = case
-    st = W.random_smooth_state(w, seed=11)
+    st = W.random_smooth_state(w, seed=11, amp=0.2)
     mu = smooth_mu(w, seed=3, scale=0.01)
     ref = sv.rhs(st, mu)
     e = to_dev(st)

@@ -1,0 +1,98 @@
+"""Pins of the oracle's discrete adjoint: dot-product identities against complex-step
+directional derivatives of the forward map, and a central-difference check of a
+functional gradient on a tiny grid."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as A, fc, solver as S
+from paper_2506_16076_gb300 import workloads as W
+
+
+def dot(a, b):
+    return sum(float(np.vdot(x, y).real) for x, y in zip(a, b))
+
+
+def rand_like(states, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.normal(size=a.shape) for a in states]
+
+
+@pytest.mark.parametrize("N,C", [(10, 27), (37, 29), (64, 27)])
+def test_fc_derivative_transpose(N, C):
+    rng = np.random.default_rng(N)
+    x, y = rng.normal(size=(3, N)), rng.normal(size=(3, N))
+    h = 1.0 / (N - 1)
+    lhs = np.sum(fc.fc_derivative(x, h, 5, C) * y)
+    rhs = np.sum(x * fc.fc_derivative_T(y, h, 5, C))
+    assert abs(lhs - rhs) < 1e-11 * np.abs(fc.fc_derivative(x, h, 5, C)).max() * np.abs(y).sum()
+    xp = rng.normal(size=(2, 48))
+    yp = rng.normal(size=(2, 48))
+    assert abs(np.sum(fc.periodic_derivative(xp, 1 / 48) * yp) - np.sum(xp * fc.periodic_derivative_T(yp, 1 / 48))) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = W.small_multipatch()
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=2, amp=0.05))
+    mu = [0.002 * (1 + np.cos(g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    return w, sv, st, mu
+
+
+def test_rhs_adjoint_dot_product(small):
+    w, sv, st, mu = small
+    v = rand_like(st, 1)
+    lam = rand_like(st, 2)
+    jv = A.rhs_jvp_complex(sv, st, mu, v)
+    jtl = A.rhs_adjoint(sv, st, mu, lam)
+    lhs, rhs = dot(jv, lam), dot(v, jtl)
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0) * 1e2, (lhs, rhs)
+
+
+def test_project_adjoint_dot_product(small):
+    w, sv, st, mu = small
+    v = rand_like(st, 3)
+    lam = rand_like(st, 4)
+    jv = A.project_jvp_complex(sv, st, v)
+    lhs, rhs = dot(jv, lam), dot(v, A.project_T(sv, lam))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+def test_step_adjoint_dot_product(small):
+    w, sv, st, mu = small
+    dt = 0.5 * sv.dt(st, mu)
+    v = rand_like(st, 5)
+    lam = rand_like(st, 6)
+    jv = A.step_jvp_complex(sv, st, mu, dt, v)
+    lam_n, _ = A.step_adjoint(sv, st, mu, dt, lam)
+    lhs, rhs = dot(jv, lam), dot(v, lam_n)
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+
+
+def test_drag_gradient_central_differences():
+    # tiny cylinder grid, frozen mu and dt: dJ/de_0 . v against central differences (step 1e-6)
+    w = W.small_multipatch()
+    sv = S.Solver(w)
+    st0 = sv.project(W.random_smooth_state(w, seed=7, amp=0.02))
+    mu = [np.zeros((p.n2, p.n1)) for p in w.patches]
+    dt = 0.5 * sv.dt(st0, mu)
+    nsteps = 2
+
+    def J_of(st):
+        for _ in range(nsteps):
+            st = A.step_forward(sv, st, mu, dt)[5]
+        return A.wall_drag(sv, st)
+
+    traj = [st0]
+    for _ in range(nsteps):
+        traj.append(A.step_forward(sv, traj[-1], mu, dt)[5])
+    lam = A.wall_drag_grad(sv, traj[-1])
+    for n in range(nsteps - 1, -1, -1):
+        lam, _ = A.step_adjoint(sv, traj[n], mu, dt, lam)
+    v = rand_like(st0, 8)
+    h = 1e-6
+    fd = (J_of([a + h * b for a, b in zip(st0, v)]) - J_of([a - h * b for a, b in zip(st0, v)])) / (2 * h)
+    ad = dot(lam, v)
+    assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-3), (fd, ad)
