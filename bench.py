@@ -39,23 +39,21 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample-patches", type=int, default=3)
+    ap.add_argument("--sample-patches", type=int, default=1)
+    ap.add_argument("--no-per-patch", action="store_true")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- CPU oracle on a bounded sample
 def oracle_sample_workload(w, npatch):
-    """The affine patches nearest the cylinder plus the O-grid: a bounded sample of the workload."""
+    """A bounded sample of the workload: its npatch largest affine patches, each run as a
+    stand-alone patch (sides made Dirichlet free stream, no hole), so the sample has the
+    workload's line lengths and per-point work without inter-patch coupling."""
+    import dataclasses
     from paper_2506_16076_gb300 import workloads as W
-    import math
     aff = [p for p in w.patches if p.kind == W.AFFINE]
-    og = [p for p in w.patches if p.kind == W.OGRID]
-
-    def dist(p):
-        x0, x1, y0, y1 = p.geom
-        return math.hypot(0.5 * (x0 + x1), 0.5 * (y0 + y1))
-    aff.sort(key=dist)
-    pts = og[:1] + aff[:npatch] if npatch > 0 else og[:1]
+    aff.sort(key=lambda p: -p.npts)
+    pts = [dataclasses.replace(p, side=(W.DIRICHLET,) * 4, hole=(0.0, 0.0, -1.0)) for p in aff[:npatch]]
     return W.Workload(w.name + "_sample", pts, w.params, w.freestream, w.init, w.steps, w.extra)
 
 
@@ -78,7 +76,7 @@ def oracle_bench(workload, steps, warmup, npatch, budget_s=None):
         if budget_s and time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    desc = (f"{len(ws.patches)} of {len(w.patches)} patches of {workload} (O-grid + nearest affine patches), "
+    desc = (f"{len(ws.patches)} largest of the {len(w.patches)} patches of {workload} (stand-alone), "
             f"{active} active points, {done} full steps, direct-DFT oracle")
     return active * 5 * done / el, desc, el, done
 
@@ -149,6 +147,19 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- ranks
+def combine_ranks(world, pu_step, steps, ms, ms_e2e, device):
+    """Whole-job rates of independent replicas: times are the maximum over ranks, work is the
+    sum over ranks (weak scaling). Returns (ms, ms_e2e, value, e2e)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, ms_e2e = t[0].item(), t[1].item()
+    return ms, ms_e2e, world * pu_step * steps / (ms / 1e3), world * pu_step / (ms_e2e / 1e3)
 
 
 # ---------------------------------------------------------------- our arm
@@ -224,22 +235,44 @@ def main_ours(args):
         n0 += args.steps
         status = ctx.sync_status(e)
 
-        # per-patch schedule on the same GPU (baseline of the batched launch), same step count
-        k_pp = max(1, min(args.steps, 3))
-        ev0.record(stream)
-        steps(k_pp, PERPATCH, n0)
-        ev1.record(stream)
-        stream.synchronize()
-        ms_pp = ev0.elapsed_time(ev1) / k_pp
-        n0 += k_pp
+        # per-patch schedule on the same GPU (baseline of the batched launch)
+        ms_pp = None
+        if not args.no_per_patch:
+            k_pp = max(1, min(args.steps, 3))
+            ev0.record(stream)
+            steps(k_pp, PERPATCH, n0)
+            ev1.record(stream)
+            stream.synchronize()
+            ms_pp = ev0.elapsed_time(ev1) / k_pp
+            n0 += k_pp
 
         # per-kernel durations, live, with CUDA events on the launching stream
         ctx.profile_reset()
+        ctx.line_stats(reset=True)
         ctx.profile(True)
         steps(2, 0, n0)
         ctx.profile(False)
         prof = ctx.profile_read()
+        skip = ctx.line_stats(reset=True)
         n0 += 2
+
+        # adjoint / forward cost: nadj steps recorded (mu, dt frozen for the adjoint, checkpoints
+        # every 2 steps), then the checkpointed reverse sweep (segment replays + adjoint steps)
+        from paper_2506_16076_gb300 import adjoint as ADJ
+        nadj = max(2, min(args.steps, 4))
+        e_adj = e.clone()
+        ev0.record(stream)
+        eN, tr = ADJ.forward(ctx, e_adj, nadj, 2)
+        ev1.record(stream)
+        stream.synchronize()
+        ms_fwd = ev0.elapsed_time(ev1)
+        lam = torch.ones_like(eN)
+        ev0.record(stream)
+        lam0, _ = ADJ.backward(ctx, tr, lam)
+        ev1.record(stream)
+        stream.synchronize()
+        ms_adj = ev0.elapsed_time(ev1)
+        del tr, lam, lam0, eN, e_adj
 
         # end to end through the public API with host buffers: H2D of the state, step, D2H of the result
         host = e.cpu().pin_memory()
@@ -254,13 +287,8 @@ def main_ours(args):
         stream.synchronize()
         ms_e2e = ev0.elapsed_time(ev1) / k_e2e
 
-    t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, ms_e2e = t[0].item(), t[1].item()
     pu_step = 5 * ctx.active
-    value = world * pu_step * args.steps / (ms / 1e3)
-    e2e = world * pu_step / (ms_e2e / 1e3)
+    ms, ms_e2e, value, e2e = combine_ranks(world, pu_step, args.steps, ms, ms_e2e, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -274,6 +302,12 @@ def main_ours(args):
     if dom:
         flops, nbytes, nl, npts = ctx.pass_stats(dom)
         tot_ms, cnt = prof[dom]
+        passes_prof = 2 * (5 if dom.startswith("cart") else 1)
+        # gradient rounds skipped on lines with mu == 0 everywhere are not counted as work done
+        skipped = {"cart_q1": skip[2], "cart_q2": skip[3]}.get(dom, 0.0) / passes_prof
+        skipped_lines = {"cart_q1": skip[0], "cart_q2": skip[1]}.get(dom, 0) / passes_prof
+        flops_full = flops
+        flops = flops - skipped
         avg_s = tot_ms / 1e3 / max(cnt, 1)
         per_launch_flops = flops / max(cnt // 2 if dom.startswith("cart") else cnt // 2, 1)
         # one pass launch group covers all its length classes; flops above are per full pass
@@ -285,6 +319,8 @@ def main_ours(args):
         ach = flops / avg_pass_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fp64_peak, 4), "traffic": None, "kernel": f"k_{dom}",
+                "lines_per_pass": nl, "inviscid_lines_per_pass": skipped_lines,
+                "flops_per_pass_executed": flops, "flops_per_pass_all_rounds": flops_full,
                 "pass_ms": round(avg_pass_s * 1e3, 3), "launches_per_pass": groups // passes,
                 "hbm_GBps": round(nbytes / avg_pass_s / 1e9, 1),
                 "hbm_frac_of_measured": round(nbytes / avg_pass_s / 1e9 / pk.get("hbm_gbs", 6787.9), 4),
@@ -298,9 +334,13 @@ def main_ours(args):
                    "patches": len(w.patches), "schedule": "batched, one launch per pass and length class, CUDA graph",
                    "l2": "inputs larger than L2 (state %.2f GB)" % (32 * ctx.P / 1e9),
                    "parallelism": "replicas" if world > 1 else "1 GPU", "init_s": round(init_s, 2)},
-        "per_patch": {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
-                      "batched_speedup": ms_pp / (ms / args.steps)},
+        "per_patch": None if ms_pp is None else {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
+                                                 "batched_speedup": ms_pp / (ms / args.steps)},
         "kernels_ms_per_step": {k: round(v[0] / 2, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
+        "adjoint": {"steps": nadj, "checkpoint_every": 2, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
+                    "adjoint_forward_ratio": ms_adj / ms_fwd,
+                    "note": "forward = steps with mu/dt recorded and checkpoints (no filter); adjoint = segment "
+                            "replays + fc_adjoint_step per step"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P, "d2h_bytes_per_step": 32 * ctx.P},

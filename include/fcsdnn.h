@@ -171,6 +171,13 @@ int fc_profile_read(fc_ctx *ctx);
 fc_status fc_profile_get(const fc_ctx *ctx, int k, const char **name, double *ms, int *launches);
 fc_status fc_profile_reset(fc_ctx *ctx);
 
+/* Affine-patch line passes skip the gradient round of a line on which mu is zero at every
+ * point (the viscous flux vanishes and H = f(e) exactly). Counts of skipped lines and of
+ * the algorithmic flops of the skipped rounds since the last reset, per direction
+ * (synchronises the device). */
+fc_status fc_line_stats(fc_ctx *ctx, long long *lines_q1, long long *lines_q2, double *flops_q1, double *flops_q2,
+                        int reset);
+
 /* Algorithmic work of one launch of a line pass ("cart_q1", "cart_q2", "filter_q1",
  * "filter_q2"): FP64 flops by the conventional FFT count (5 L log2 L per complex
  * transform) plus continuation, multiplier and pointwise work; compulsory HBM

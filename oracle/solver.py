@@ -169,6 +169,8 @@ class Solver:
         best = np.inf
         for g, e, m in zip(self.geos, states, mus):
             v = ~g.blank
+            if not v.any():
+                continue
             S = euler.mwsb(e, self.prm.gamma)[v].max()
             M = m[v].max()
             best = min(best, self.prm.cfl / (S / g.htil + M / g.htil ** 2))

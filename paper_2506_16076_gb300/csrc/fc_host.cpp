@@ -73,6 +73,7 @@ struct fc_ctx {
   Plan* d_plans = nullptr;
   double2* d_tw = nullptr;
   double* d_rp = nullptr;
+  int* d_ip = nullptr;
   uint32_t* d_info = nullptr;
   PatchDev* d_patches = nullptr;
   double* d_J = nullptr;
@@ -111,6 +112,8 @@ struct fc_ctx {
   double *d_phi = nullptr, *d_S = nullptr, *d_muhat = nullptr, *d_num = nullptr, *d_tmp = nullptr, *d_mu = nullptr;
   double* d_dt = nullptr;
   unsigned long long* d_pmax = nullptr;
+  unsigned long long* d_skip_lines = nullptr;
+  double* d_skip_flops = nullptr;
   int* d_flag = nullptr;
 
   // discrete adjoint: exchange transpose as a CSR over donor points, stage states, accumulators
@@ -418,6 +421,7 @@ struct Builder {
   std::vector<Plan> plans;
   std::vector<double2> tw;
   std::vector<double> rp;
+  std::vector<int> ip;
   std::map<int, int> fcm_of_C;
 
   int plan(int L) {
@@ -435,6 +439,20 @@ struct Builder {
       w.x = (double)cosl(ang);
       w.y = (double)sinl(ang);
       tw.push_back(w);
+    }
+    // slot -> mode table of the in-place transforms: slot p = sum_s d_s L/(R_0..R_s)
+    // holds mode k = sum_s d_s R_0..R_{s-1}
+    p.rev = (int)ip.size();
+    for (int slot = 0; slot < L; ++slot) {
+      int rem = slot, k = 0, w = 1, span = L;
+      for (int st = 0; st < p.nst; ++st) {
+        span /= p.rad[st];
+        const int dgt = rem / span;
+        rem -= dgt * span;
+        k += dgt * w;
+        w *= p.rad[st];
+      }
+      ip.push_back(k);
     }
     p.sig = (int)rp.size();
     const fc_params& prm = c->prm;
@@ -950,7 +968,11 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     pdev[p] = PatchDev{h.off, h.gbase, h.n1, h.n2, h.d.kind, h.periodic1 ? 1 : 0, h.hhat, h.htil};
   }
   const std::vector<double> Rv(prm->R, prm->R + 4);
+  for (const Plan& pl : B.plans)
+    for (int st = 0; st < pl.nst; ++st)
+      if (pl.rad[st] > MAX_GENERIC_RADIX) return bad("a continued line length has a prime factor above 128");
   ok = ok && c->upload(&c->d_plans, B.plans) && c->upload(&c->d_tw, B.tw) && c->upload(&c->d_rp, B.rp) &&
+       c->upload(&c->d_ip, B.ip) &&
        c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
        c->upload(&c->d_fix, fix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
@@ -971,16 +993,21 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->alloc(&c->d_R1, 4 * P) && c->alloc(&c->d_G, 16 * Pg) && c->alloc(&c->d_phi, P) && c->alloc(&c->d_S, P) &&
        c->alloc(&c->d_muhat, P) && c->alloc(&c->d_num, P) && c->alloc(&c->d_tmp, P) && c->alloc(&c->d_mu, P) &&
        c->alloc(&c->d_den, P) && c->alloc(&c->d_dt, 1) && c->alloc(&c->d_pmax, 2 * (size_t)npatch) &&
-       c->alloc(&c->d_flag, 1);
+       c->alloc(&c->d_flag, 1) && c->alloc(&c->d_skip_lines, 2) && c->alloc(&c->d_skip_flops, 2);
   if (!ok) {
     fprintf(stderr, "fc_init_patches: %s\n", c->err.c_str());
     delete c;
     return FC_ERR_OOM;
   }
   cudaMemset(c->d_flag, 0, sizeof(int));
+  cudaMemset(c->d_skip_lines, 0, 2 * sizeof(unsigned long long));
+  cudaMemset(c->d_skip_flops, 0, 2 * sizeof(double));
   DevTables& T = c->T;
+  T.skip_lines = c->d_skip_lines;
+  T.skip_flops = c->d_skip_flops;
   T.tw = c->d_tw;
   T.rp = c->d_rp;
+  T.ip = c->d_ip;
   T.plans = c->d_plans;
   T.info = c->d_info;
   T.patches = c->d_patches;
@@ -1434,6 +1461,26 @@ fc_status fc_pass_stats(const fc_ctx* c, const char* pass, double* flops, double
   *bytes = Bt;
   *lines = nl;
   *points = np;
+  return FC_OK;
+}
+
+fc_status fc_line_stats(fc_ctx* c, long long* lines_q1, long long* lines_q2, double* flops_q1, double* flops_q2,
+                        int reset) {
+  if (!c) return FC_ERR_INVALID;
+  unsigned long long l[2] = {0, 0};
+  double f[2] = {0, 0};
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(l, c->d_skip_lines, sizeof(l), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(f, c->d_skip_flops, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_check(c, "fc_line_stats");
+  if (lines_q1) *lines_q1 = (long long)l[0];
+  if (lines_q2) *lines_q2 = (long long)l[1];
+  if (flops_q1) *flops_q1 = f[0];
+  if (flops_q2) *flops_q2 = f[1];
+  if (reset) {
+    cudaMemset(c->d_skip_lines, 0, sizeof(l));
+    cudaMemset(c->d_skip_flops, 0, sizeof(f));
+  }
   return FC_OK;
 }
 

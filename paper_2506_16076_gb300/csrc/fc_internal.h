@@ -11,6 +11,7 @@ constexpr int MAXST = 24;       // max FFT stages per plan
 constexpr int MAXW = 8;         // max warps per CTA in the line kernels
 constexpr size_t SMEM_CAP = 200 * 1024;  // dynamic shared memory budget per CTA
 constexpr int SDNN_H = 16;      // hidden width of the stand-in classifier
+constexpr int MAX_GENERIC_RADIX = 128;  // largest prime factor of a continued length
 
 // Per-point flag word.
 enum : uint32_t {
@@ -32,6 +33,7 @@ struct Plan {
   int rad[MAXST];
   int tw;     // offset of the L-entry forward twiddle table exp(-2 pi i e / L) in the twiddle pool
   int sig;    // offset of the L-entry filter table sigma(2k/L)/L in the real pool (-1: none)
+  int rev;    // offset of the L-entry slot -> mode table of the in-place transforms in the int pool
 };
 
 // One line segment processed by one warp.
@@ -87,6 +89,7 @@ struct StageCoef {
 struct DevTables {
   const double2* tw;        // twiddle pool
   const double* rp;         // real pool (continuation matrices, filter tables)
+  const int* ip;            // int pool (slot -> mode tables)
   const Plan* plans;
   const uint32_t* info;     // per-point flags
   const PatchDev* patches;
@@ -95,6 +98,10 @@ struct DevTables {
   long long Pg;             // points of curvilinear patches (component stride of the scratch)
   double gamma;
   int d;
+  // lines whose gradient round was skipped because mu == 0 on the whole line (H = f(e)
+  // exactly there), and the algorithmic flops of the skipped rounds: [q1, q2] each
+  unsigned long long* skip_lines;
+  double* skip_flops;
 };
 
 // ---- launch wrappers (fc_kernels.cu) ----

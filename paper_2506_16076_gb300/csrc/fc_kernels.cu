@@ -15,14 +15,14 @@
 
 namespace fcx {
 
-// warps per CTA for a line kernel whose longest line has Lmax points: 4 Lmax complex
-// values of shared memory per warp (two packed sequences, Stockham ping-pong)
+// warps per CTA for a line kernel whose longest line has Lmax points: 2 Lmax complex
+// values of shared memory per warp (two packed sequences, transformed in place)
 int line_warps(int Lmax) {
-  const size_t per = (size_t)4 * Lmax * sizeof(double2);
+  const size_t per = (size_t)2 * Lmax * sizeof(double2);
   int w = (int)(SMEM_CAP / per);
   return w < 1 ? 1 : (w > MAXW ? MAXW : w);
 }
-size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * 4 * Lmax * sizeof(double2); }
+size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * 2 * Lmax * sizeof(double2); }
 
 __device__ __forceinline__ void flux_xy(double r, double mx, double my, double E, double gam, double* fx, double* fy) {
   const double ir = 1.0 / r;
@@ -67,20 +67,35 @@ __device__ __forceinline__ void load4(double2* A, int L, const Job& J, const dou
   }
 }
 
-// Forward FFT, derivative multiplier, inverse FFT of the two sequences in A (continued
-// first if the line is not periodic). Returns the buffer with the derivative.
-__device__ __forceinline__ double2* deriv2(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
-                                           int lane) {
+// In place on the two sequences in A (continued first if the line is not periodic):
+// forward transform, derivative multiplier, inverse transform (eq. fc_der).
+__device__ __forceinline__ void deriv2(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
   if (J.fcm >= 0) {
     FC_SYNC();
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
   }
   FC_SYNC();
-  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
-  double2* Y = (X == A) ? B : A;
-  mul_deriv(X, P.L, 2, J.scale * TWO_PI / ((double)P.L * (double)P.L), lane, 32);
+  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
+  mul_deriv_rev(A, P.L, 2, J.scale * TWO_PI / ((double)P.L * (double)P.L), T.ip + P.rev, lane, 32);
   FC_SYNC();
-  return fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
+}
+
+// true on every lane when mu != 0 somewhere on the line (warp vote)
+__device__ __forceinline__ bool line_viscous(const Job& J, const double* __restrict__ mu, int lane) {
+  bool v = false;
+  for (int t = lane; t < J.n; t += 32) v |= (mu[J.base + (long long)t * J.stride] != 0.0);
+  return __any_sync(0xffffffffu, v);
+}
+
+// record a skipped gradient round: one line, its algorithmic flops (2 packed transforms
+// forward and inverse, continuation of 4 components, multiplier)
+__device__ __forceinline__ void count_skip(const DevTables& T, int dir, const Job& J, int L, int lane) {
+  if (lane == 0 && T.skip_lines) {
+    atomicAdd(T.skip_lines + dir, 1ull);
+    const double f = 4.0 * 5.0 * L * log2((double)L) + 16.0 * T.d * J.C + 8.0 * L;
+    atomicAdd(T.skip_flops + dir, f);
+  }
 }
 
 __device__ __forceinline__ void stage_write(const StageCoef& sc, long long p, long long cs, const double* L4) {
@@ -112,26 +127,35 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* _
                                                         double* __restrict__ R1) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
-    load4(A, L, J, e, cs, lane);
-    double2* X = deriv2(A, B, J, P, T, lane);
-    double2* Y = (X == A) ? B : A;
+    const bool visc = line_viscous(J, mu, lane);
+    if (visc) {
+      load4(A, L, J, e, cs, lane);
+      deriv2(A, J, P, T, lane);
+    } else {
+      count_skip(T, 0, J, L, lane);
+    }
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       double f[4];
       flux_x(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
-      const double m = mu[p];
-      const double2 g0 = X[t], g1 = X[L + t];
-      Y[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
-      Y[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+      if (visc) {
+        const double m = mu[p];
+        const double2 g0 = A[t], g1 = A[L + t];
+        A[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
+        A[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+      } else {
+        A[t] = cpx(f[0], f[1]);
+        A[L + t] = cpx(f[2], f[3]);
+      }
     }
-    double2* Z = deriv2(Y, X, J, P, T, lane);
+    deriv2(A, J, P, T, lane);
+    double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const double2 a = Z[t], b = Z[L + t];
@@ -151,27 +175,36 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* _
                                                         StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P;
   const double* e = sc.Ucur;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
-    load4(A, L, J, e, cs, lane);
-    double2* X = deriv2(A, B, J, P, T, lane);
-    double2* Y = (X == A) ? B : A;
+    const bool visc = line_viscous(J, mu, lane);
+    if (visc) {
+      load4(A, L, J, e, cs, lane);
+      deriv2(A, J, P, T, lane);
+    } else {
+      count_skip(T, 1, J, L, lane);
+    }
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       double f[4];
       flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
-      const double m = mu[p];
-      const double2 g0 = X[t], g1 = X[L + t];
-      Y[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
-      Y[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+      if (visc) {
+        const double m = mu[p];
+        const double2 g0 = A[t], g1 = A[L + t];
+        A[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
+        A[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+      } else {
+        A[t] = cpx(f[0], f[1]);
+        A[L + t] = cpx(f[2], f[3]);
+      }
     }
-    double2* Z = deriv2(Y, X, J, P, T, lane);
+    deriv2(A, J, P, T, lane);
+    double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const double2 a = Z[t], b = Z[L + t];
@@ -202,13 +235,13 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __r
                                                       const double* __restrict__ e, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     load4(A, P.L, J, e, T.P, lane);
-    double2* X = deriv2(A, B, J, P, T, lane);
+    deriv2(A, J, P, T, lane);
+    double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       gslot(G, T.Pg, 0, 0)[g] = X[t].x;
@@ -227,16 +260,16 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
                                                       const double* __restrict__ Jm, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4(A, L, J, e, cs, lane);
-    double2* X = deriv2(A, B, J, P, T, lane);
-    double2* Y = (X == A) ? B : A;
+    deriv2(A, J, P, T, lane);
+    double2* X = A;
+    double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;
@@ -259,8 +292,9 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
       Y[t] = cpx(hx[0], hx[1]);
       Y[L + t] = cpx(hx[2], hx[3]);
     }
-    double2* Z = deriv2(Y, X, J, P, T, lane);
-    double2* W = (Z == A) ? B : A;
+    deriv2(A, J, P, T, lane);
+    double2* Z = A;
+    double2* W = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double j2x = Jm[g + 2 * Pg];
@@ -271,7 +305,8 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
       W[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
       W[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
     }
-    double2* V = deriv2(W, Z, J, P, T, lane);
+    deriv2(A, J, P, T, lane);
+    double2* V = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double j2y = Jm[g + 3 * Pg];
@@ -294,8 +329,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
                                                       StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -306,8 +340,9 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
       A[t] = cpx(gslot(G, Pg, 1, 0)[g], gslot(G, Pg, 1, 1)[g]);
       A[L + t] = cpx(gslot(G, Pg, 1, 2)[g], gslot(G, Pg, 1, 3)[g]);
     }
-    double2* X = deriv2(A, B, J, P, T, lane);
-    double2* Y = (X == A) ? B : A;
+    deriv2(A, J, P, T, lane);
+    double2* X = A;
+    double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double j1x = Jm[g];
@@ -318,7 +353,8 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
       Y[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
       Y[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
     }
-    double2* Z = deriv2(Y, X, J, P, T, lane);
+    deriv2(A, J, P, T, lane);
+    double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;
@@ -395,18 +431,16 @@ __device__ __forceinline__ double energy_of(double r, double mx, double my, doub
   return r * th / (gam - 1.0) + 0.5 * (mx * mx + my * my) / r;
 }
 
-__device__ __forceinline__ double2* filter2(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
-                                            int lane) {
+__device__ __forceinline__ void filter2(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
   if (J.fcm >= 0) {
     FC_SYNC();
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
   }
   FC_SYNC();
-  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
-  double2* Y = (X == A) ? B : A;
-  mul_filter(X, P.L, 2, T.rp + P.sig, lane, 32);
+  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
+  mul_filter_rev(A, P.L, 2, T.rp + P.sig, T.ip + P.rev, lane, 32);
   FC_SYNC();
-  return fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
 }
 
 __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job* __restrict__ jobs, int njobs,
@@ -414,8 +448,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job*
                                                           double* __restrict__ F) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -427,7 +460,8 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job*
       A[t] = cpx(r, mx);
       A[L + t] = cpx(my, theta_of(r, mx, my, e[p + 3 * cs], T.gamma));
     }
-    double2* X = filter2(A, B, J, P, T, lane);
+    filter2(A, J, P, T, lane);
+    double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       F[p] = X[t].x;
@@ -444,15 +478,15 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q2(DevTables T, const Job*
                                                           double* __restrict__ e) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4(A, L, J, F, cs, lane);
-    double2* X = filter2(A, B, J, P, T, lane);
+    filter2(A, J, P, T, lane);
+    double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const double r = X[t].x, mx = X[t].y, my = X[L + t].x, th = X[L + t].y;
@@ -755,19 +789,18 @@ __global__ void k_check_state(DevTables T, const double* __restrict__ e, int* fl
 // Transposed FC derivative of the two packed sequences in A (data in [0, n)):
 // D^T = extend^T o (-spectral derivative) o zero padding; extend^T folds the C
 // continuation entries back onto the first and last d points with ML^T and MR^T.
-__device__ __forceinline__ double2* deriv2T(double2* A, double2* B, const Job& J, const Plan& P, const DevTables& T,
-                                            int lane) {
+__device__ __forceinline__ double2* deriv2T(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
   const int L = P.L, n = J.n, C = J.C, d = T.d;
   for (int idx = lane; idx < 2 * C; idx += 32) {
     const int s = idx / C, k = idx - s * C;
     A[s * L + n + k] = cpx(0.0, 0.0);
   }
   FC_SYNC();
-  double2* X = fft_lines<false>(A, B, P, 2, T.tw, lane, 32);
-  double2* Y = (X == A) ? B : A;
-  mul_deriv(X, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), lane, 32);
+  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
+  mul_deriv_rev(A, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), T.ip + P.rev, lane, 32);
   FC_SYNC();
-  X = fft_lines<true>(X, Y, P, 2, T.tw, lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
+  double2* X = A;
   if (J.fcm >= 0) {
     const double* ML = T.rp + J.fcm;
     const double* MR = ML + C * d;
@@ -841,16 +874,15 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* 
                                                          const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4_masked(A, L, J, T, psi, lane);
-    double2* X = deriv2T(A, B, J, P, T, lane);
-    double2* Y = (X == A) ? B : A;
+    double2* X = deriv2T(A, J, P, T, lane);
+    double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const double eta[4] = {-X[t].x, -X[t].y, -X[L + t].x, -X[L + t].y};
@@ -872,7 +904,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* 
       Y[t] = cpx(m * eta[0], m * eta[1]);
       Y[L + t] = cpx(m * eta[2], m * eta[3]);
     }
-    double2* Z = deriv2T(Y, X, J, P, T, lane);
+    double2* Z = deriv2T(A, J, P, T, lane);
     const double dt = dir ? *dtp : 0.0;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -897,8 +929,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job*
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -912,7 +943,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job*
         A[t] = cpx(w * psi[p], w * psi[p + cs]);
         A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
       }
-      double2* X = deriv2T(A, B, J, P, T, lane);
+      double2* X = deriv2T(A, J, P, T, lane);
       for (int t = lane; t < J.n; t += 32) {
         const long long g = J.gbase + (long long)t * J.stride;
         gslot(G, Pg, which, 0)[g] = X[t].x;
@@ -933,8 +964,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job*
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -948,7 +978,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job*
         A[t] = cpx(w * psi[p], w * psi[p + cs]);
         A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
       }
-      double2* X = deriv2T(A, B, J, P, T, lane);
+      double2* X = deriv2T(A, J, P, T, lane);
       for (int t = lane; t < J.n; t += 32) {
         const long long g = J.gbase + (long long)t * J.stride;
         const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
@@ -983,7 +1013,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job*
       A[t] = cpx(g2[0], g2[1]);
       A[L + t] = cpx(g2[2], g2[3]);
     }
-    double2* Z = deriv2T(A, B, J, P, T, lane);
+    double2* Z = deriv2T(A, J, P, T, lane);
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double z[4] = {Z[t].x, Z[t].y, Z[L + t].x, Z[L + t].y};
@@ -1000,8 +1030,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_C(DevTables T, const Job*
                                                           double* __restrict__ acc, const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 4 * Lmax;
-  double2* B = A + 2 * Lmax;
+  double2* A = sm + warp * 2 * Lmax;
   const long long cs = T.P, Pg = T.Pg;
   const double dt = *dtp;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
@@ -1013,7 +1042,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_C(DevTables T, const Job*
       A[t] = cpx(gslot(G, Pg, 3, 0)[g], gslot(G, Pg, 3, 1)[g]);
       A[L + t] = cpx(gslot(G, Pg, 3, 2)[g], gslot(G, Pg, 3, 3)[g]);
     }
-    double2* X = deriv2T(A, B, J, P, T, lane);
+    double2* X = deriv2T(A, J, P, T, lane);
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;

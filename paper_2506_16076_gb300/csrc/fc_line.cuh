@@ -243,6 +243,157 @@ FC_HD double2* fft_lines(double2* a, double2* b, const Plan& P, int nseq, const 
   return a;
 }
 
+// ---- in-place transforms (one buffer): decimation in frequency forward, decimation in
+// time inverse. With stage radices R_0..R_{m-1} and spans L/(R_0..R_s), the forward
+// transform leaves mode k at slot p where p = sum_s d_s L/(R_0..R_s) and
+// k = sum_s d_s R_0..R_{s-1} (digit-reversed order, table Plan::rev); the inverse
+// transform takes that order back to natural order, so no permutation pass is needed
+// and spectral multipliers look up each slot's mode number.
+template <int R, bool INV, bool DIF>
+FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2* __restrict__ tw, int lane, int nl) {
+  const int nbf = L / R;
+  const int tws = L / (R * span);
+  for (int idx = lane; idx < nseq * nbf; idx += nl) {
+    const int s = idx / nbf;
+    const int t = idx - s * nbf;
+    const int bb = t / span;
+    const int j = t - bb * span;
+    double2* x = a + s * L + bb * R * span + j;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[r * span];
+    if (!DIF && j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        double2 w = tw[q * j * tws];
+        if (INV) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
+    }
+    Dft<R, INV>::run(v);
+    if (DIF && j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        double2 w = tw[q * j * tws];
+        if (INV) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r * span] = v[r];
+  }
+}
+
+template <bool INV, bool DIF>
+FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const double2* __restrict__ tw, int lane,
+                             int nl) {
+  const int nbf = L / R;
+  const int tws = L / (R * span);
+  const int wr = L / R;  // exp(s 2 pi i / R) = tw[wr]
+  for (int idx = lane; idx < nseq * nbf; idx += nl) {
+    const int s = idx / nbf;
+    const int t = idx - s * nbf;
+    const int bb = t / span;
+    const int j = t - bb * span;
+    double2* x = a + s * L + bb * R * span + j;
+    double2 v[MAX_GENERIC_RADIX], y[MAX_GENERIC_RADIX];
+    for (int r = 0; r < R; ++r) {
+      v[r] = x[r * span];
+      if (!DIF && j != 0 && r) {
+        double2 w = tw[r * j * tws];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    for (int q = 0; q < R; ++q) {
+      double ax = 0.0, ay = 0.0;
+      int e = 0;
+      for (int m = 0; m < R; ++m) {
+        double2 w = tw[e * wr];
+        if (INV) w.y = -w.y;
+        ax = fma(v[m].x, w.x, fma(-v[m].y, w.y, ax));
+        ay = fma(v[m].x, w.y, fma(v[m].y, w.x, ay));
+        e += q;
+        if (e >= R) e -= R;
+      }
+      y[q] = cpx(ax, ay);
+    }
+    for (int q = 0; q < R; ++q) {
+      double2 o = y[q];
+      if (DIF && j != 0 && q) {
+        double2 w = tw[q * j * tws];
+        if (INV) w.y = -w.y;
+        o = cmul(o, w);
+      }
+      x[q * span] = o;
+    }
+  }
+}
+
+// forward (DIF) or inverse (DIT) in-place transform of nseq sequences of length P.L in a
+template <bool INV>
+FC_HD void fft_inplace(double2* a, const Plan& P, int nseq, const double2* twpool, int lane, int nl) {
+  const double2* tw = twpool + P.tw;
+  const int L = P.L;
+  if (!INV) {
+    int span = L;
+    for (int st = 0; st < P.nst; ++st) {
+      const int R = P.rad[st];
+      span /= R;
+      switch (R) {
+        case 2: inplace_stage_r<2, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 3: inplace_stage_r<3, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 4: inplace_stage_r<4, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 5: inplace_stage_r<5, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 7: inplace_stage_r<7, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 8: inplace_stage_r<8, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        default: inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl); break;
+      }
+      FC_SYNC();
+    }
+  } else {
+    int span = 1;
+    for (int st = P.nst - 1; st >= 0; --st) {
+      const int R = P.rad[st];
+      switch (R) {
+        case 2: inplace_stage_r<2, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        case 3: inplace_stage_r<3, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        case 4: inplace_stage_r<4, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        case 5: inplace_stage_r<5, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        case 7: inplace_stage_r<7, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        case 8: inplace_stage_r<8, true, false>(a, L, span, nseq, tw, lane, nl); break;
+        default: inplace_stage_gen<true, false>(a, L, span, R, nseq, tw, lane, nl); break;
+      }
+      FC_SYNC();
+      span *= R;
+    }
+  }
+}
+
+// Z at slot t <- i m_k Z with k = rev[t] the mode held there (derivative, eq. fc_der)
+FC_HD void mul_deriv_rev(double2* a, int L, int nseq, double fac, const int* __restrict__ rev, int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) {
+    const int s = idx / L;
+    const int t = idx - s * L;
+    const int k = rev[t];
+    int kk = (2 * k <= L) ? k : k - L;
+    if (2 * k == L) kk = 0;
+    const double m = fac * (double)kk;
+    const double2 z = a[idx];
+    a[idx] = cpx(-m * z.y, m * z.x);
+  }
+}
+
+// Z at slot t <- sig[rev[t]] Z (eq. filtering; sig already divided by L)
+FC_HD void mul_filter_rev(double2* a, int L, int nseq, const double* __restrict__ sig, const int* __restrict__ rev,
+                          int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) {
+    const int s = idx / L;
+    const int t = idx - s * L;
+    a[idx] = cscl(a[idx], sig[rev[t]]);
+  }
+}
+
 // FC-Gram continuation (eq. continuation) of the nseq complex sequences in a: entries
 // [0, n) hold the data (two real lines packed as re/im); entries [n, n+C) receive
 //   ext = ML F_l + MR F_r,   ML = A_l Q^T, MR = A_r Q^T (C x d).

@@ -26,7 +26,7 @@ STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
            "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_drag", "fc_sync_status",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
-           "fc_pass_stats", "fc_last_error", "fc_destroy"]
+           "fc_pass_stats", "fc_line_stats", "fc_last_error", "fc_destroy"]
 
 
 class FcError(RuntimeError):
@@ -83,6 +83,8 @@ def load():
         "fc_profile_reset": (C.c_int, [vp]),
         "fc_pass_stats": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "fc_line_stats": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), ip]),
         "fc_last_error": (C.c_char_p, [vp]),
         "fc_destroy": (None, [vp]),
     }
@@ -251,5 +253,12 @@ class Context:
                                            C.byref(npt)))
         return f.value, b.value, nl.value, npt.value
 
+    def line_stats(self, reset=True):
+        """(skipped q1 lines, skipped q2 lines, skipped q1 flops, skipped q2 flops) since the last reset."""
+        a, b, f, g = C.c_longlong(), C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self.lib.fc_line_stats(self.ctx, C.byref(a), C.byref(b), C.byref(f), C.byref(g), 1 if reset else 0))
+        return a.value, b.value, f.value, g.value
+
     def profile_reset(self):
         self._check(self.lib.fc_profile_reset(self.ctx))
+

@@ -171,8 +171,8 @@ def cyl_m25_array(nx, nmin, nmax, seed, taper, nth, nr, name):
     sizes = seeded_sizes(nx, nx, nmin, nmax, seed, -8.0, 16.0, -12.0, 12.0, taper)
     og = _ogrid(nth, nr, 0.5, 1.5, fs)
     cart = _cart_array(nx, nx, -8.0, 16.0, -12.0, 12.0, None, 19, fs, hole=(0.0, 0.0, 1.0), sizes=sizes)
-    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs, init="freestream", steps=200,
-                    extra={"taper": taper, "seed": seed})
+    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs, init="potential", steps=200,
+                    extra={"taper": taper, "seed": seed, "cyl_radius": 0.5, "cutoff": 3.0})
 
 
 def cyl_m25_32():
@@ -237,10 +237,30 @@ def initial_state(w: Workload):
             L, R = w.extra["left"], w.extra["right"]
             left = x < w.extra["x_split"]
             prim = [np.where(left, L[k], R[k]) for k in range(4)]
+        elif w.init == "potential":
+            prim = potential_flow_prim(x, y, w.freestream, w.extra["cyl_radius"], w.extra["cutoff"])
         else:
             prim = [np.full(x.shape, w.freestream[k]) for k in range(4)]
         out.append(prim_to_cons(*prim, gamma=w.params.gamma))
     return out
+
+
+def potential_flow_prim(x, y, fs, R, cutoff):
+    """Free-stream density and pressure with the incompressible potential-flow velocity
+    around a cylinder of radius R at the origin, u - i v = U (e^{-ia} - R^2 e^{ia} / z^2),
+    whose wall-normal velocity vanishes on r = R. The disturbance is switched off smoothly
+    between r = cutoff and 2 cutoff so that the outer boundaries see the free stream."""
+    rho, u0, v0, p = fs
+    U = np.hypot(u0, v0)
+    a = np.arctan2(v0, u0)
+    z = x + 1j * y
+    r = np.abs(z)
+    zs = np.where(r > 0, z, 1.0)
+    dist = -U * R * R * np.exp(1j * a) / (zs * zs)  # disturbance of u - i v
+    t = np.clip((r - cutoff) / cutoff, 0.0, 1.0)
+    sw = np.where(t <= 0, 1.0, np.where(t >= 1, 0.0, 0.5 * (1 + np.cos(np.pi * t))))
+    w = u0 - 1j * v0 + sw * dist
+    return [np.full(x.shape, rho), w.real, -w.imag, np.full(x.shape, p)]
 
 
 def flatten(per_patch):
