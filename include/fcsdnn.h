@@ -186,6 +186,25 @@ fc_status fc_line_stats(fc_ctx *ctx, long long *lines_q1, long long *lines_q2, d
 fc_status fc_pass_stats(const fc_ctx *ctx, const char *pass, double *flops, double *bytes, long long *lines,
                         long long *points);
 
+/* RHS of one stand-alone affine patch without any device allocation. For callers that
+ * cannot allocate device memory: code under a host memory manager that owns all device
+ * memory, plug-ins whose host forbids allocation, paths that must not allocate once set
+ * up. (The paper has no counterpart: this is an interface of this library.)
+ * rhs_dev = L[e_dev] on the box [box[0], box[1]] x [box[2], box[3]] (host array) with
+ * n1 x n2 points (q1 fastest, state layout as above, P = n1 n2), viscosity mu_dev,
+ * FC order d and C continuation points on every line; table: host array of the
+ * d x d Q, C x d A_l and C x d A_r blocks (one C block of the fc_params tables).
+ * No boundary condition is applied (as in fc_rhs). The scratch is one static device
+ * array of about 18 MB held by every GPU that loads the library until exit; limits:
+ * n1 n2 <= 262144, n + C <= 1024, C <= 128, d <= 8 (beyond them the call prints the
+ * limits to stderr and returns FC_ERR_INVALID). All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race. The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture. The call
+ * synchronises the stream once (table upload from host memory). */
+fc_status fc_rhs_patch_noalloc(const double *e_dev, const double *mu_dev, double *rhs_dev, int n1, int n2,
+                               const double *box, int d, int C, const double *table, double gamma, void *stream);
+
 const char *fc_last_error(const fc_ctx *ctx);
 void fc_destroy(fc_ctx *ctx);
 

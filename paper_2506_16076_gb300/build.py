@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libfcsdnn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
-SOURCES = ["fc_kernels.cu", "fc_host.cpp"]
+SOURCES = ["fc_kernels.cu", "fc_host.cpp", "fc_noalloc.cu"]
 
 
 def nvcc():

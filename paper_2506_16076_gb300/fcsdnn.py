@@ -26,7 +26,7 @@ STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
            "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_drag", "fc_sync_status",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
-           "fc_pass_stats", "fc_line_stats", "fc_last_error", "fc_destroy"]
+           "fc_pass_stats", "fc_line_stats", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
 
 
 class FcError(RuntimeError):
@@ -85,6 +85,8 @@ def load():
                                     C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fc_line_stats": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), ip]),
+        "fc_rhs_patch_noalloc": (C.c_int, [vp, vp, vp, ip, ip, C.POINTER(C.c_double), ip, ip,
+                                           C.POINTER(C.c_double), C.c_double, vp]),
         "fc_last_error": (C.c_char_p, [vp]),
         "fc_destroy": (None, [vp]),
     }
@@ -262,3 +264,17 @@ class Context:
     def profile_reset(self):
         self._check(self.lib.fc_profile_reset(self.ctx))
 
+
+def rhs_patch_noalloc(e, mu, out, n1, n2, box, d, ncont, gamma=W.GAMMA):
+    """fc_rhs_patch_noalloc: RHS of one stand-alone affine patch, no device allocation."""
+    lib = load()
+    tab = fc_table_blob(d)
+    cmin = int(tab[1])
+    off = 3 + sum(d * d + 2 * c * d for c in range(cmin, ncont))
+    block = np.ascontiguousarray(tab[off:off + d * d + 2 * ncont * d])
+    bx = np.ascontiguousarray(np.asarray(box, dtype=np.float64))
+    st = lib.fc_rhs_patch_noalloc(_ptr(e), _ptr(mu), _ptr(out), int(n1), int(n2),
+                                  bx.ctypes.data_as(C.POINTER(C.c_double)), int(d), int(ncont),
+                                  block.ctypes.data_as(C.POINTER(C.c_double)), float(gamma), _stream())
+    if st != FC_OK:
+        raise FcError(st, "fc_rhs_patch_noalloc failed (see stderr)")
