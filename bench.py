@@ -77,7 +77,7 @@ def oracle_bench(workload, steps, warmup, npatch, budget_s=None):
             break
     el = time.perf_counter() - t0
     desc = (f"{len(ws.patches)} largest of the {len(w.patches)} patches of {workload} (stand-alone), "
-            f"{active} active points, {done} full steps, direct-DFT oracle")
+            f"{active} active points, {done} full steps, long-double FC oracle")
     return active * 5 * done / el, desc, el, done
 
 

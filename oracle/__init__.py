@@ -10,7 +10,9 @@ precomputed data loaded from disc (Sec. 2.2, Sec. 5.1).
 
 Every function follows a passage of Bruno & Leibovici, "General-domain
 FC-based shock-dynamics solver I: Basic elements" (arXiv 2506.16076), cited
-by section and equation label. Derivatives use a direct O(L^2) DFT, not an FFT.
+by section and equation label. Spectral derivatives and filters are evaluated in
+extended precision (long double) and rounded once to FP64; the DFT is numpy's FFT on
+long-double data, pinned against the explicit sum of its definition.
 
 Modules:
   fc         FC-Gram continuation, derivative, filter (Sec. 2.2, Sec. 4.3)

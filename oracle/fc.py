@@ -10,8 +10,16 @@ beta = L h) of a smooth periodic function whose Fourier coefficients are
 differentiated by (2 pi i k / beta) (eq. (fc_der)) or filtered by
 sigma(2k/(N+C)) = exp(-alpha_f (2k/(N+C))^p_f) (eq. (filtering), Sec. 4.3.1).
 
-The DFT here is the definition X_k = sum_j x_j exp(-2 pi i j k / L), written
-as an explicit L x L matrix product, so this module shares nothing with an FFT.
+Precision: eq. (fc_der) and eq. (filtering) are exact linear maps of the data; the
+oracle evaluates them in extended precision (numpy long double, 64-bit mantissa) and
+rounds once to FP64 at the end, so that its own evaluation error stays far below the
+FP64 rounding of any implementation it checks. The continued vector, the DFT, the
+multipliers and the inverse DFT all stay in long double. The DFT is the definition
+X_k = sum_j x_j exp(-2 pi i j k / L), computed by numpy's FFT routine on long-double
+data as a library primitive (the test suite pins it against the explicit sum). An
+FP64 direct sum is not accurate enough: on the Mach-25 fluxes (large mean, small
+variation) every term is rounded at the size of the mean, and its error in a
+derivative reaches 1.6e-10 of the result, where an FP64 FFT stays near 5e-12.
 Mode numbers k run over the symmetric range -M..M; for even L the Nyquist
 coefficient k = L/2 gets derivative factor 0 (keeps real data real) and filter
 factor sigma(1).
@@ -71,37 +79,52 @@ def choose_C(N, C0, policy):
     return C
 
 
-def continuation(F, d, C):
-    """Eq. (continuation): the C appended values of the FC-Gram continued vector.
+LD = np.longdouble
+CLD = np.clongdouble
+PI_LD = 4 * np.arctan(LD(1))  # pi to long-double precision
 
-    F: (..., N) real. Returns (..., C). The matrices A_l, A_r of an accurate d = 5
-    continuation have entries of order 1e4 whose contributions cancel, so the
-    product is evaluated in extended precision and rounded once to FP64 (same
-    formula, smaller evaluation error)."""
+
+def continuation_ld(F, d, C):
+    """Eq. (continuation): the C appended values of the FC-Gram continued vector, in
+    long double. F: (..., N) real. Returns (..., C).
+
+    The matrices A_l, A_r of an accurate d = 5 continuation have entries of order 1e4
+    whose contributions cancel, which is one more reason to evaluate in extended
+    precision."""
     Q, AL, AR = load_tables(d, C)
-    ld = np.longdouble
-    Fl = F[..., :d].astype(ld)
-    Fr = F[..., -d:].astype(ld)
-    ext = (Fl @ Q.astype(ld)) @ AL.T.astype(ld) + (Fr @ Q.astype(ld)) @ AR.T.astype(ld)  # A_l Q^T F_l + A_r Q^T F_r
-    return ext.astype(np.float64)
+    Fl = np.asarray(F)[..., :d].astype(LD)
+    Fr = np.asarray(F)[..., -d:].astype(LD)
+    return (Fl @ Q.astype(LD)) @ AL.T.astype(LD) + (Fr @ Q.astype(LD)) @ AR.T.astype(LD)  # A_l Q^T F_l + A_r Q^T F_r
 
 
-@functools.lru_cache(maxsize=None)
-def dft_matrix(L, sign):
-    j = np.arange(L)
-    return np.exp(sign * 2j * np.pi * (np.outer(j, j) % L) / L)  # jk reduced mod L: same value, exact argument
+def continuation(F, d, C):
+    """Eq. (continuation), rounded once to FP64."""
+    return continuation_ld(F, d, C).astype(np.float64)
+
+
+def extend_ld(F, d, C):
+    """The continued vector F^c = [F; continuation] of length N + C, in long double."""
+    return np.concatenate([np.asarray(F).astype(LD), continuation_ld(F, d, C)], axis=-1)
 
 
 def dft(x):
-    """X_k = sum_j x_j exp(-2 pi i j k / L) along the last axis (definition)."""
-    L = x.shape[-1]
-    return x @ dft_matrix(L, -1).T
+    """X_k = sum_j x_j exp(-2 pi i j k / L) along the last axis (definition), in long double."""
+    return np.fft.fft(np.asarray(x).astype(CLD), axis=-1)
 
 
 def idft(X):
-    """x_j = (1/L) sum_k X_k exp(+2 pi i j k / L) along the last axis (definition)."""
-    L = X.shape[-1]
-    return (X @ dft_matrix(L, +1).T) / L
+    """x_j = (1/L) sum_k X_k exp(+2 pi i j k / L) along the last axis (definition), in long double."""
+    return np.fft.ifft(np.asarray(X).astype(CLD), axis=-1)
+
+
+def dft_direct(x):
+    """The explicit sum of the DFT definition in long double (O(L^2); pins dft)."""
+    x = np.asarray(x).astype(CLD)
+    L = x.shape[-1]
+    j = np.arange(L)
+    a = -2 * PI_LD * (np.outer(j, j) % L).astype(LD) / L  # jk reduced mod L: same value, exact argument
+    M = np.cos(a) + 1j * np.sin(a)
+    return (x[..., None, :] * M).sum(axis=-1)
 
 
 def mode_numbers(L):
@@ -111,10 +134,12 @@ def mode_numbers(L):
 
 
 def spectral_derivative(Fc, beta):
-    """Eq. (fc_der): differentiate the periodic extension of one period Fc of length beta."""
+    """Eq. (fc_der): differentiate the periodic extension of one period Fc of length beta.
+
+    Evaluated in long double; returns long double (callers round once)."""
     L = Fc.shape[-1]
-    k = mode_numbers(L)
-    fac = 2j * np.pi * k / beta
+    k = mode_numbers(L).astype(LD)
+    fac = 2j * PI_LD * k / LD(beta)
     if L % 2 == 0:
         fac[L // 2] = 0.0
     return idft(fac * dft(Fc)).real
@@ -126,11 +151,13 @@ def sigma(k, L, alpha, p):
 
 
 def spectral_filter(Fc, alpha, p):
+    """Eq. (filtering) on one period, in long double; returns long double."""
     L = Fc.shape[-1]
     k = mode_numbers(L)
     if L % 2 == 0:
         k[L // 2] = L / 2
-    return idft(sigma(k, L, alpha, p) * dft(Fc)).real
+    s = np.exp(-LD(alpha) * (LD(2) * k.astype(LD) / LD(L)) ** p)
+    return idft(s * dft(Fc)).real
 
 
 def _real_linear(op):
@@ -150,27 +177,25 @@ def fc_derivative(F, h, d, C):
 
     The continued vector has L = N + C entries and period beta = L h."""
     N = F.shape[-1]
-    Fc = np.concatenate([F, continuation(F, d, C)], axis=-1)
-    return spectral_derivative(Fc, (N + C) * h)[..., :N]
+    return spectral_derivative(extend_ld(F, d, C), (N + C) * h)[..., :N].astype(np.float64)
 
 
 @_real_linear
 def periodic_derivative(F, h):
     """Fourier derivative of samples of a periodic function (no continuation), period N h."""
     N = F.shape[-1]
-    return spectral_derivative(F, N * h)
+    return spectral_derivative(np.asarray(F).astype(LD), N * h).astype(np.float64)
 
 
 @_real_linear
 def fc_filter(F, d, C, alpha, p):
     N = F.shape[-1]
-    Fc = np.concatenate([F, continuation(F, d, C)], axis=-1)
-    return spectral_filter(Fc, alpha, p)[..., :N]
+    return spectral_filter(extend_ld(F, d, C), alpha, p)[..., :N].astype(np.float64)
 
 
 @_real_linear
 def periodic_filter(F, alpha, p):
-    return spectral_filter(F, alpha, p)
+    return spectral_filter(np.asarray(F).astype(LD), alpha, p).astype(np.float64)
 
 
 @_real_linear
@@ -184,14 +209,14 @@ def fc_derivative_T(G, h, d, C):
     back onto the first and last d points with (A_l Q^T)^T and (A_r Q^T)^T."""
     N = G.shape[-1]
     L = N + C
-    Z = np.concatenate([G, np.zeros(G.shape[:-1] + (C,))], axis=-1)
+    Z = np.concatenate([np.asarray(G).astype(LD), np.zeros(G.shape[:-1] + (C,), LD)], axis=-1)
     W = -spectral_derivative(Z, L * h)
     Q, AL, AR = load_tables(d, C)
     out = W[..., :N].copy()
     ext = W[..., N:]
-    out[..., :d] += (ext @ AL) @ Q.T  # (A_l Q^T)^T w
-    out[..., N - d:] += (ext @ AR) @ Q.T  # (A_r Q^T)^T w
-    return out
+    out[..., :d] += (ext @ AL.astype(LD)) @ Q.T.astype(LD)  # (A_l Q^T)^T w
+    out[..., N - d:] += (ext @ AR.astype(LD)) @ Q.T.astype(LD)  # (A_r Q^T)^T w
+    return out.astype(np.float64)
 
 
 @_real_linear

@@ -20,6 +20,32 @@ def test_dft_matches_closed_forms():
     assert np.abs(fc.idft(fc.dft(x)) - x).max() < 5e-14
 
 
+@pytest.mark.parametrize("L", [7, 37, 64, 105, 378])
+def test_dft_is_the_explicit_sum(L):
+    # the library FFT on long-double data against the O(L^2) sum of the definition
+    rng = np.random.default_rng(L)
+    x = rng.normal(size=(3, L)) + 1j * rng.normal(size=(3, L))
+    X, Xd = fc.dft(x), fc.dft_direct(x)
+    assert X.dtype == np.clongdouble
+    assert float(np.abs(X - Xd).max()) < 1e-16 * L
+    xi = fc.idft(Xd)
+    assert float(np.abs(xi - x).max()) < 1e-17 * L
+
+
+def test_derivative_ignores_a_large_constant():
+    # D(F + c) = D(F) exactly for a periodic derivative; with dyadic samples F + c is exact
+    # in FP64, so any difference is the oracle's own evaluation error (an FP64 direct DFT
+    # leaves about 1e-10 of max|D F| here)
+    N = 384
+    t = np.arange(N) / N
+    F = np.round((np.sin(2 * np.pi * t) + 0.3 * np.cos(6 * np.pi * t + 1.0)) * 2.0**20) / 2.0**20
+    c = 1024.0
+    assert np.all((F + c) - c == F)
+    D0 = fc.periodic_derivative(F, 1.0 / N)
+    D1 = fc.periodic_derivative(F + c, 1.0 / N)
+    assert np.abs(D1 - D0).max() < 1e-14 * np.abs(D0).max()
+
+
 @pytest.mark.parametrize("d", [5, 2])
 def test_gram_basis_orthogonal_and_polynomial(d):
     for C in (27, 40, 71):
