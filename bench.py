@@ -173,6 +173,38 @@ def peaks():
     return p
 
 
+KERNEL_SOURCES = ["fc_kernels.cu", "fc_line.cuh", "fc_internal.h"]
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_16076_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes (read + write) of one pass of `kernel` from the committed ncu summary
+    profiles/traffic_<kernel>_<workload>.txt, or None when there is none or the kernel
+    sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for ln in f:
+                ln = ln.strip()
+                if ln and not ln.startswith("#") and " " in ln:
+                    k, v = ln.split(None, 1)
+                    kv[k] = v.strip()
+    except OSError:
+        return None
+    if kv.get("kernel_sources_sha256") != kernel_sources_sha():
+        return None
+    return int(kv["dram_bytes_read_per_pass"]) + int(kv["dram_bytes_write_per_pass"])
+
+
 def main_ours(args):
     import torch
     import torch.distributed as dist
@@ -309,7 +341,6 @@ def main_ours(args):
         flops_full = flops
         flops = flops - skipped
         avg_s = tot_ms / 1e3 / max(cnt, 1)
-        per_launch_flops = flops / max(cnt // 2 if dom.startswith("cart") else cnt // 2, 1)
         # one pass launch group covers all its length classes; flops above are per full pass
         groups = cnt
         passes = 2 * (5 if dom.startswith("cart") else 1)  # profiled 2 steps
@@ -318,14 +349,15 @@ def main_ours(args):
         fp64_peak = 152 * sm_max * 1e6 * 4 / 1e12  # 2 FP64 FMA lanes / clk / SM on GB300, TFLOP/s
         ach = flops / avg_pass_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": round(ach / fp64_peak, 4), "traffic": None, "kernel": f"k_{dom}",
+                "frac": round(ach / fp64_peak, 4), "traffic": measured_traffic(f"k_{dom}", args.workload),
+                "traffic_unit": "DRAM bytes per pass (all length-class launches), ncu", "kernel": f"k_{dom}",
+                "algorithmic_bytes_per_pass": nbytes,
                 "lines_per_pass": nl, "inviscid_lines_per_pass": skipped_lines,
                 "flops_per_pass_executed": flops, "flops_per_pass_all_rounds": flops_full,
                 "pass_ms": round(avg_pass_s * 1e3, 3), "launches_per_pass": groups // passes,
                 "hbm_GBps": round(nbytes / avg_pass_s / 1e9, 1),
                 "hbm_frac_of_measured": round(nbytes / avg_pass_s / 1e9 / pk.get("hbm_gbs", 6787.9), 4),
                 "peak_note": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flops x max SM clock (probe measured 1.199 TF/s)"}
-        _ = per_launch_flops
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -9,9 +9,11 @@ namespace fcx {
 
 constexpr int MAXST = 24;       // max FFT stages per plan
 constexpr int MAXW = 8;         // max warps per CTA in the line kernels
+constexpr int LINE_WARPS_DEFAULT = 1;  // default warps per CTA in the line kernels
 constexpr size_t SMEM_CAP = 200 * 1024;  // dynamic shared memory budget per CTA
 constexpr int SDNN_H = 16;      // hidden width of the stand-in classifier
 constexpr int MAX_GENERIC_RADIX = 128;  // largest prime factor of a continued length
+constexpr int CONT_TMP = 32;    // complex scratch per warp after the line buffer (detrended end data, d <= 8)
 
 // Per-point flag word.
 enum : uint32_t {

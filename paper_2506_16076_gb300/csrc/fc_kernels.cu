@@ -9,20 +9,34 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "fc_internal.h"
 #include "fc_line.cuh"
 
 namespace fcx {
 
-// warps per CTA for a line kernel whose longest line has Lmax points: 2 Lmax complex
-// values of shared memory per warp (two packed sequences, transformed in place)
-int line_warps(int Lmax) {
-  const size_t per = (size_t)2 * Lmax * sizeof(double2);
-  int w = (int)(SMEM_CAP / per);
-  return w < 1 ? 1 : (w > MAXW ? MAXW : w);
+// Warps per CTA of the line kernels. Each warp owns one line at a time and the warps of
+// a CTA never synchronise with each other, so small CTAs let the block scheduler hand a
+// freed warp slot the next line at once (lines differ in length and in the number of
+// derivative rounds); FCSDNN_LINE_WARPS (1..8) overrides the default for launch-shape
+// sweeps. Shared memory per warp: 2 Lmax complex values (two packed sequences,
+// transformed in place) plus the continuation's end data.
+static int line_warps_cap() {
+  static int cap = [] {
+    const char* v = getenv("FCSDNN_LINE_WARPS");
+    const int c = v ? atoi(v) : LINE_WARPS_DEFAULT;
+    return c < 1 ? 1 : (c > MAXW ? MAXW : c);
+  }();
+  return cap;
 }
-size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * 2 * Lmax * sizeof(double2); }
+int line_warps(int Lmax) {
+  const size_t per = (size_t)(2 * Lmax + CONT_TMP) * sizeof(double2);
+  int w = (int)(SMEM_CAP / per);
+  const int cap = line_warps_cap();
+  return w < 1 ? 1 : (w > cap ? cap : w);
+}
+size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * (2 * Lmax + CONT_TMP) * sizeof(double2); }
 
 __device__ __forceinline__ void flux_xy(double r, double mx, double my, double E, double gam, double* fx, double* fy) {
   const double ir = 1.0 / r;
@@ -69,10 +83,11 @@ __device__ __forceinline__ void load4(double2* A, int L, const Job& J, const dou
 
 // In place on the two sequences in A (continued first if the line is not periodic):
 // forward transform, derivative multiplier, inverse transform (eq. fc_der).
-__device__ __forceinline__ void deriv2(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
+__device__ __forceinline__ void deriv2(double2* A, int Lmax, const Job& J, const Plan& P, const DevTables& T,
+                                       int lane) {
   if (J.fcm >= 0) {
     FC_SYNC();
-    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
+    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
   fft_inplace<false>(A, P, 2, T.tw, lane, 32);
@@ -127,7 +142,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* _
                                                         double* __restrict__ R1) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -136,7 +151,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* _
     const bool visc = line_viscous(J, mu, lane);
     if (visc) {
       load4(A, L, J, e, cs, lane);
-      deriv2(A, J, P, T, lane);
+      deriv2(A, Lmax, J, P, T, lane);
     } else {
       count_skip(T, 0, J, L, lane);
     }
@@ -154,7 +169,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* _
         A[L + t] = cpx(f[2], f[3]);
       }
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -175,7 +190,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* _
                                                         StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P;
   const double* e = sc.Ucur;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* _
     const bool visc = line_viscous(J, mu, lane);
     if (visc) {
       load4(A, L, J, e, cs, lane);
-      deriv2(A, J, P, T, lane);
+      deriv2(A, Lmax, J, P, T, lane);
     } else {
       count_skip(T, 1, J, L, lane);
     }
@@ -203,7 +218,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* _
         A[L + t] = cpx(f[2], f[3]);
       }
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -235,12 +250,12 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __r
                                                       const double* __restrict__ e, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     load4(A, P.L, J, e, T.P, lane);
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
@@ -260,14 +275,14 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
                                                       const double* __restrict__ Jm, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4(A, L, J, e, cs, lane);
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* X = A;
     double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
@@ -292,7 +307,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
       Y[t] = cpx(hx[0], hx[1]);
       Y[L + t] = cpx(hx[2], hx[3]);
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* Z = A;
     double2* W = A;
     for (int t = lane; t < J.n; t += 32) {
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
       W[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
       W[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* V = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
                                                       StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
       A[t] = cpx(gslot(G, Pg, 1, 0)[g], gslot(G, Pg, 1, 1)[g]);
       A[L + t] = cpx(gslot(G, Pg, 1, 2)[g], gslot(G, Pg, 1, 3)[g]);
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* X = A;
     double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __r
       Y[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
       Y[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
     }
-    deriv2(A, J, P, T, lane);
+    deriv2(A, Lmax, J, P, T, lane);
     double2* Z = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -431,10 +446,11 @@ __device__ __forceinline__ double energy_of(double r, double mx, double my, doub
   return r * th / (gam - 1.0) + 0.5 * (mx * mx + my * my) / r;
 }
 
-__device__ __forceinline__ void filter2(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
+__device__ __forceinline__ void filter2(double2* A, int Lmax, const Job& J, const Plan& P, const DevTables& T,
+                                        int lane) {
   if (J.fcm >= 0) {
     FC_SYNC();
-    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32);
+    continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
   fft_inplace<false>(A, P, 2, T.tw, lane, 32);
@@ -448,7 +464,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job*
                                                           double* __restrict__ F) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -460,7 +476,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job*
       A[t] = cpx(r, mx);
       A[L + t] = cpx(my, theta_of(r, mx, my, e[p + 3 * cs], T.gamma));
     }
-    filter2(A, J, P, T, lane);
+    filter2(A, Lmax, J, P, T, lane);
     double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -478,14 +494,14 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q2(DevTables T, const Job*
                                                           double* __restrict__ e) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4(A, L, J, F, cs, lane);
-    filter2(A, J, P, T, lane);
+    filter2(A, Lmax, J, P, T, lane);
     double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -874,7 +890,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* 
                                                          const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -929,7 +945,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job*
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -964,7 +980,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job*
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P, Pg = T.Pg;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
@@ -1030,7 +1046,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_C(DevTables T, const Job*
                                                           double* __restrict__ acc, const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2* A = sm + warp * 2 * Lmax;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   const long long cs = T.P, Pg = T.Pg;
   const double dt = *dtp;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {

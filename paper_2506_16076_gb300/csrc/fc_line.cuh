@@ -1,4 +1,4 @@
-// Per-line building blocks of the FC derivative and filter: mixed-radix Stockham FFT
+// Per-line building blocks of the FC derivative and filter: in-place mixed-radix FFT
 // stages in shared memory, FC-Gram continuation, spectral multipliers.
 //
 // Every function takes (lane, nl): lane index and lane count of the group that
@@ -72,18 +72,20 @@ struct Dft<8, INV> {
     Dft<4, INV>::run(e);
     Dft<4, INV>::run(o);
     const double r = 0.7071067811865476;
-    const double s = INV ? 1.0 : -1.0;
-    double2 t1 = cpx(r * (o[1].x - s * o[1].y), r * (o[1].y + s * o[1].x));   // w8^1 o1
-    double2 t2 = mul_si<INV>(o[2]);                                            // w8^2 o2
-    double2 t3 = cpx(r * (-o[3].x - s * o[3].y), r * (-o[3].y + s * o[3].x));  // w8^3 o3
+    // w8^1 o1 = r a1, w8^3 o3 = r a3 with the sums below; r folded into the FMAs
+    const double2 a1 = INV ? cpx(o[1].x - o[1].y, o[1].y + o[1].x)   // o1.x - s o1.y, o1.y + s o1.x
+                           : cpx(o[1].x + o[1].y, o[1].y - o[1].x);
+    const double2 a3 = INV ? cpx(-(o[3].x + o[3].y), o[3].x - o[3].y)  // -o3.x - s o3.y, -o3.y + s o3.x
+                           : cpx(o[3].y - o[3].x, -(o[3].y + o[3].x));
+    const double2 t2 = mul_si<INV>(o[2]);  // w8^2 o2
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], t1);
-    v[5] = csub(e[1], t1);
+    v[1] = cpx(fma(r, a1.x, e[1].x), fma(r, a1.y, e[1].y));
+    v[5] = cpx(fma(-r, a1.x, e[1].x), fma(-r, a1.y, e[1].y));
     v[2] = cadd(e[2], t2);
     v[6] = csub(e[2], t2);
-    v[3] = cadd(e[3], t3);
-    v[7] = csub(e[3], t3);
+    v[3] = cpx(fma(r, a3.x, e[3].x), fma(r, a3.y, e[3].y));
+    v[7] = cpx(fma(-r, a3.x, e[3].x), fma(-r, a3.y, e[3].y));
   }
 };
 
@@ -126,7 +128,8 @@ struct DftOdd {
     for (int m = 0; m < H; ++m) y0 = cadd(y0, a[m]);
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
-      double2 t = x0, u = cpx(0.0, 0.0);
+      double2 t = x0;
+      double2 u;
 #pragma unroll
       for (int m = 1; m <= H; ++m) {
         int km = (q * m) % R;  // angle index in 1..R-1
@@ -139,7 +142,7 @@ struct DftOdd {
           ss = -OddConst<R>::s(R - km);
         }
         t = cpx(fma(cc, a[m - 1].x, t.x), fma(cc, a[m - 1].y, t.y));
-        u = cpx(fma(ss, b[m - 1].x, u.x), fma(ss, b[m - 1].y, u.y));
+        u = (m == 1) ? cpx(ss * b[0].x, ss * b[0].y) : cpx(fma(ss, b[m - 1].x, u.x), fma(ss, b[m - 1].y, u.y));
       }
       double2 iu = mul_si<INV>(u);
       v[q] = cadd(t, iu);
@@ -154,94 +157,6 @@ template <bool INV>
 struct Dft<5, INV> : DftOdd<5, INV> {};
 template <bool INV>
 struct Dft<7, INV> : DftOdd<7, INV> {};
-
-// ---- one Stockham stage of radix R over nseq sequences of length L (Ns = product of earlier radices)
-template <int R, bool INV>
-FC_HD void stage_r(const double2* __restrict__ in, double2* __restrict__ out, int L, int Ns, int nseq,
-                   const double2* __restrict__ tw, int lane, int nl) {
-  const int nb = L / R;
-  const int tws = L / (Ns * R);
-  for (int idx = lane; idx < nseq * nb; idx += nl) {
-    const int s = idx / nb;
-    const int j = idx - s * nb;
-    const double2* x = in + s * L;
-    double2* y = out + s * L;
-    const int k = j % Ns;
-    double2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = x[j + r * nb];
-    if (k != 0) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        double2 w = tw[r * k * tws];
-        if (INV) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
-    }
-    Dft<R, INV>::run(v);
-    const int base = j + (j / Ns) * Ns * (R - 1);
-#pragma unroll
-    for (int r = 0; r < R; ++r) y[base + r * Ns] = v[r];
-  }
-}
-
-// generic radix (any prime R): one output element per iteration, O(R) work each
-template <bool INV>
-FC_HD void stage_gen(const double2* __restrict__ in, double2* __restrict__ out, int L, int Ns, int R, int nseq,
-                     const double2* __restrict__ tw, int lane, int nl) {
-  const int nb = L / R;
-  const int str = L / (Ns * R);
-  for (int idx = lane; idx < nseq * L; idx += nl) {
-    const int s = idx / L;
-    const int o = idx - s * L;
-    const int g = o / (Ns * R);
-    const int rem = o - g * Ns * R;
-    const int q = rem / Ns;
-    const int k = rem - q * Ns;
-    const int j = g * Ns + k;
-    const double2* x = in + s * L;
-    const int ph = (k + q * Ns) * str;  // < L
-    int e = 0;
-    double ax = 0.0, ay = 0.0;
-    for (int m = 0; m < R; ++m) {
-      double2 w = tw[e];
-      if (INV) w.y = -w.y;
-      const double2 xv = x[j + m * nb];
-      ax = fma(xv.x, w.x, fma(-xv.y, w.y, ax));
-      ay = fma(xv.x, w.y, fma(xv.y, w.x, ay));
-      e += ph;
-      if (e >= L) e -= L;
-    }
-    out[s * L + o] = cpx(ax, ay);
-  }
-}
-
-// Full transform of nseq sequences stored back to back in a (length L each); b is scratch
-// of the same size. Returns the buffer that holds the result (a or b).
-template <bool INV>
-FC_HD double2* fft_lines(double2* a, double2* b, const Plan& P, int nseq, const double2* twpool, int lane, int nl) {
-  const double2* tw = twpool + P.tw;
-  const int L = P.L;
-  int Ns = 1;
-  for (int st = 0; st < P.nst; ++st) {
-    const int R = P.rad[st];
-    switch (R) {
-      case 2: stage_r<2, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      case 3: stage_r<3, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      case 4: stage_r<4, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      case 5: stage_r<5, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      case 7: stage_r<7, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      case 8: stage_r<8, INV>(a, b, L, Ns, nseq, tw, lane, nl); break;
-      default: stage_gen<INV>(a, b, L, Ns, R, nseq, tw, lane, nl); break;
-    }
-    FC_SYNC();
-    double2* t = a;
-    a = b;
-    b = t;
-    Ns *= R;
-  }
-  return a;
-}
 
 // ---- in-place transforms (one buffer): decimation in frequency forward, decimation in
 // time inverse. With stage radices R_0..R_{m-1} and spans L/(R_0..R_s), the forward
@@ -378,7 +293,7 @@ FC_HD void mul_deriv_rev(double2* a, int L, int nseq, double fac, const int* __r
     const int k = rev[t];
     int kk = (2 * k <= L) ? k : k - L;
     if (2 * k == L) kk = 0;
-    const double m = fac * (double)kk;
+    const double m = (fac * (double)kk);
     const double2 z = a[idx];
     a[idx] = cpx(-m * z.y, m * z.x);
   }
@@ -404,61 +319,58 @@ FC_HD void mul_filter_rev(double2* a, int L, int nseq, const double* __restrict_
 // with uL = ML 1, vL = ML tau_l, uR = MR 1, vR = MR tau_r precomputed. The detrended
 // values are differences of nearby samples (exact or nearly so), so the large
 // coefficients multiply only second differences. Layout of M: ML, MR, uL, vL, uR, vR.
+// tmp: 2 d nseq complex scratch (the detrended end data, computed once per line).
 FC_HD void continue_lines(double2* a, int L, int n, int C, int d, const double* __restrict__ M, int nseq, int lane,
-                          int nl) {
+                          int nl, double2* tmp) {
   const double* ML = M;
   const double* MR = M + C * d;
   const double* uL = MR + C * d;
   const double* vL = uL + C;
   const double* uR = vL + C;
   const double* vR = uR + C;
+  // phase 1: per sequence, the detrended end values F~_l[2..d-1], F~_r[0..d-3] and the
+  // end value / end slope of both ends, 2d complex values per sequence, into tmp
+  for (int idx = lane; idx < nseq * 2 * d; idx += nl) {
+    const int s = idx / (2 * d);
+    const int q = idx - s * 2 * d;
+    const double2* x = a + s * L;
+    const double2 f0 = x[0], f1 = x[1], fn = x[n - 1], fm = x[n - 2];
+    const double2 dl = csub(f1, f0), dr = csub(fn, fm);
+    double2 v;
+    if (q < d - 2) {  // left, j = q + 2
+      const double j = (double)(q + 2);
+      v = cpx(fma(-j, dl.x, (x[q + 2].x - f0.x)), fma(-j, dl.y, (x[q + 2].y - f0.y)));
+    } else if (q < 2 * d - 4) {  // right, j = q - (d - 2)
+      const int j = q - (d - 2);
+      const double t = (double)(d - 1 - j);
+      v = cpx(fma(t, dr.x, (x[n - d + j].x - fn.x)), fma(t, dr.y, (x[n - d + j].y - fn.y)));
+    } else {
+      const int w = q - (2 * d - 4);  // 0: f0, 1: dl, 2: fn, 3: dr
+      v = w == 0 ? f0 : (w == 1 ? dl : (w == 2 ? fn : dr));
+    }
+    tmp[idx] = v;
+  }
+  FC_SYNC();
+  // phase 2: ext_k = ML F~_l + MR F~_r + F_0 uL + dl vL + F_{n-1} uR + dr vR
   for (int idx = lane; idx < nseq * C; idx += nl) {
     const int s = idx / C;
     const int k = idx - s * C;
-    const double2* x = a + s * L;
-    const double2 f0 = x[0], f1 = x[1], fn = x[n - 1], fm = x[n - 2];
-    const double dlx = f1.x - f0.x, dly = f1.y - f0.y;
-    const double drx = fn.x - fm.x, dry = fn.y - fm.y;
+    const double2* e = tmp + s * 2 * d;
     double ex = 0.0, ey = 0.0;
     for (int j = 2; j < d; ++j) {
       const double ml = ML[k * d + j];
-      const double2 fl = x[j];
-      ex = fma(ml, (fl.x - f0.x) - (double)j * dlx, ex);
-      ey = fma(ml, (fl.y - f0.y) - (double)j * dly, ey);
+      ex = fma(ml, e[j - 2].x, ex);
+      ey = fma(ml, e[j - 2].y, ey);
     }
     for (int j = 0; j < d - 2; ++j) {
       const double mr = MR[k * d + j];
-      const double2 fr = x[n - d + j];
-      const double t = (double)(d - 1 - j);
-      ex = fma(mr, (fr.x - fn.x) + t * drx, ex);
-      ey = fma(mr, (fr.y - fn.y) + t * dry, ey);
+      ex = fma(mr, e[d - 2 + j].x, ex);
+      ey = fma(mr, e[d - 2 + j].y, ey);
     }
-    ex = fma(f0.x, uL[k], fma(dlx, vL[k], fma(fn.x, uR[k], fma(drx, vR[k], ex))));
-    ey = fma(f0.y, uL[k], fma(dly, vL[k], fma(fn.y, uR[k], fma(dry, vR[k], ey))));
+    const double2 f0 = e[2 * d - 4], dl = e[2 * d - 3], fn = e[2 * d - 2], dr = e[2 * d - 1];
+    ex = fma(f0.x, uL[k], fma(dl.x, vL[k], fma(fn.x, uR[k], fma(dr.x, vR[k], ex))));
+    ey = fma(f0.y, uL[k], fma(dl.y, vL[k], fma(fn.y, uR[k], fma(dr.y, vR[k], ey))));
     a[s * L + n + k] = cpx(ex, ey);
-  }
-}
-
-// Z_k <- i m_k Z_k with m_k = fac * k, k the signed mode number; the Nyquist mode of an
-// even length gets 0 (eq. fc_der). fac includes the 1/L of the inverse transform.
-FC_HD void mul_deriv(double2* a, int L, int nseq, double fac, int lane, int nl) {
-  for (int idx = lane; idx < nseq * L; idx += nl) {
-    const int s = idx / L;
-    const int t = idx - s * L;
-    int kk = (2 * t <= L) ? t : t - L;
-    if (2 * t == L) kk = 0;
-    const double m = fac * (double)kk;
-    const double2 z = a[idx];
-    a[idx] = cpx(-m * z.y, m * z.x);
-  }
-}
-
-// Z_k <- sig[k] Z_k (sig already divided by L) (eq. filtering)
-FC_HD void mul_filter(double2* a, int L, int nseq, const double* __restrict__ sig, int lane, int nl) {
-  for (int idx = lane; idx < nseq * L; idx += nl) {
-    const int s = idx / L;
-    const int t = idx - s * L;
-    a[idx] = cscl(a[idx], sig[t]);
   }
 }
 

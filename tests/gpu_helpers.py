@@ -46,3 +46,9 @@ def smooth_mu(w, seed, scale):
         x, y = W.patch_xy(p)
         out.append(scale * (1.0 + np.sin(a * x) * np.cos(b * y + c)) ** 2)
     return out
+
+
+def rel_err_normwise(gpu, orc):
+    """max over points and components of |gpu - orc|, over max |orc| (all components)."""
+    top = max(np.abs(o).max() for o in orc)
+    return max(np.abs(g - o).max() for g, o in zip(gpu, orc)) / max(top, 1e-300)

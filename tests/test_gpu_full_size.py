@@ -1,0 +1,117 @@
+"""Parity at the full size of the Mach-25 32 x 32 workload (28.0M points, 1025 patches).
+
+The GPU evaluates the whole batched operator (one launch per pass and length class, the
+launch configuration of the timed step); the oracle recomputes sampled patches one by
+one. The RHS of a patch (eq. general_curvilinear with the FC derivatives of Sec. 2.2)
+and the per-step filter (Sec. 4.3.1) depend only on that patch's own state and
+viscosity, so each sampled patch is an exact, independent check of the batched result.
+Samples: the O-grid, the largest and the smallest affine patch, a hole-cut patch and
+seeded random patches; two viscosity fields, one smooth everywhere and one that is zero
+on half of the lines (the inviscid-line path of the kernels).
+
+States: the seeded smooth perturbation of the free stream with relative amplitude 0.2
+used by every RHS parity test. Error measure: normwise, the largest difference over
+points and components relative to the largest |RHS| entry. At Mach 25 the pressure is
+a small difference of large energies (E/p about 200), so each component's RHS carries
+rounding noise of the size of the pressure's rounding times the derivative's norm; the
+rho v component, two orders smaller than the energy component, then has a
+per-component relative noise floor near 1e-11: two FP64 evaluations of the oracle
+itself that differ only in how u, v and p are rounded differ by 4e-12 in rho v at
+amplitude 0.2 and 2e-11 at 0.05. The per-component errors are reported with each
+assertion.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import geometry, solver as S
+from paper_2506_16076_gb300 import workloads as W
+from tests.gpu_helpers import rel_err, rel_err_normwise, smooth_mu
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def full(gpu_lib):
+    w = W.cyl_m25_32()
+    ctx = gpu_lib.Context(w)
+    sv = S.Solver.__new__(S.Solver)  # per-patch oracle operators only (no global connectivity)
+    sv.prm = w.params
+    sizes = [p.n1 * p.n2 for p in w.patches]
+    aff = [k for k, p in enumerate(w.patches) if p.kind == W.AFFINE]
+    big = max(aff, key=lambda k: sizes[k])
+    small = min(aff, key=lambda k: sizes[k])
+    holed = None  # a patch that the hole cuts only in part (segments of several lengths)
+    for k in aff:
+        x0, x1, y0, y1 = w.patches[k].geom
+        if x0 < 1.0 and x1 > -1.0 and y0 < 1.0 and y1 > -1.0:
+            nb = int(geometry.PatchGeo(w.patches[k], w.params).blank.sum())
+            if 0 < nb < sizes[k] and k != big:
+                holed = k
+                break
+    rng = np.random.default_rng(7)
+    rand = [int(k) for k in rng.choice(aff, 2, replace=False)]
+    sample = sorted({0, big, small, holed, *rand} - {None})
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    return w, ctx, sv, sample, offs
+
+
+def _state(w, seed):
+    st = W.random_smooth_state(w, seed=seed, amp=0.2)
+    return st, torch.from_numpy(np.ascontiguousarray(W.flatten(st))).cuda()
+
+
+def _mu_fields(w):
+    a = smooth_mu(w, seed=3, scale=1e-3)
+    b = []
+    for k, m in enumerate(a):
+        if k % 2 == 1:
+            b.append(m.copy())
+        else:
+            z = m.copy()
+            z[: m.shape[0] // 2, :] = 0.0  # rows of the lower half carry mu = 0
+            b.append(z)
+    return {"smooth": a, "half_inviscid": b}
+
+
+def _patch(t, offs, k, P, ncomp=4):
+    a = t.detach().cpu().numpy().reshape(ncomp, P)
+    return a[:, offs[k]:offs[k + 1]]
+
+
+@pytest.mark.parametrize("which", ["smooth", "half_inviscid"])
+def test_full_size_rhs_sampled(full, which):
+    w, ctx, sv, sample, offs = full
+    st, e = _state(w, seed=31)
+    mu = _mu_fields(w)[which]
+    m = torch.from_numpy(np.concatenate([a.ravel() for a in mu])).cuda()
+    out = torch.empty_like(e)
+    ctx.rhs(e, out, m)
+    torch.cuda.synchronize()
+    P = int(offs[-1])
+    got, ref = [], []
+    for k in sample:
+        p = w.patches[k]
+        g = geometry.PatchGeo(p, w.params)
+        ref.append(sv.rhs_patch(g, st[k], mu[k]))
+        got.append(_patch(out, offs, k, P).reshape(4, p.n2, p.n1))
+    err = rel_err_normwise(got, ref)
+    assert err < RHS_TOL, (sample, err, rel_err(got, ref))
+
+
+def test_full_size_filter_sampled(full):
+    w, ctx, sv, sample, offs = full
+    st, e = _state(w, seed=37)
+    ctx.filter(e)
+    torch.cuda.synchronize()
+    P = int(offs[-1])
+    got, ref = [], []
+    for k in sample:
+        p = w.patches[k]
+        g = geometry.PatchGeo(p, w.params)
+        ref.append(sv.filter_patch(g, st[k]))
+        got.append(_patch(e, offs, k, P).reshape(4, p.n2, p.n1))
+    errs = rel_err(got, ref)
+    assert max(errs) < RHS_TOL, (sample, errs)

@@ -161,3 +161,17 @@ def test_slip_wall_zeroes_normal_momentum():
     g = sv.geos[0]
     mn = out[0][1][0] * g.cos[0] + out[0][2][0] * g.sin[0]
     assert np.abs(mn).max() < 1e-13
+
+
+def test_stored_sod_reference_matches_oracle():
+    # the stored 100-step shock-tube state (tests/golden/sod128_100steps.npz) comes from
+    # this oracle: its first two CFL steps are recomputed here
+    from tests.golden.make_sod128_reference import OUT
+    ref = np.load(OUT)
+    w = W.sod128(128)
+    sv = S.Solver(w)
+    st = S.smear_initial(sv, W.initial_state(w), 0.5)
+    for n in range(2):
+        st = sv.step(st, n)
+        assert abs(sv.last_dt - ref["dt"][n]) <= 1e-15 * ref["dt"][n]
+    assert ref["state"].shape == (4, 128, 128) and np.isfinite(ref["state"]).all()
