@@ -71,7 +71,12 @@ typedef struct {
  * w_{0,9} (win_r 9, Sec. 5.2), 7x7 localisation (loc 7), R = (1.5,1,0.5,0) (Sec. 5.1).
  * fc_tables: host array, [0]=d, [1]=Cmin, [2]=Cmax, then for C = Cmin..Cmax the
  *   blocks Q (d x d), A_l (C x d), A_r (C x d), row-major (eq. continuation).
- * c_policy 0: C = C0 on every line; 1: smallest C >= C0 with N + C 7-smooth.
+ * c_policy (the paper leaves C free, Sec. 2.2): 0: C = C0 on every line; 1: smallest
+ *   C >= C0 with N + C 7-smooth; 2: the C in [C0, Cmax] whose continued length N + C
+ *   has the smallest estimated transform cost: N + C factored greedily into 8, 4, 2,
+ *   3, 5, 7, cost = sum over stages of (L/R) B(R) with B = 4, 16, 52, 14, 36, 66 for
+ *   R = 2, 4, 8, 3, 5, 7, plus 4 (L/R)(R-1) on every stage but the last; ties to the
+ *   smaller C; falls back to policy 1 when no N + C in range is 7-smooth.
  * sdnn_w: host FP32 weights of the 7-16-16-4 classifier: W1[16][7], b1[16],
  *   W2[16][16], b2[16], W3[4][16], b3[4] (sdnn_len = 420).
  * depth_cap: cap of the index distance used to rank donors. */

@@ -55,7 +55,7 @@ def d1T(sv, g, G):
             out[..., j, a:a + n] = fc.periodic_derivative_T(G[..., j, a:a + n], g.h1)
         elif n >= 2 * prm.d:
             out[..., j, a:a + n] = fc.fc_derivative_T(G[..., j, a:a + n], g.h1, prm.d,
-                                                      fc.choose_C(n, prm.C0, prm.c_policy))
+                                                      fc.choose_C(n, prm.C0, prm.c_policy, prm.d))
     return out
 
 
@@ -65,7 +65,7 @@ def d2T(sv, g, G):
     for (i, a, n, per) in g.seg2:
         if n >= 2 * prm.d:
             out[..., a:a + n, i] = fc.fc_derivative_T(G[..., a:a + n, i], g.h2, prm.d,
-                                                      fc.choose_C(n, prm.C0, prm.c_policy))
+                                                      fc.choose_C(n, prm.C0, prm.c_policy, prm.d))
     return out
 
 

@@ -65,14 +65,59 @@ def is_7smooth(n):
     return n == 1
 
 
-def choose_C(N, C0, policy):
-    """Continuation length for a line of N points.
+@functools.lru_cache(maxsize=None)
+def table_range(d):
+    """Smallest and largest C with an FC table for order d."""
+    path = os.path.join(_DATA, f"fc_tables_d{d}.txt")
+    cs = []
+    with open(path) as f:
+        prev = None
+        for ln in f:
+            ln = ln.strip()
+            if prev == f"d {d}" and ln.startswith("C "):
+                cs.append(int(ln.split()[1]))
+            prev = ln
+    return min(cs), max(cs)
+
+
+def transform_cost(L):
+    """Cost rule of policy 2: L split greedily into factors 8, 4, 2, 3, 5, 7; each
+    stage of radix R costs (L/R) B(R) with B(2, 4, 8, 3, 5, 7) = (4, 16, 52, 14, 36, 66),
+    plus 4 (L/R)(R-1) on every stage except the last. None if a prime factor exceeds 7."""
+    B = {2: 4, 4: 16, 8: 52, 3: 14, 5: 36, 7: 66}
+    radices = []
+    m = L
+    for r in (8, 4, 2, 3, 5, 7):
+        while m % r == 0:
+            radices.append(r)
+            m //= r
+    if m != 1:
+        return None
+    total = 0
+    for i, r in enumerate(radices):
+        total += (L // r) * B[r]
+        if i < len(radices) - 1:
+            total += 4 * (L // r) * (r - 1)
+    return total
+
+
+def choose_C(N, C0, policy, d=5):
+    """Continuation length for a line of N points (the paper leaves C free, Sec. 2.2).
 
     policy 0: C = C0 for every line (the paper uses one C per run).
-    policy 1: smallest C >= C0 with N + C having no prime factor above 7
-    (a reading of the free parameter C; see the design notes)."""
+    policy 1: smallest C >= C0 with N + C having no prime factor above 7.
+    policy 2: among C0 <= C <= (largest tabulated C), the C whose N + C has the
+    smallest transform_cost, ties to the smaller C; policy 1 if none qualifies."""
     if policy == 0:
         return C0
+    if policy == 2:
+        best = None
+        for C in range(C0, table_range(d)[1] + 1):
+            k = transform_cost(N + C)
+            if k is not None and (best is None or k < best[0]):
+                best = (k, C)
+        if best is not None:
+            return best[1]
     C = C0
     while not is_7smooth(N + C):
         C += 1

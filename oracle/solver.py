@@ -80,7 +80,7 @@ class Solver:
             if per:
                 out[..., rows, a:a + n] = fc.periodic_derivative(lines, g.h1)
             elif n >= 2 * d:
-                out[..., rows, a:a + n] = fc.fc_derivative(lines, g.h1, d, fc.choose_C(n, C0, pol))
+                out[..., rows, a:a + n] = fc.fc_derivative(lines, g.h1, d, fc.choose_C(n, C0, pol, d))
         return out
 
     def d2(self, g, F):
@@ -93,7 +93,7 @@ class Solver:
         for (a, n), cols in groups.items():
             cols = np.array(cols)
             if n >= 2 * d:
-                out[..., cols, a:a + n] = fc.fc_derivative(Ft[..., cols, a:a + n], g.h2, d, fc.choose_C(n, C0, pol))
+                out[..., cols, a:a + n] = fc.fc_derivative(Ft[..., cols, a:a + n], g.h2, d, fc.choose_C(n, C0, pol, d))
         return np.swapaxes(out, -1, -2)
 
     # ---- eq. (semi-discrete) ------------------------------------------------------------
@@ -153,11 +153,11 @@ class Solver:
             if per:
                 G[:, j, s:s + n] = fc.periodic_filter(F[:, j, s:s + n], a, p)
             elif n >= 2 * d:
-                G[:, j, s:s + n] = fc.fc_filter(F[:, j, s:s + n], d, fc.choose_C(n, C0, pol), a, p)
+                G[:, j, s:s + n] = fc.fc_filter(F[:, j, s:s + n], d, fc.choose_C(n, C0, pol, d), a, p)
         H = G.copy()
         for (i, s, n, per) in g.seg2:
             if n >= 2 * d:
-                H[:, s:s + n, i] = fc.fc_filter(G[:, s:s + n, i], d, fc.choose_C(n, C0, pol), a, p)
+                H[:, s:s + n, i] = fc.fc_filter(G[:, s:s + n, i], d, fc.choose_C(n, C0, pol, d), a, p)
         out = np.stack([H[0], H[1], H[2], euler.energy_from_theta(H[0], H[1], H[2], H[3], gam)])
         return np.where(g.blank[None], e, out)
 
@@ -235,7 +235,7 @@ def smear_initial(solver, states, x_disc, direction=1):
             out.append(e)
             continue
         F = np.stack([e[0], e[1], e[2], euler.temperature(e, gam)])
-        C = fc.choose_C(g.n1, prm.C0, prm.c_policy)
+        C = fc.choose_C(g.n1, prm.C0, prm.c_policy, prm.d)
         Ff = fc.fc_filter(F, prm.d, C, 10.0, 2)
         w = viscosity.window_weight((g.x - x_disc) / h, 18, 9)
         G = w[None] * Ff + (1.0 - w[None]) * F

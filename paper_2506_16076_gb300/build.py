@@ -1,6 +1,6 @@
 """Compile the CUDA library libfcsdnn.so in-tree for sm_103a (nvcc, no cmake).
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_2506_16076_gb300/_lib/libfcsdnn.so, which the binding loads.
 """
 import os
@@ -15,6 +15,9 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libfcsdnn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+# extra nvcc flags for tuning builds, e.g. FCSDNN_NVCC_FLAGS="-DFC_LINE_MAXNREG=96"
+EXTRA = os.environ.get("FCSDNN_NVCC_FLAGS", "").split()
+STAMP = os.path.join(OUT, "flags.txt")
 SOURCES = ["fc_kernels.cu", "fc_host.cpp", "fc_noalloc.cu"]
 
 
@@ -35,14 +38,20 @@ def _newer(target, deps):
 def build(force=False, verbose=False):
     os.makedirs(OUT, exist_ok=True)
     deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(HERE, "..", "include", "fcsdnn.h")]
-    if not force and _newer(LIB, deps):
+    flags_now = " ".join(ARCH + FLAGS + EXTRA)
+    try:
+        with open(STAMP) as f:
+            same_flags = f.read() == flags_now
+    except OSError:
+        same_flags = False
+    if not force and same_flags and _newer(LIB, deps):
         return LIB
     cc = nvcc()
     objs = []
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(SRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -57,6 +66,8 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(flags_now)
     return LIB
 
 

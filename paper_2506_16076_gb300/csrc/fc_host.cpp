@@ -410,6 +410,54 @@ bool smooth7(int n) {
   return n == 1;
 }
 
+// Estimated FP64 operations of one in-place transform of length L: L factored greedily
+// into 8s, 4s, 2s, 3s, 5s, 7s (the order of the plans), L/R butterflies of radix R per
+// stage at B(R) operations (B = 4, 16, 52 for R = 2, 4, 8; 14, 36, 66 for R = 3, 5, 7)
+// and 4 operations per twiddled element, (R - 1) L / R of them, on every stage but the
+// last. -1 when L has a prime factor above 7.
+long long fft_cost(int L) {
+  std::vector<int> f;
+  int m = L;
+  for (int r : {8, 4, 2, 3, 5, 7})
+    while (m % r == 0) {
+      f.push_back(r);
+      m /= r;
+    }
+  if (m != 1) return -1;
+  long long cost = 0;
+  for (size_t s = 0; s < f.size(); ++s) {
+    const int R = f[s];
+    const int B = R == 2 ? 4 : R == 4 ? 16 : R == 8 ? 52 : R == 3 ? 14 : R == 5 ? 36 : 66;
+    cost += (long long)(L / R) * B;
+    if (s + 1 < f.size()) cost += 4LL * (L / R) * (R - 1);
+  }
+  return cost;
+}
+
+// Continuation length C of a non-periodic line of N points (the paper leaves C free):
+//   policy 0: C0 on every line;
+//   policy 1: the smallest C >= C0 with N + C 7-smooth;
+//   policy 2: the C in [C0, Cmax] whose continued length has the smallest fft_cost
+//             (ties to the smaller C); policy 1 if none is 7-smooth.
+int choose_continuation(int N, const fc_params& prm, int Cmax) {
+  if (prm.c_policy == 0) return prm.C0;
+  if (prm.c_policy == 2) {
+    int best = -1;
+    long long best_cost = 0;
+    for (int C = prm.C0; C <= Cmax; ++C) {
+      const long long k = fft_cost(N + C);
+      if (k >= 0 && (best < 0 || k < best_cost)) {
+        best = C;
+        best_cost = k;
+      }
+    }
+    if (best >= 0) return best;
+  }
+  int C = prm.C0;
+  while (!smooth7(N + C)) ++C;
+  return C;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- context build
@@ -506,13 +554,7 @@ struct Builder {
     return off;
   }
 
-  int choose_C(int N) {
-    const fc_params& prm = c->prm;
-    if (prm.c_policy == 0) return prm.C0;
-    int C = prm.C0;
-    while (!smooth7(N + C)) ++C;
-    return C;
-  }
+  int choose_C(int N) { return choose_continuation(N, c->prm, c->Cmax); }
 };
 
 void make_queue(fc_ctx* c, fc_ctx::Queue& q, std::vector<Job>& jobs, const std::vector<Plan>& plans, int npatch,
@@ -1441,18 +1483,13 @@ fc_status fc_pass_stats(const fc_ctx* c, const char* pass, double* flops, double
     if (want1)
       for (const Seg& s : h.seg1) {
         if (!s.periodic && s.n < 2 * c->prm.d) continue;
-        int C = 0;
-        if (!s.periodic) {
-          C = c->prm.C0;
-          if (c->prm.c_policy) while (!smooth7(s.n + C)) ++C;
-        }
+        const int C = s.periodic ? 0 : choose_continuation(s.n, c->prm, c->Cmax);
         add_line(s.n, s.n + C, C);
       }
     if (want2)
       for (const Seg& s : h.seg2) {
         if (s.n < 2 * c->prm.d) continue;
-        int C = c->prm.C0;
-        if (c->prm.c_policy) while (!smooth7(s.n + C)) ++C;
+        const int C = choose_continuation(s.n, c->prm, c->Cmax);
         add_line(s.n, s.n + C, C);
       }
   }

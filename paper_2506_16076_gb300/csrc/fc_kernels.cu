@@ -16,6 +16,15 @@
 
 namespace fcx {
 
+// Register budget of the line kernels: by default the compiler may use up to 255
+// registers per thread for a 256-thread CTA; FC_LINE_MAXNREG (a build flag) caps it
+// instead, trading a few spills for more resident warps per SM.
+#ifdef FC_LINE_MAXNREG
+#define LINE_KERNEL_BOUNDS __maxnreg__(FC_LINE_MAXNREG)
+#else
+#define LINE_KERNEL_BOUNDS __launch_bounds__(MAXW * 32)
+#endif
+
 // Warps per CTA of the line kernels. Each warp owns one line at a time and the warps of
 // a CTA never synchronise with each other, so small CTAs let the block scheduler hand a
 // freed warp slot the next line at once (lines differ in length and in the number of
@@ -137,7 +146,7 @@ __device__ __forceinline__ void stage_write(const StageCoef& sc, long long p, lo
 
 // ---------------------------------------------------------------- affine patches, q1 lines
 // d/dx of e -> H_x = f_x(e) - mu d/dx e -> R1 = d/dx H_x  (J11 folded into J.scale = 1/hx)
-__global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+__global__ void LINE_KERNEL_BOUNDS k_cart_q1(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                         const double* __restrict__ e, const double* __restrict__ mu,
                                                         double* __restrict__ R1) {
   extern __shared__ double2 sm[];
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_cart_q1(DevTables T, const Job* _
 
 // ---------------------------------------------------------------- affine patches, q2 lines
 // d/dy of e -> H_y -> R2 = d/dy H_y; L = -(R1 + R2) (0 on PT_NODIFF points); stage combination.
-__global__ void __launch_bounds__(MAXW * 32) k_cart_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+__global__ void LINE_KERNEL_BOUNDS k_cart_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                         const double* __restrict__ mu, const double* __restrict__ R1,
                                                         StageCoef sc) {
   extern __shared__ double2 sm[];
@@ -246,7 +255,7 @@ __device__ __forceinline__ const double* gslot(const double* G, long long Pg, in
 }
 
 // pass A: D1e = d/dq1 e
-__global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+__global__ void LINE_KERNEL_BOUNDS k_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                       const double* __restrict__ e, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_A(DevTables T, const Job* __r
 
 // pass B: D2e; grad_x e = J1x D1 + J2x D2, grad_y e = J1y D1 + J2y D2; H_x, H_y;
 // R2 = J2x d/dq2 H_x + J2y d/dq2 H_y
-__global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+__global__ void LINE_KERNEL_BOUNDS k_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                       const double* __restrict__ e, const double* __restrict__ mu,
                                                       const double* __restrict__ Jm, double* __restrict__ G) {
   extern __shared__ double2 sm[];
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_gen_B(DevTables T, const Job* __r
 }
 
 // pass C: R1 = J1x d/dq1 H_x + J1y d/dq1 H_y; L = -(R1 + R2); stage combination
-__global__ void __launch_bounds__(MAXW * 32) k_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+__global__ void LINE_KERNEL_BOUNDS k_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                       const double* __restrict__ Jm, double* __restrict__ G,
                                                       StageCoef sc) {
   extern __shared__ double2 sm[];
@@ -459,7 +468,7 @@ __device__ __forceinline__ void filter2(double2* A, int Lmax, const Job& J, cons
   fft_inplace<true>(A, P, 2, T.tw, lane, 32);
 }
 
-__global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_filter_q1(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ e,
                                                           double* __restrict__ F) {
   extern __shared__ double2 sm[];
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_filter_q1(DevTables T, const Job*
   }
 }
 
-__global__ void __launch_bounds__(MAXW * 32) k_filter_q2(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_filter_q2(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ F,
                                                           double* __restrict__ e) {
   extern __shared__ double2 sm[];
@@ -883,7 +892,7 @@ __device__ __forceinline__ void load4_masked(double2* A, int L, const Job& J, co
 
 // affine patches, pass 1 (q1 lines): R1 = A_x^T eta_x - D_x^T(mu eta_x), eta_x = -D_x^T (N psi)
 // pass 2 (q2 lines): acc += dt (R1 + A_y^T eta_y - D_y^T(mu eta_y))
-__global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_adj_cart(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                          int Lmax, int dir, const double* __restrict__ u,
                                                          const double* __restrict__ mu, const double* __restrict__ psi,
                                                          double* __restrict__ R1, double* __restrict__ acc,
@@ -940,7 +949,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_cart(DevTables T, const Job* 
 
 // curvilinear patches. scratch G slots: 0 = S1x then eta_x, 1 = S1y, 2 = partial, 3 = g1
 // pass A (q1): S1x = D_1^T(J1x N psi), S1y = D_1^T(J1y N psi)
-__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_adj_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ Jm,
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
@@ -974,7 +983,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_A(DevTables T, const Job*
 
 // pass B (q2): eta_x = -(S1x + D_2^T(J2x N psi)), eta_y = -(S1y + D_2^T(J2y N psi));
 // partial = A_x^T eta_x + A_y^T eta_y - D_2^T(mu (J2x eta_x + J2y eta_y)); g1 = mu (J1x eta_x + J1y eta_y)
-__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ Jm,
                                                           const double* __restrict__ u, const double* __restrict__ mu,
                                                           const double* __restrict__ psi, double* __restrict__ G) {
@@ -1041,7 +1050,7 @@ __global__ void __launch_bounds__(MAXW * 32) k_adj_gen_B(DevTables T, const Job*
 }
 
 // pass C (q1): acc += dt (partial - D_1^T(g1))
-__global__ void __launch_bounds__(MAXW * 32) k_adj_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ G,
                                                           double* __restrict__ acc, const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];

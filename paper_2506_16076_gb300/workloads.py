@@ -48,7 +48,8 @@ class PatchDesc:
 class Params:
     d: int = 5
     C0: int = 27
-    c_policy: int = 0  # 0: C = C0 on every line; 1: smallest C >= C0 with N+C 7-smooth
+    c_policy: int = 0  # 0: C = C0 on every line; 1: smallest C >= C0 with N+C 7-smooth;
+    #                    2: C in [C0, largest tabulated C] with the cheapest transform of N+C
     gamma: float = GAMMA
     alpha_f: float = 10.0
     p_f: int = 14
@@ -142,7 +143,7 @@ def cyl_m3(scale=1.0):
     og = _ogrid(int(round(512 * scale)), int(round(96 * scale)), 0.5, 1.5, fs)
     cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, nc, 10, fs, hole=(0.0, 0.0, 1.0))
     return Workload("cyl_m3" if scale == 1.0 else f"cyl_m3_x{scale}", [og] + cart,
-                    Params(d=5, C0=27, c_policy=1), freestream=fs, init="freestream", steps=2000)
+                    Params(d=5, C0=27, c_policy=2), freestream=fs, init="freestream", steps=2000)
 
 
 def cyl_m2_half():
@@ -150,7 +151,7 @@ def cyl_m2_half():
     fs = (1.4, 2.0 * math.cos(a), 2.0 * math.sin(a), 1.0)
     og = _ogrid(256, 48, 0.5, 1.5, fs)
     cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, 80, 10, fs, hole=(0.0, 0.0, 1.0))
-    return Workload("cyl_m2_half", [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs,
+    return Workload("cyl_m2_half", [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs,
                     init="freestream", steps=400, extra={"mach": 2.0, "alpha_deg": 2.0})
 
 
@@ -171,7 +172,7 @@ def cyl_m25_array(nx, nmin, nmax, seed, taper, nth, nr, name):
     sizes = seeded_sizes(nx, nx, nmin, nmax, seed, -8.0, 16.0, -12.0, 12.0, taper)
     og = _ogrid(nth, nr, 0.5, 1.5, fs)
     cart = _cart_array(nx, nx, -8.0, 16.0, -12.0, 12.0, None, 19, fs, hole=(0.0, 0.0, 1.0), sizes=sizes)
-    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs, init="potential", steps=200,
+    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs, init="potential", steps=200,
                     extra={"taper": taper, "seed": seed, "cyl_radius": 0.5, "cutoff": 3.0})
 
 
@@ -190,7 +191,7 @@ def small_multipatch():
     fs = (1.4, 3.0, 0.0, 1.0)
     og = _ogrid(128, 32, 0.5, 1.5, fs)
     cart = _cart_array(2, 2, -2.5, 2.5, -2.5, 2.5, 64, 10, fs, hole=(0.0, 0.0, 0.85))
-    return Workload("small_multipatch", [og] + cart, Params(d=5, C0=27, c_policy=1), freestream=fs,
+    return Workload("small_multipatch", [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs,
                     init="freestream", steps=20)
 
 

@@ -133,3 +133,23 @@ def test_choose_C_policies():
         assert 27 <= C <= 71 and fc.is_7smooth(N + C)
         assert all(not fc.is_7smooth(N + c) for c in range(27, C))
     assert fc.choose_C(160, 27, 1) == 29  # 189 = 3^3 7
+
+
+def test_choose_C_policies():
+    # policy 1: smallest C >= 27 with N + C free of primes above 7
+    assert fc.choose_C(160, 27, 1) == 29  # 189 = 3^3 7
+    assert fc.choose_C(128, 27, 1) == 32  # 160
+    # policy 2, worked by hand from the stated cost rule: N = 160 -> 189 = 3.3.3.7 costs
+    # 3 (63 * 14) + 27 * 66 + 3 * 4 * 189 * 2/3 = 5940; 192 = 8.8.3 costs
+    # 2 (24 * 52) + 64 * 14 + 2 * 4 * 24 * 7 = 4736, the least over C = 27..71
+    assert fc.transform_cost(189) == 5940 and fc.transform_cost(192) == 4736
+    assert fc.choose_C(160, 27, 2) == 32
+    assert fc.transform_cost(187) is None  # 11 x 17
+    assert fc.choose_C(48, 27, 2) == 32  # 80 = 8.2.5
+    assert fc.choose_C(384, 27, 2) == 64  # 448 = 8.8.7
+    lo, hi = fc.table_range(5)
+    assert (lo, hi) == (27, 71)
+    for n in range(10, 600, 7):
+        C = fc.choose_C(n, 27, 2)
+        assert lo <= C <= hi and fc.transform_cost(n + C) == min(
+            fc.transform_cost(n + c) for c in range(27, hi + 1) if fc.transform_cost(n + c) is not None)
