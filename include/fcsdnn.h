@@ -50,8 +50,20 @@ typedef enum {
 
 /* patch kinds (Sec. 3.1): affine box (C/I-type), annulus around an obstacle with a periodic angle */
 enum { FC_PATCH_AFFINE = 0, FC_PATCH_OGRID = 1 };
-/* side types, side order (q1=0, q1=1, q2=0, q2=1) (Sec. 3.4 internal/external sides, Sec. 4.2) */
-enum { FC_SIDE_INTERNAL = 0, FC_SIDE_DIRICHLET = 1, FC_SIDE_SLIPWALL = 2, FC_SIDE_OUTFLOW = 3, FC_SIDE_PERIODIC = 4 };
+/* side types, side order (q1=0, q1=1, q2=0, q2=1) (Sec. 3.4 internal/external sides, Sec. 4.2).
+ * SLIPWALL: the wall-normal momentum is set to 0 at every stage.
+ * ADIABATIC: no-slip adiabatic wall (Sec. 4.2, Remarks adiabatic_th and adiabatic): both
+ *   momenta are set to 0 and the wall temperature is the value at the wall of the
+ *   degree d-1 polynomial through the temperatures of the d-1 next points inward with
+ *   zero normal derivative at the wall (the Neumann FC end data); E follows from it. */
+enum {
+  FC_SIDE_INTERNAL = 0,
+  FC_SIDE_DIRICHLET = 1,
+  FC_SIDE_SLIPWALL = 2,
+  FC_SIDE_OUTFLOW = 3,
+  FC_SIDE_PERIODIC = 4,
+  FC_SIDE_ADIABATIC = 5
+};
 
 /* One patch (Sec. 3.1-3.2). AFFINE: geom = (x0, x1, y0, y1), q1 -> x, q2 -> y.
  * OGRID: geom = (xc, yc, r0, r1), q1 -> angle (periodic, n1 points), q2 -> radius.
@@ -139,22 +151,26 @@ fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, do
  * and the exchange. mu_dev: P doubles, written (or read with FROZEN_MU). */
 fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
 
-/* Discrete adjoint of one fc_rk_step with mu and dt frozen and no filter (the
- * smoothness classifier is not differentiable, so the viscosity of the forward step
- * is held fixed): lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev for the step that
- * starts from e_n_dev with viscosity mu_dev (P doubles) and step *dt_dev (device
- * scalar). The stage states are recomputed from e_n_dev. Transposes: FC derivative
- * (zero padding, negated spectral derivative, continuation folded back onto the
- * 2d end points), flux Jacobians, viscous term with mu fixed, inter-patch exchange
+/* Discrete adjoint of one fc_rk_step with mu and dt frozen (the smoothness
+ * classifier is not differentiable, so the viscosity of the forward step is held
+ * fixed): lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev for the step that starts from
+ * e_n_dev with viscosity mu_dev (P doubles) and step *dt_dev (device scalar). flags:
+ * FC_STEP_FILTER when the forward step applied the per-step filter (Sec. 4.3.1); other
+ * bits are ignored. The stage states are recomputed from e_n_dev. Transposes: FC
+ * derivative (zero padding, negated spectral derivative, continuation folded back onto
+ * the 2d end points), flux Jacobians, viscous term with mu fixed, inter-patch exchange
  * (donors gather the receivers' adjoint with the interpolation weights), boundary
- * overwrite. gbc_dev (nullable, [4][P]) accumulates the adjoint that reaches the
- * Dirichlet points, i.e. the sensitivity of the step result to the imposed states.
- * The first call allocates 11 state-sized device buffers. */
+ * overwrite, adiabatic walls (linearised at the stage state), and the filter
+ * (linearised at the state it was applied to: theta and E rebuild Jacobians around
+ * the line filters, whose transposes fold the continuation back like the derivative's).
+ * gbc_dev (nullable, [4][P]) accumulates the adjoint that reaches the Dirichlet
+ * points, i.e. the sensitivity of the step result to the imposed states. The first
+ * call allocates 11 state-sized device buffers, and 2 more with the filter. */
 fc_status fc_adjoint_step(fc_ctx *ctx, const double *e_n_dev, const double *mu_dev, const double *dt_dev,
-                          const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, void *stream);
+                          const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, int flags, void *stream);
 
 /* Wall-pressure drag functional J = sum over the wall ring of the first curvilinear
- * patch with a slip wall of p n_x r0 dtheta (periodic trapezoid of the integral of
+ * patch with a slip or adiabatic wall of p n_x r0 dtheta (periodic trapezoid of the integral of
  * wall pressure times n_x, n the outward body normal); J_dev: device scalar.
  * dJde_dev (nullable, [4][P]): dJ/de, zero off the wall. */
 fc_status fc_drag(fc_ctx *ctx, const double *e_dev, double *J_dev, double *dJde_dev, void *stream);

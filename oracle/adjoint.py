@@ -142,14 +142,106 @@ def bc_T(sv, lams, gbc=None):
     return out
 
 
-def project_T(sv, lams, gbc=None):
-    """P = exchange o bc  =>  P^T = bc^T o exchange^T."""
-    return bc_T(sv, exchange_T(sv, lams), gbc)
+def wall_T(sv, lams, states):
+    """Transpose of the linearised no-slip adiabatic wall condition at the state it was
+    applied to (the wall density and the inward points are not changed by it):
+    E_w = rho_w theta_w / (gamma - 1), theta_w = sum_j w_j theta(e_j), momenta set to 0."""
+    from . import euler
+    from .solver import _side_slice, _inward_slice, adiabatic_weights
+    gam = sv.prm.gamma
+    g1 = gam - 1.0
+    out = [l.copy() for l in lams]
+    for k, (g, lam) in enumerate(zip(sv.geos, out)):
+        side = g.desc.side
+        e = states[k]
+        for s in range(4):
+            if side[s] != W.ADIABATIC:
+                continue
+            sl = _side_slice(s)
+            live = ~g.blank[sl]
+            w = adiabatic_weights(sv.prm.d)
+            lamE = np.where(live, lam[3][sl], 0.0)
+            rho_w = e[0][sl]
+            th_w = sum(wj * euler.temperature(e[(slice(None),) + _inward_slice(s, j + 1)], gam) for j, wj in enumerate(w))
+            for c in (1, 2, 3):
+                lam[c][sl] = np.where(live, 0.0, lam[c][sl])
+            lam[0][sl] = lam[0][sl] + lamE * th_w / g1
+            for j, wj in enumerate(w):
+                isl = _inward_slice(s, j + 1)
+                r, mx, my, E = (e[c][isl] for c in range(4))
+                gcoef = lamE * rho_w / g1 * wj
+                lam[0][isl] = lam[0][isl] + gcoef * g1 * (-E / r ** 2 + (mx * mx + my * my) / r ** 3)
+                lam[1][isl] = lam[1][isl] + gcoef * (-g1 * mx / r ** 2)
+                lam[2][isl] = lam[2][isl] + gcoef * (-g1 * my / r ** 2)
+                lam[3][isl] = lam[3][isl] + gcoef * (g1 / r)
+    return out
 
 
-def step_forward(sv, e_n, mu, dt):
-    """The differentiated step (mu, dt frozen, no filter); returns the stage states u_0..u_5."""
-    u = [sv.project([a.copy() for a in e_n])]
+def project_T(sv, lams, gbc=None, states=None):
+    """P = exchange o wall o bc  =>  P^T = bc^T o wall^T o exchange^T; the wall term needs
+    the state at which P was applied (states, any time the walls are adiabatic)."""
+    lam = exchange_T(sv, lams)
+    if any(W.ADIABATIC in g.desc.side for g in sv.geos):
+        lam = wall_T(sv, lam, states)
+    return bc_T(sv, lam, gbc)
+
+
+def filter_T(sv, lams, states):
+    """Transpose of the linearised per-step filter (Sec. 4.3.1) at the state it was applied
+    to: Q = (rho, rho u, rho v, theta(e)) is filtered along q1 lines, then q2 lines, and E
+    is rebuilt from the filtered Q (eq. perfect_gas_T); blanked points are unchanged."""
+    from . import euler
+    prm = sv.prm
+    gam, a, pf, d = prm.gamma, prm.alpha_f, prm.p_f, prm.d
+    g1 = gam - 1.0
+    out = []
+    for g, lam, e in zip(sv.geos, lams, states):
+        Fq = np.stack([e[0], e[1], e[2], euler.temperature(e, gam)])
+        # forward values: G after q1, H after q2
+        H = sv.filter_patch(g, e)
+        r2, m2, n2 = H[0], H[1], H[2]
+        th2 = euler.temperature(H, gam)
+        # E' = r th/(g-1) + (m^2 + n^2)/(2 r): adjoint of the rebuild
+        mu = np.stack([lam[0] + lam[3] * (th2 / g1 - 0.5 * (m2 * m2 + n2 * n2) / r2 ** 2),
+                       lam[1] + lam[3] * m2 / r2,
+                       lam[2] + lam[3] * n2 / r2,
+                       lam[3] * r2 / g1])
+        # q2 lines (transposed), then q1 lines
+        muG = mu.copy()
+        for (i, s, n, per) in g.seg2:
+            if n >= 2 * d:
+                muG[:, s:s + n, i] = fc_filter_T_lines(mu[:, s:s + n, i], d, fc.choose_C(n, prm.C0, prm.c_policy, d), a, pf)
+        muQ = muG.copy()
+        for (j, s, n, per) in g.seg1:
+            if per:
+                muQ[:, j, s:s + n] = fc.periodic_filter(muG[:, j, s:s + n], a, pf)
+            elif n >= 2 * d:
+                muQ[:, j, s:s + n] = fc_filter_T_lines(muG[:, j, s:s + n], d, fc.choose_C(n, prm.C0, prm.c_policy, d), a, pf)
+        # Q_theta = theta(e): adjoint through theta = (g-1)(E/r - (m^2+n^2)/(2 r^2))
+        r, m, n_, E = e
+        lt = muQ[3]
+        res = np.stack([muQ[0] + lt * g1 * (-E / r ** 2 + (m * m + n_ * n_) / r ** 3),
+                        muQ[1] + lt * (-g1 * m / r ** 2),
+                        muQ[2] + lt * (-g1 * n_ / r ** 2),
+                        lt * g1 / r])
+        out.append(np.where(g.blank[None], lam, res))
+    return out
+
+
+def fc_filter_T_lines(G, d, C, a, pf):
+    return fc.fc_filter_T(G, d, C, a, pf)
+
+
+def filter_jvp_complex(sv, u, v, h=1e-30):
+    z = [x + 1j * h * y for x, y in zip(u, v)]
+    return [np.imag(a) / h for a in sv.filter(z)]
+
+
+def step_forward(sv, e_n, mu, dt, filt=False):
+    """The differentiated step (mu, dt frozen; the per-step filter if filt); returns the
+    stage states u_0..u_5 and, with the filter, the projected state it was applied to."""
+    pre = sv.project([a.copy() for a in e_n])
+    u = [sv.project(sv.filter(pre)) if filt else pre]
     Ls = {}
     for i in range(5):
         new = []
@@ -164,12 +256,15 @@ def step_forward(sv, e_n, mu, dt):
                     acc = acc + SSP54_BETA[i][k] * dt * Ls[k][p]
             new.append(acc)
         u.append(sv.project(new))
-    return u
+    return (u, pre) if filt else u
 
 
-def step_adjoint(sv, e_n, mu, dt, lam_np1):
+def step_adjoint(sv, e_n, mu, dt, lam_np1, filt=False):
     """lam_n = (d e_{n+1}/d e_n)^T lam_{n+1} and the Dirichlet sensitivity of the step."""
-    u = step_forward(sv, e_n, mu, dt)
+    if filt:
+        u, pre = step_forward(sv, e_n, mu, dt, filt=True)
+    else:
+        u = step_forward(sv, e_n, mu, dt)
     npch = len(sv.geos)
     gbc = [np.zeros_like(a) for a in e_n]
     lam_u = [[np.zeros_like(a) for a in e_n] for _ in range(6)]
@@ -179,7 +274,7 @@ def step_adjoint(sv, e_n, mu, dt, lam_np1):
         if any(np.any(x) for x in psi[i]):
             add = rhs_adjoint(sv, u[i], mu, psi[i])
             lam_u[i] = [a + dt * b for a, b in zip(lam_u[i], add)]
-        lam_v = project_T(sv, lam_u[i], gbc)
+        lam_v = project_T(sv, lam_u[i], gbc, u[i])
         for k in range(i):
             al, be = SSP54_ALPHA[i - 1][k], SSP54_BETA[i - 1][k]
             for p in range(npch):
@@ -189,14 +284,16 @@ def step_adjoint(sv, e_n, mu, dt, lam_np1):
                     psi[k][p] = psi[k][p] + be * lam_v[p]
     add = rhs_adjoint(sv, u[0], mu, psi[0])
     lam_u[0] = [a + dt * b for a, b in zip(lam_u[0], add)]
-    lam_n = project_T(sv, lam_u[0], gbc)
+    lam_n = project_T(sv, lam_u[0], gbc, u[0])
+    if filt:
+        lam_n = project_T(sv, filter_T(sv, lam_n, pre), gbc, pre)
     return lam_n, gbc
 
 
-def step_jvp_complex(sv, e_n, mu, dt, v, h=1e-30):
+def step_jvp_complex(sv, e_n, mu, dt, v, h=1e-30, filt=False):
     """Directional derivative of the frozen step by the complex step: Im(step(e + i h v)) / h."""
     z = [a + 1j * h * b for a, b in zip(e_n, v)]
-    out = step_forward(sv, z, mu, dt)[5]
+    out = (step_forward(sv, z, mu, dt, filt=True)[0] if filt else step_forward(sv, z, mu, dt))[5]
     return [np.imag(a) / h for a in out]
 
 
@@ -215,7 +312,7 @@ def wall_drag(sv, states):
     (periodic trapezoid of the integral of wall pressure times n_x, outward body normal)."""
     from . import euler
     for g, e in zip(sv.geos, states):
-        if g.kind == W.OGRID and g.desc.side[2] == W.SLIPWALL:
+        if g.kind == W.OGRID and g.desc.side[2] in (W.SLIPWALL, W.ADIABATIC):
             r0 = g.desc.geom[2]
             p = euler.primitives(e[:, 0, :], sv.prm.gamma)[3]
             return np.sum(p * g.cos[0]) * r0 * 2 * np.pi / g.n1
@@ -228,7 +325,7 @@ def wall_drag_grad(sv, states):
     out = [np.zeros_like(e) for e in states]
     gam = sv.prm.gamma
     for k, (g, e) in enumerate(zip(sv.geos, states)):
-        if g.kind == W.OGRID and g.desc.side[2] == W.SLIPWALL:
+        if g.kind == W.OGRID and g.desc.side[2] in (W.SLIPWALL, W.ADIABATIC):
             r0 = g.desc.geom[2]
             rho, m, n, E = e[:, 0, :]
             w = g.cos[0] * r0 * 2 * np.pi / g.n1

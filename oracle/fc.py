@@ -265,6 +265,21 @@ def fc_derivative_T(G, h, d, C):
 
 
 @_real_linear
+def fc_filter_T(G, d, C, alpha, p):
+    """Transpose of fc_filter: extend^T o (spectral filter) o zero-padding. The filter
+    multiplier is real and even in k, so the filter on the period is a symmetric circulant."""
+    N = G.shape[-1]
+    Z = np.concatenate([np.asarray(G).astype(LD), np.zeros(G.shape[:-1] + (C,), LD)], axis=-1)
+    W = spectral_filter(Z, alpha, p)
+    Q, AL, AR = load_tables(d, C)
+    out = W[..., :N].copy()
+    ext = W[..., N:]
+    out[..., :d] += (ext @ AL.astype(LD)) @ Q.T.astype(LD)
+    out[..., N - d:] += (ext @ AR.astype(LD)) @ Q.T.astype(LD)
+    return out.astype(np.float64)
+
+
+@_real_linear
 def periodic_derivative_T(G, h):
     """Transpose of the periodic Fourier derivative: its negative (skew-symmetric circulant)."""
     return -periodic_derivative(G, h)

@@ -20,6 +20,8 @@ and is followed by the boundary overwrite and the exchange; every step starts
 by applying the boundary overwrite and the exchange to its input (idempotent
 on a consistent state); slip walls zero the wall-normal momentum.
 """
+import functools
+
 import numpy as np
 
 from paper_2506_16076_gb300 import workloads as W
@@ -135,6 +137,17 @@ class Solver:
                 val = euler.cons_from_prim(*[np.float64(v) for v in g.desc.bc[s]], gam)
                 for k in range(4):
                     e[k][sl] = np.where(g.blank[sl], e[k][sl], val[k])
+            for s in range(4):
+                if side[s] != W.ADIABATIC:
+                    continue
+                # no-slip adiabatic wall (Sec. 4.2, Remarks adiabatic_th and adiabatic)
+                sl = _side_slice(s)
+                th_w = sum(wj * euler.temperature(e[(slice(None),) + _inward_slice(s, j + 1)], gam)
+                           for j, wj in enumerate(adiabatic_weights(self.prm.d)))
+                keep = g.blank[sl]
+                e[1][sl] = np.where(keep, e[1][sl], 0.0)
+                e[2][sl] = np.where(keep, e[2][sl], 0.0)
+                e[3][sl] = np.where(keep, e[3][sl], e[0][sl] * th_w / (gam - 1.0))
         return states
 
     def project(self, states):
@@ -216,6 +229,32 @@ class Solver:
 
 def _side_slice(s):
     return [(slice(None), 0), (slice(None), -1), (0, slice(None)), (-1, slice(None))][s]
+
+
+def _inward_slice(s, j):
+    """Grid points j steps inward from side s (along the wall-normal grid lines)."""
+    return [(slice(None), j), (slice(None), -1 - j), (j, slice(None)), (-1 - j, slice(None))][s]
+
+
+@functools.lru_cache(maxsize=None)
+def adiabatic_weights(d):
+    """Weights w_1..w_{d-1} with sum_j w_j theta_j = p(0) for the polynomial p of degree
+    d-1 with p'(0) = 0 and p(j) = theta_j, j = 1..d-1 (unit spacing): the wall value of
+    the Neumann FC end data (Sec. 2.2, Remark adiabatic). Exact rational elimination."""
+    from fractions import Fraction
+    m = d - 1
+    powers = [0] + list(range(2, d))  # p'(0) = 0 removes the linear term
+    A = [[Fraction(j) ** k for k in powers] + [Fraction(int(r == j)) for r in range(1, d)] for j in range(1, d)]
+    for col in range(m):  # Gauss-Jordan on [A | I]
+        piv = next(r for r in range(col, m) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        pv = A[col][col]
+        A[col] = [x / pv for x in A[col]]
+        for r in range(m):
+            if r != col and A[r][col] != 0:
+                f = A[r][col]
+                A[r] = [x - f * y for x, y in zip(A[r], A[col])]
+    return tuple(float(x) for x in A[0][m:])  # row of a_0 in the inverse
 
 
 # ---- Sec. 4.3.2: localised smearing of discontinuous initial data ----------------------------

@@ -2,10 +2,12 @@
 
 The differentiated map is a sequence of fc_rk_step calls with the viscosity and
 the time step of each step frozen at their forward values (the smoothness
-classifier is not differentiable) and no filter. The forward run stores the
-state every K steps; the backward run recomputes each segment of K states from
-its checkpoint (fc_rk_step with FROZEN_MU | FIXED_DT, replaying the recorded
-mu and dt) and applies fc_adjoint_step backwards through the segment.
+classifier is not differentiable); with filter=True the per-step filter runs on
+steps n >= 1 as in a plain run (Sec. 4.3.1) and is differentiated too. The forward
+run stores the state every K steps; the backward run recomputes each segment of K
+states from its checkpoint (fc_rk_step with FROZEN_MU | FIXED_DT and the recorded
+filter flag, replaying the recorded mu and dt) and applies fc_adjoint_step
+backwards through the segment.
 
 Orchestration only: every step and adjoint step runs in the CUDA library.
 """
@@ -23,30 +25,34 @@ class Trajectory:
         self.checkpoints = {}
         self.mus = []
         self.dts = []
+        self.flags = []  # STEP_FILTER or 0, per step
 
 
-def forward(ctx, e0, nsteps, K, flags=0):
-    """Run nsteps steps from e0 (not modified); returns (e_N, Trajectory)."""
+def forward(ctx, e0, nsteps, K, flags=0, filter=False):
+    """Run nsteps steps from e0 (not modified); returns (e_N, Trajectory). filter: apply
+    the per-step filter on steps n >= 1."""
     e = e0.clone()
     tr = Trajectory(K)
     tr.checkpoints[0] = e0.clone()
     for n in range(nsteps):
         mu = torch.empty(ctx.P, dtype=torch.float64, device=e.device)
         dt = torch.zeros(1, dtype=torch.float64, device=e.device)
-        ctx.rk_step(e, dt, mu, flags & ~fcsdnn.STEP_FILTER)
+        f = fcsdnn.STEP_FILTER if (filter and n >= 1) else 0
+        ctx.rk_step(e, dt, mu, (flags & ~fcsdnn.STEP_FILTER) | f)
         tr.mus.append(mu)
         tr.dts.append(dt)
+        tr.flags.append(f)
         if (n + 1) % K == 0 and n + 1 < nsteps:
             tr.checkpoints[n + 1] = e.clone()
     return e, tr
 
 
 def replay(ctx, tr, e0, n0, n1):
-    """States e_{n0}..e_{n1-1} recomputed from e_{n0} with the recorded mu and dt."""
+    """States e_{n0}..e_{n1-1} recomputed from e_{n0} with the recorded mu, dt and filter flag."""
     out = [e0.clone()]
     e = e0.clone()
     for n in range(n0, n1 - 1):
-        ctx.rk_step(e, tr.dts[n], tr.mus[n], fcsdnn.STEP_FROZEN_MU | fcsdnn.STEP_FIXED_DT)
+        ctx.rk_step(e, tr.dts[n], tr.mus[n], fcsdnn.STEP_FROZEN_MU | fcsdnn.STEP_FIXED_DT | tr.flags[n])
         out.append(e.clone())
     return out
 
@@ -63,7 +69,7 @@ def backward(ctx, tr, lam_N):
         n1 = starts[si + 1] if si + 1 < len(starts) else nsteps
         states = replay(ctx, tr, tr.checkpoints[n0], n0, n1)
         for n in range(n1 - 1, n0 - 1, -1):
-            ctx.adjoint_step(states[n - n0], tr.mus[n], tr.dts[n], lam, nxt, gbc)
+            ctx.adjoint_step(states[n - n0], tr.mus[n], tr.dts[n], lam, nxt, gbc, tr.flags[n])
             lam, nxt = nxt, lam
     return lam, gbc
 
@@ -103,12 +109,12 @@ def freestream_state_derivs(fs, gamma=W.GAMMA):
     return dM, da
 
 
-def drag_gradients(w, ctx, e0, nsteps, K):
+def drag_gradients(w, ctx, e0, nsteps, K, filter=False):
     """J after nsteps from the free-stream state e0 and dJ/dMach, dJ/dangle, dJ/drho_0(x).
 
     Mach and angle enter through the initial state and the Dirichlet free-stream
     states; rho_0 perturbs the initial density at fixed velocity and pressure."""
-    eN, tr = forward(ctx, e0, nsteps, K)
+    eN, tr = forward(ctx, e0, nsteps, K, filter=filter)
     J, dJde = drag(ctx, eN)
     lam0, gbc = backward(ctx, tr, dJde)
     dM, da = freestream_state_derivs(w.freestream, w.params.gamma)

@@ -99,6 +99,8 @@ struct fc_ctx {
   int nfcopy2 = 0;
   BcPt* d_bc = nullptr;
   int nbc = 0;
+  WallPt* d_walls = nullptr;  // no-slip adiabatic wall points
+  int nwalls = 0;
   Recv* d_recv = nullptr;
   int nrecv = 0;
   int* d_cross_dst = nullptr;
@@ -124,6 +126,7 @@ struct fc_ctx {
   int ndon = 0;
   double* d_U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *d_A0 = nullptr, *d_A14 = nullptr, *d_A2 = nullptr, *d_A3 = nullptr, *d_PSa = nullptr, *d_PSb = nullptr;
+  double *d_FX = nullptr, *d_FY = nullptr;  // adjoint with the filter: state before / after it
   bool adj_ready = false;
   // wall ring for the drag functional
   int* d_wall = nullptr;
@@ -432,6 +435,49 @@ long long fft_cost(int L) {
     if (s + 1 < f.size()) cost += 4LL * (L / R) * (R - 1);
   }
   return cost;
+}
+
+// Weights of the adiabatic wall temperature: theta_w = sum_{j=1}^{d-1} w[j-1] theta_j is the
+// value at 0 of the polynomial p of degree d-1 with p'(0) = 0 and p(j) = theta_j,
+// j = 1..d-1 (unit spacing along the wall-normal grid line; the Neumann FC end data).
+// Solves for the coefficients (a_0, a_2, .., a_{d-1}) in long double; w = first row of
+// the inverse.
+std::vector<double> adiabatic_weights(int d) {
+  const int m = d - 1;
+  std::vector<long double> A((size_t)m * m), Inv((size_t)m * m, 0.0L);
+  for (int j = 1; j <= m; ++j)
+    for (int c = 0; c < m; ++c) {
+      const int k = c == 0 ? 0 : c + 1;  // powers 0, 2, 3, .., d-1
+      long double v = 1.0L;
+      for (int q = 0; q < k; ++q) v *= (long double)j;
+      A[(size_t)(j - 1) * m + c] = v;
+    }
+  for (int i = 0; i < m; ++i) Inv[(size_t)i * m + i] = 1.0L;
+  for (int col = 0; col < m; ++col) {  // Gauss-Jordan with partial pivoting
+    int piv = col;
+    for (int r = col + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + col]) > std::fabs(A[(size_t)piv * m + col])) piv = r;
+    for (int q = 0; q < m; ++q) {
+      std::swap(A[(size_t)col * m + q], A[(size_t)piv * m + q]);
+      std::swap(Inv[(size_t)col * m + q], Inv[(size_t)piv * m + q]);
+    }
+    const long double dv = A[(size_t)col * m + col];
+    for (int q = 0; q < m; ++q) {
+      A[(size_t)col * m + q] /= dv;
+      Inv[(size_t)col * m + q] /= dv;
+    }
+    for (int r = 0; r < m; ++r) {
+      if (r == col) continue;
+      const long double f = A[(size_t)r * m + col];
+      for (int q = 0; q < m; ++q) {
+        A[(size_t)r * m + q] -= f * A[(size_t)col * m + q];
+        Inv[(size_t)r * m + q] -= f * Inv[(size_t)col * m + q];
+      }
+    }
+  }
+  std::vector<double> w(m);
+  for (int j = 0; j < m; ++j) w[j] = (double)Inv[j];  // row 0: coefficient a_0 = p(0)
+  return w;
 }
 
 // Continuation length C of a non-periodic line of N points (the paper leaves C free):
@@ -812,6 +858,33 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     }
     for (auto& kv : m) bcs.push_back(kv.second);
   }
+  // ---- no-slip adiabatic wall points (Sec. 4.2, Remark adiabatic): applied after the overwrites above
+  std::vector<WallPt> walls;
+  {
+    const std::vector<double> aw = adiabatic_weights(prm->d);
+    for (int p = 0; p < npatch; ++p) {
+      const HPatch& h = c->hp[p];
+      for (int s = 0; s < 4; ++s) {
+        if (h.d.side[s] != FC_SIDE_ADIABATIC) continue;
+        if (h.d.kind == FC_PATCH_OGRID && s < 2) return bad("an O-grid wall must be its q2 = 0 or q2 = 1 side");
+        const int nline = s < 2 ? h.n1 : h.n2;
+        if (nline < prm->d + 1) return bad("a wall-normal grid line is shorter than d + 1 points");
+        const int step = s == 0 ? 1 : s == 1 ? -1 : s == 2 ? h.n1 : -h.n1;
+        const int cnt = s < 2 ? h.n2 : h.n1;
+        for (int t = 0; t < cnt; ++t) {
+          const size_t k = s < 2 ? (size_t)t * h.n1 + (s == 0 ? 0 : h.n1 - 1) : (size_t)(s == 2 ? 0 : h.n2 - 1) * h.n1 + t;
+          if (h.blank[k]) continue;
+          WallPt wp;
+          std::memset(&wp, 0, sizeof(wp));
+          wp.idx = (int)(h.off + (long long)k);
+          wp.step = step;
+          wp.nw = prm->d - 1;
+          for (int j = 0; j < wp.nw; ++j) wp.w[j] = aw[j];
+          walls.push_back(wp);
+        }
+      }
+    }
+  }
 
   // ---- per-point flags and viscosity windows
   std::vector<uint32_t> info((size_t)c->P);
@@ -982,11 +1055,11 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     }
     if (!ent.empty()) dptr.push_back((int)drecv.size());
   }
-  // ---- wall ring of the first curvilinear patch with a slip wall at q2 = 0 (drag functional)
+  // ---- wall ring of the first curvilinear patch with a wall at q2 = 0 (drag functional)
   std::vector<int> wall;
   std::vector<double> wallw, wallc;
   for (const HPatch& h : c->hp) {
-    if (h.d.kind != FC_PATCH_OGRID || h.d.side[2] != FC_SIDE_SLIPWALL) continue;
+    if (h.d.kind != FC_PATCH_OGRID || (h.d.side[2] != FC_SIDE_SLIPWALL && h.d.side[2] != FC_SIDE_ADIABATIC)) continue;
     for (int i = 0; i < h.n1; ++i) {
       const double dx = h.x[i] - h.d.geom[0], dy = h.y[i] - h.d.geom[1];
       wall.push_back((int)(h.off + i));
@@ -1018,7 +1091,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
        c->upload(&c->d_fix, fix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
-       c->upload(&c->d_bc, bcs) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
+       c->upload(&c->d_bc, bcs) && c->upload(&c->d_walls, walls) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
        c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
        c->upload(&c->d_dsrc, dsrc) && c->upload(&c->d_drecv, drecv) && c->upload(&c->d_dw, dw) &&
        c->upload(&c->d_wall, wall) && c->upload(&c->d_wallw, wallw) && c->upload(&c->d_wallc, wallc);
@@ -1028,6 +1101,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
   c->nbc = (int)bcs.size();
+  c->nwalls = (int)walls.size();
   c->nrecv = (int)recv.size();
   c->ncross = (int)cdst.size();
   const size_t P = (size_t)c->P, Pg = (size_t)std::max<long long>(c->Pg, 1);
@@ -1166,6 +1240,10 @@ void project(fc_ctx* c, double* e, cudaStream_t st) {
     launch_bc(c->d_bc, c->nbc, e, c->P, st);
     c->launches++;
   }
+  if (c->nwalls) {
+    launch_bc_wall(c->d_walls, c->nwalls, e, c->P, c->prm.gamma, st);
+    c->launches++;
+  }
   if (c->nrecv) {
     launch_exchange(c->d_recv, c->nrecv, e, c->P, st);
     c->launches++;
@@ -1196,6 +1274,26 @@ void filter(fc_ctx* c, double* e, bool per_patch, cudaStream_t st) {
             [&](const Job* j, int n, int L) { launch_filter_q2(T, j, n, L, F, e, st); });
   if (c->nfcopy2) {
     launch_filter_copy_q2(T, c->d_fcopy2, c->nfcopy2, F, e, st);
+    c->launches++;
+  }
+}
+
+// transpose of filter() linearised at its input state pre (filt: its output): lam -> out;
+// MF is scratch; blanked points pass lam through
+void filterT(fc_ctx* c, const double* lam, const double* pre, const double* filt, double* MF, double* out,
+             cudaStream_t st) {
+  const DevTables& T = c->T;
+  cudaMemcpyAsync(out, lam, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
+  run_queue(c, c->q_filt2, false, st, "filterT_q2",
+            [&](const Job* j, int n, int L) { launch_filterT_q2(T, j, n, L, lam, filt, MF, st); });
+  if (c->nfcopy2) {
+    launch_filterT_copy2(T, c->d_fcopy2, c->nfcopy2, lam, filt, MF, st);
+    c->launches++;
+  }
+  run_queue(c, c->q_filt1, false, st, "filterT_q1",
+            [&](const Job* j, int n, int L) { launch_filterT_q1(T, j, n, L, MF, pre, out, st); });
+  if (c->nfcopy1) {
+    launch_filterT_copy1(T, c->d_fcopy1, c->nfcopy1, MF, pre, out, st);
     c->launches++;
   }
 }
@@ -1242,11 +1340,13 @@ void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream
   project(c, e, st);
 }
 
-void projectT(fc_ctx* c, double* lam, double* gbc, cudaStream_t st) {
+// transpose of project(); u: the state project() was applied to (used by the adiabatic walls)
+void projectT(fc_ctx* c, double* lam, double* gbc, const double* u, cudaStream_t st) {
   Prof pr(c, st, "bc_exchange_T");
   launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv, c->nrecv, lam, c->P, st);
+  launch_bc_wall_T(c->d_walls, c->nwalls, u, lam, c->P, c->prm.gamma, st);
   launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->P, st);
-  c->launches += (c->ndon > 0) + (c->nrecv > 0) + (c->nbc > 0);
+  c->launches += (c->ndon > 0) + (c->nrecv > 0) + (c->nwalls > 0) + (c->nbc > 0);
 }
 
 // acc += dt L'(u)^T psi
@@ -1522,7 +1622,7 @@ fc_status fc_line_stats(fc_ctx* c, long long* lines_q1, long long* lines_q2, dou
 }
 
 fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const double* dt, const double* lam_np1,
-                          double* lam_n, double* gbc, void* stream) {
+                          double* lam_n, double* gbc, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   if (!c->adj_ready) {
@@ -1534,54 +1634,93 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
     if (!ok) return FC_ERR_OOM;
     c->adj_ready = true;
   }
+  const bool filt = (flags & FC_STEP_FILTER) != 0;
+  const size_t bytes4 = sizeof(double) * 4 * (size_t)c->P;
+  if (filt && !c->d_FX) {
+    if (!(c->alloc(&c->d_FX, 4 * (size_t)c->P) && c->alloc(&c->d_FY, 4 * (size_t)c->P))) return FC_ERR_OOM;
+  }
   double** U = c->d_U;
-  // forward recompute of the stage states u_0..u_4 (mu, dt frozen, no filter)
-  cudaMemcpyAsync(U[0], e_n, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
+  // forward recompute of the stage states u_0..u_4 (mu, dt frozen); with the filter,
+  // u_0 = P(F(P(e_n))) and the states before (FX) and after (FY) F are kept
+  cudaMemcpyAsync(U[0], e_n, bytes4, cudaMemcpyDeviceToDevice, st);
   project(c, U[0], st);
+  if (filt) {
+    cudaMemcpyAsync(c->d_FX, U[0], bytes4, cudaMemcpyDeviceToDevice, st);
+    filter(c, U[0], false, st);
+    cudaMemcpyAsync(c->d_FY, U[0], bytes4, cudaMemcpyDeviceToDevice, st);
+    project(c, U[0], st);
+  }
   StageCoef s{};
   s.dt = dt;
   s.U0 = U[0];
   const double c0[4] = {0.0, A20, A30, A40}, c1[4] = {1.0, A21, A32, A43}, cb[4] = {B1, B2, B3, B4};
+  double *A0 = c->d_A0, *A14 = c->d_A14, *A2 = c->d_A2, *A3 = c->d_A3, *PSa = c->d_PSa, *PSb = c->d_PSb;
   for (int i = 0; i < 4; ++i) {
     s.Ucur = U[i];
     s.out = U[i + 1];
     s.c0 = c0[i];
     s.c1 = c1[i];
     s.cb = cb[i];
+    if (i == 3 && c->nwalls) {  // acc = a52 u2 + a53 u3 + b53 dt L(u3) for u5 below
+      s.Uaux = U[2];
+      s.out2 = PSb;
+      s.d1 = A53;
+      s.d2 = A52;
+      s.db = B53;
+    }
     stage(c, s, mu, false, st);
     project(c, U[i + 1], st);
   }
+  // the adiabatic walls' transpose at the last projection needs u5 = e_{n+1} (in A3 until
+  // the reverse sweep first writes A3)
+  if (c->nwalls) {
+    StageCoef s5{};
+    s5.dt = dt;
+    s5.Ucur = U[4];
+    s5.Uaux = PSb;
+    s5.out = A3;
+    s5.c1 = A54;
+    s5.c2 = 1.0;
+    s5.cb = B54;
+    stage(c, s5, mu, false, st);
+    project(c, A3, st);
+  }
   // reverse sweep (Shu-Osher coefficients, see the forward stages)
-  double *A0 = c->d_A0, *A14 = c->d_A14, *A2 = c->d_A2, *A3 = c->d_A3, *PSa = c->d_PSa, *PSb = c->d_PSb;
   axpby(c, 1.0, lam_np1, 0.0, A14, st);
-  projectT(c, A14, gbc, st);  // lam_v5
+  projectT(c, A14, gbc, A3, st);  // lam_v5
   axpby(c, A53, A14, 0.0, A3, st);
   axpby(c, B53, A14, 0.0, PSb, st);
   axpby(c, A52, A14, 0.0, A2, st);
   axpby(c, B54, A14, 0.0, PSa, st);
   axpby(c, A54, A14, 0.0, A14, st);  // lam_u4 (without its L' term)
   adj_stage(c, U[4], mu, PSa, A14, dt, st);
-  projectT(c, A14, gbc, st);  // lam_v4
+  projectT(c, A14, gbc, U[4], st);  // lam_v4
   axpby(c, A40, A14, 0.0, A0, st);
   axpby(c, A43, A14, 1.0, A3, st);
   axpby(c, B4, A14, 1.0, PSb, st);
   adj_stage(c, U[3], mu, PSb, A3, dt, st);
-  projectT(c, A3, gbc, st);  // lam_v3
+  projectT(c, A3, gbc, U[3], st);  // lam_v3
   axpby(c, A30, A3, 1.0, A0, st);
   axpby(c, A32, A3, 1.0, A2, st);
   axpby(c, B3, A3, 0.0, PSa, st);
   adj_stage(c, U[2], mu, PSa, A2, dt, st);
-  projectT(c, A2, gbc, st);  // lam_v2
+  projectT(c, A2, gbc, U[2], st);  // lam_v2
   axpby(c, A20, A2, 1.0, A0, st);
   axpby(c, A21, A2, 0.0, A14, st);
   axpby(c, B2, A2, 0.0, PSb, st);
   adj_stage(c, U[1], mu, PSb, A14, dt, st);
-  projectT(c, A14, gbc, st);  // lam_v1
+  projectT(c, A14, gbc, U[1], st);  // lam_v1
   axpby(c, 1.0, A14, 1.0, A0, st);
   axpby(c, B1, A14, 0.0, PSa, st);
   adj_stage(c, U[0], mu, PSa, A0, dt, st);
-  projectT(c, A0, gbc, st);
-  cudaMemcpyAsync(lam_n, A0, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
+  projectT(c, A0, gbc, U[0], st);
+  if (filt) {  // transposes of F and of the projection before it
+    filterT(c, A0, c->d_FX, c->d_FY, PSb, PSa, st);
+    projectT(c, PSa, gbc, c->d_FX, st);
+    cudaMemcpyAsync(lam_n, PSa, bytes4, cudaMemcpyDeviceToDevice, st);
+    return cuda_check(c, "fc_adjoint_step");
+  }
+  cudaMemcpyAsync(lam_n, A0, bytes4, cudaMemcpyDeviceToDevice, st);
   return cuda_check(c, "fc_adjoint_step");
 }
 

@@ -73,6 +73,15 @@ struct BcPt {
   double val[4];    // Dirichlet conserved state
 };
 
+// No-slip adiabatic wall point: momenta set to 0, E = rho theta_w / (gamma - 1) with
+// theta_w = sum_j w[j] theta(e at idx + (j + 1) step), j < nw (the inward grid line).
+struct WallPt {
+  int idx;
+  int step;  // state-index step to the next point inward along the wall-normal grid line
+  int nw;    // d - 1
+  double w[7];
+};
+
 // Runge-Kutta stage combination applied in the last pass of a stage:
 //   out  = c0 U0 + c1 Ucur + c2 Uaux + cb dt L
 //   out2 = d2 Uaux + d1 Ucur + db dt L        (only when out2 != nullptr)
@@ -118,6 +127,17 @@ void launch_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, cons
                   const StageCoef& sc, cudaStream_t st);
 void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef& sc, cudaStream_t st);
 void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st);
+void launch_bc_wall(const WallPt* w, int n, double* e, long long P, double gamma, cudaStream_t st);
+void launch_bc_wall_T(const WallPt* w, int n, const double* u, double* lam, long long P, double gamma,
+                      cudaStream_t st);
+void launch_filterT_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* lam, const double* ef,
+                       double* MF, cudaStream_t st);
+void launch_filterT_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* MF, const double* e,
+                       double* out, cudaStream_t st);
+void launch_filterT_copy2(const DevTables& T, const int* idx, int n, const double* lam, const double* ef, double* MF,
+                          cudaStream_t st);
+void launch_filterT_copy1(const DevTables& T, const int* idx, int n, const double* MF, const double* e, double* out,
+                          cudaStream_t st);
 void launch_exchange(const Recv* r, int n, double* e, long long P, cudaStream_t st);
 void launch_filter_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* F, cudaStream_t st);
 void launch_filter_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* F, double* e, cudaStream_t st);

@@ -425,6 +425,25 @@ __global__ void k_bc(const BcPt* __restrict__ bc, int n, double* __restrict__ e,
   }
 }
 
+// no-slip adiabatic wall (Sec. 4.2, Remark adiabatic): zero momenta; the wall temperature
+// from the inward temperatures with zero normal derivative; E = rho theta_w / (gamma - 1)
+__global__ void k_bc_wall(const WallPt* __restrict__ wp, int n, double* __restrict__ e, long long P, double gam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const WallPt w = wp[i];
+  double th = 0.0;
+  for (int j = 0; j < w.nw; ++j) {
+    const long long q = w.idx + (long long)(j + 1) * w.step;
+    const double r = e[q], mx = e[q + P], my = e[q + 2 * P], E = e[q + 3 * P];
+    const double tj = (gam - 1.0) * (E - 0.5 * (mx * mx + my * my) / r) / r;
+    th = fma(w.w[j], tj, th);
+  }
+  const long long p = w.idx;
+  e[p + P] = 0.0;
+  e[p + 2 * P] = 0.0;
+  e[p + 3 * P] = e[p] * th / (gam - 1.0);
+}
+
 // ---------------------------------------------------------------- inter-patch exchange (Sec. 3.4.1)
 // iterated 1-D quadratic interpolation: along q1 in each of the 3 stencil rows, then along q2
 __global__ void k_exchange(const Recv* __restrict__ r, int n, double* __restrict__ e, long long P) {
@@ -811,10 +830,13 @@ __global__ void k_check_state(DevTables T, const double* __restrict__ e, int* fl
 }
 
 // ---------------------------------------------------------------- discrete adjoint (mu, dt frozen)
-// Transposed FC derivative of the two packed sequences in A (data in [0, n)):
-// D^T = extend^T o (-spectral derivative) o zero padding; extend^T folds the C
-// continuation entries back onto the first and last d points with ML^T and MR^T.
-__device__ __forceinline__ double2* deriv2T(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
+// Transposed line operator of the two packed sequences in A (data in [0, n)):
+// extend^T o M o zero padding with M = -spectral derivative (the transposed FC
+// derivative, FILT false) or the spectral filter (FILT true: real and even in k, so
+// symmetric); extend^T folds the C continuation entries back onto the first and last d
+// points with ML^T and MR^T.
+template <bool FILT>
+__device__ __forceinline__ double2* line2T(double2* A, const Job& J, const Plan& P, const DevTables& T, int lane) {
   const int L = P.L, n = J.n, C = J.C, d = T.d;
   for (int idx = lane; idx < 2 * C; idx += 32) {
     const int s = idx / C, k = idx - s * C;
@@ -822,7 +844,10 @@ __device__ __forceinline__ double2* deriv2T(double2* A, const Job& J, const Plan
   }
   FC_SYNC();
   fft_inplace<false>(A, P, 2, T.tw, lane, 32);
-  mul_deriv_rev(A, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), T.ip + P.rev, lane, 32);
+  if (FILT)
+    mul_filter_rev(A, L, 2, T.rp + P.sig, T.ip + P.rev, lane, 32);
+  else
+    mul_deriv_rev(A, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), T.ip + P.rev, lane, 32);
   FC_SYNC();
   fft_inplace<true>(A, P, 2, T.tw, lane, 32);
   double2* X = A;
@@ -906,7 +931,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_cart(DevTables T, const Job* __restrict
     const Plan P = T.plans[J.plan];
     const int L = P.L;
     load4_masked(A, L, J, T, psi, lane);
-    double2* X = deriv2T(A, J, P, T, lane);
+    double2* X = line2T<false>(A, J, P, T, lane);
     double2* Y = A;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -929,7 +954,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_cart(DevTables T, const Job* __restrict
       Y[t] = cpx(m * eta[0], m * eta[1]);
       Y[L + t] = cpx(m * eta[2], m * eta[3]);
     }
-    double2* Z = deriv2T(A, J, P, T, lane);
+    double2* Z = line2T<false>(A, J, P, T, lane);
     const double dt = dir ? *dtp : 0.0;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
@@ -968,7 +993,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_A(DevTables T, const Job* __restric
         A[t] = cpx(w * psi[p], w * psi[p + cs]);
         A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
       }
-      double2* X = deriv2T(A, J, P, T, lane);
+      double2* X = line2T<false>(A, J, P, T, lane);
       for (int t = lane; t < J.n; t += 32) {
         const long long g = J.gbase + (long long)t * J.stride;
         gslot(G, Pg, which, 0)[g] = X[t].x;
@@ -1003,7 +1028,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restric
         A[t] = cpx(w * psi[p], w * psi[p + cs]);
         A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
       }
-      double2* X = deriv2T(A, J, P, T, lane);
+      double2* X = line2T<false>(A, J, P, T, lane);
       for (int t = lane; t < J.n; t += 32) {
         const long long g = J.gbase + (long long)t * J.stride;
         const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
@@ -1038,7 +1063,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restric
       A[t] = cpx(g2[0], g2[1]);
       A[L + t] = cpx(g2[2], g2[3]);
     }
-    double2* Z = deriv2T(A, J, P, T, lane);
+    double2* Z = line2T<false>(A, J, P, T, lane);
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double z[4] = {Z[t].x, Z[t].y, Z[L + t].x, Z[L + t].y};
@@ -1067,7 +1092,7 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restric
       A[t] = cpx(gslot(G, Pg, 3, 0)[g], gslot(G, Pg, 3, 1)[g]);
       A[L + t] = cpx(gslot(G, Pg, 3, 2)[g], gslot(G, Pg, 3, 3)[g]);
     }
-    double2* X = deriv2T(A, J, P, T, lane);
+    double2* X = line2T<false>(A, J, P, T, lane);
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;
@@ -1136,6 +1161,139 @@ __global__ void k_bc_T(const BcPt* __restrict__ bc, int n, double* __restrict__ 
     lam[p + 2 * P] = my - mn * b.ny;
   }
 }
+// ---- transpose of the linearised per-step filter (Sec. 4.3.1) -----------------------------
+// forward: Q = (rho, rho u, rho v, theta(e)) filtered along q1 lines (into F), then along q2
+// lines, and E rebuilt from the filtered Q (eq. perfect_gas_T)
+__device__ __forceinline__ void rebuild_T(const double* __restrict__ lam, const double* __restrict__ ef, long long p,
+                                          long long cs, double gam, double* o) {
+  const double r = ef[p], m = ef[p + cs], nn = ef[p + 2 * cs];
+  const double th = theta_of(r, m, nn, ef[p + 3 * cs], gam);
+  const double g1 = gam - 1.0, lE = lam[p + 3 * cs], ir = 1.0 / r;
+  o[0] = lam[p] + lE * (th / g1 - 0.5 * (m * m + nn * nn) * ir * ir);
+  o[1] = lam[p + cs] + lE * m * ir;
+  o[2] = lam[p + 2 * cs] + lE * nn * ir;
+  o[3] = lE * r / g1;
+}
+__device__ __forceinline__ void theta_T(const double* q, const double* __restrict__ e, long long p, long long cs,
+                                        double gam, double* o) {
+  const double r = e[p], m = e[p + cs], nn = e[p + 2 * cs], E = e[p + 3 * cs];
+  const double g1 = gam - 1.0, lt = q[3], ir = 1.0 / r, ir2 = ir * ir;
+  o[0] = q[0] + lt * g1 * (-E * ir2 + (m * m + nn * nn) * ir2 * ir);
+  o[1] = q[1] + lt * (-g1 * m * ir2);
+  o[2] = q[2] + lt * (-g1 * nn * ir2);
+  o[3] = lt * g1 * ir;
+}
+
+// q2 lines: lam (adjoint of the filtered state), ef (the filter output) -> MF
+__global__ void LINE_KERNEL_BOUNDS k_filterT_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                const double* __restrict__ lam, const double* __restrict__ ef,
+                                                double* __restrict__ MF) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      double o[4];
+      rebuild_T(lam, ef, p, cs, T.gamma, o);
+      A[t] = cpx(o[0], o[1]);
+      A[L + t] = cpx(o[2], o[3]);
+    }
+    FC_SYNC();
+    double2* X = line2T<true>(A, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      MF[p] = X[t].x;
+      MF[p + cs] = X[t].y;
+      MF[p + 2 * cs] = X[L + t].x;
+      MF[p + 3 * cs] = X[L + t].y;
+    }
+    FC_SYNC();
+  }
+}
+// q1 lines: MF, e (the state the filter was applied to) -> out (adjoint of that state)
+__global__ void LINE_KERNEL_BOUNDS k_filterT_q1(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                const double* __restrict__ MF, const double* __restrict__ e,
+                                                double* __restrict__ out) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, MF, cs, lane);
+    FC_SYNC();
+    double2* X = line2T<true>(A, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const double q[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+      double o[4];
+      theta_T(q, e, p, cs, T.gamma, o);
+      out[p] = o[0];
+      out[p + cs] = o[1];
+      out[p + 2 * cs] = o[2];
+      out[p + 3 * cs] = o[3];
+    }
+    FC_SYNC();
+  }
+}
+// points that no filtered line covers (identity filter there)
+__global__ void k_filterT_copy2(DevTables T, const int* __restrict__ idx, int n, const double* __restrict__ lam,
+                                const double* __restrict__ ef, double* __restrict__ MF) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = idx[i], cs = T.P;
+  double o[4];
+  rebuild_T(lam, ef, p, cs, T.gamma, o);
+  for (int c = 0; c < 4; ++c) MF[p + c * cs] = o[c];
+}
+__global__ void k_filterT_copy1(DevTables T, const int* __restrict__ idx, int n, const double* __restrict__ MF,
+                                const double* __restrict__ e, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = idx[i], cs = T.P;
+  const double q[4] = {MF[p], MF[p + cs], MF[p + 2 * cs], MF[p + 3 * cs]};
+  double o[4];
+  theta_T(q, e, p, cs, T.gamma, o);
+  for (int c = 0; c < 4; ++c) out[p + c * cs] = o[c];
+}
+
+// transpose of the linearised adiabatic wall condition at the state u it was applied to
+// (u's wall density and inward points are unchanged by it): the wall momenta and energy
+// adjoints are cleared and lam_E,w is passed to rho_w and, through theta, to the inward points
+__global__ void k_bc_wall_T(const WallPt* __restrict__ wp, int n, const double* __restrict__ u,
+                            double* __restrict__ lam, long long P, double gam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const WallPt w = wp[i];
+  const long long p = w.idx;
+  const double g1 = gam - 1.0;
+  const double lE = lam[p + 3 * P];
+  const double rw = u[p];
+  double th = 0.0;
+  for (int j = 0; j < w.nw; ++j) {
+    const long long q = w.idx + (long long)(j + 1) * w.step;
+    const double r = u[q], mx = u[q + P], my = u[q + 2 * P], E = u[q + 3 * P];
+    th = fma(w.w[j], g1 * (E - 0.5 * (mx * mx + my * my) / r) / r, th);
+    const double g = lE * rw / g1 * w.w[j];
+    const double ir = 1.0 / r, ir2 = ir * ir;
+    atomicAdd(lam + q, g * g1 * (-E * ir2 + (mx * mx + my * my) * ir2 * ir));
+    atomicAdd(lam + q + P, g * (-g1 * mx * ir2));
+    atomicAdd(lam + q + 2 * P, g * (-g1 * my * ir2));
+    atomicAdd(lam + q + 3 * P, g * (g1 * ir));
+  }
+  lam[p + P] = 0.0;
+  lam[p + 2 * P] = 0.0;
+  lam[p + 3 * P] = 0.0;
+  atomicAdd(lam + p, lE * th / g1);
+}
+
 // y = a x + b y over n doubles (b == 0: y = a x)
 __global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1211,6 +1369,35 @@ void launch_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, cons
 void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef& sc, cudaStream_t st) {
   if (n <= 0) return;
   k_rk_fixup<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, sc);
+}
+void launch_filterT_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* lam, const double* ef,
+                       double* MF, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_filterT_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, lam, ef, MF);
+}
+void launch_filterT_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* MF, const double* e,
+                       double* out, cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_filterT_q1<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, MF, e, out);
+}
+void launch_filterT_copy2(const DevTables& T, const int* idx, int n, const double* lam, const double* ef, double* MF,
+                          cudaStream_t st) {
+  if (n <= 0) return;
+  k_filterT_copy2<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, lam, ef, MF);
+}
+void launch_filterT_copy1(const DevTables& T, const int* idx, int n, const double* MF, const double* e, double* out,
+                          cudaStream_t st) {
+  if (n <= 0) return;
+  k_filterT_copy1<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, MF, e, out);
+}
+void launch_bc_wall_T(const WallPt* w, int n, const double* u, double* lam, long long P, double gamma,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  k_bc_wall_T<<<grid_pts(n, 128), 128, 0, st>>>(w, n, u, lam, P, gamma);
+}
+void launch_bc_wall(const WallPt* w, int n, double* e, long long P, double gamma, cudaStream_t st) {
+  if (n <= 0) return;
+  k_bc_wall<<<grid_pts(n, 128), 128, 0, st>>>(w, n, e, P, gamma);
 }
 void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st) {
   if (n <= 0) return;
@@ -1321,6 +1508,8 @@ void set_kernel_attributes() {
   cudaFuncSetAttribute(k_adj_gen_A, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_adj_gen_B, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_adj_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_filterT_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_filterT_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st) {
   k_check_state<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, flag);

@@ -73,7 +73,7 @@ def load():
         "fc_project": (C.c_int, [vp, vp, vp]),
         "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
-        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "fc_drag": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_sync_status": (C.c_int, [vp, vp, ip, vp]),
         "fc_launch_count": (C.c_uint64, [vp]),
@@ -220,9 +220,9 @@ class Context:
     def rk_step(self, e, dt, mu, flags=0):
         self._check(self.lib.fc_rk_step(self.ctx, _ptr(e), _ptr(dt), _ptr(mu), int(flags), _stream()))
 
-    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None):
+    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None, flags=0):
         self._check(self.lib.fc_adjoint_step(self.ctx, _ptr(e_n), _ptr(mu), _ptr(dt), _ptr(lam_np1), _ptr(lam_n),
-                                             _ptr(gbc), _stream()))
+                                             _ptr(gbc), int(flags), _stream()))
 
     def drag(self, e, J, dJde=None):
         self._check(self.lib.fc_drag(self.ctx, _ptr(e), _ptr(J), _ptr(dJde), _stream()))

@@ -8,8 +8,10 @@ the initial primitive states, and the flat state layout. Both the oracle
 Workloads (stand-ins for the paper's meshes, which are not published):
   sod128      single affine patch [0,1]^2, 128x128, Sod tube along x
   cyl_m3      O-grid r in [0.5,1.5] (512 theta x 96 r) + 4x4 affine 160x160
-              patches on [-4,8]x[-6,6] with 10-point overlaps, Mach 3 free stream
-  cyl_m2_half same geometry at half resolution (256x48, 80x80), Mach 2 at 2 deg
+              patches on [-4,8]x[-6,6] with 10-point overlaps, Mach 3 free stream,
+              no-slip adiabatic cylinder wall
+  cyl_m2_half same geometry at half resolution (256x48, 80x80), Mach 2 at 2 deg,
+              no-slip adiabatic cylinder wall
   cyl_m25_32  [-8,16]x[-12,12] as 32x32 affine patches with seeded uneven sizes
               48..384 (refined toward the body) + 1024x192 O-grid, Mach 25
   cyl_m25_4096 64x64 affine patches with seeded sizes 64..512 + O-grid, Mach 25
@@ -24,7 +26,7 @@ import numpy as np
 # patch kinds
 AFFINE, OGRID = 0, 1
 # side types (side order: q1=0, q1=1, q2=0, q2=1)
-INTERNAL, DIRICHLET, SLIPWALL, OUTFLOW, PERIODIC = 0, 1, 2, 3, 4
+INTERNAL, DIRICHLET, SLIPWALL, OUTFLOW, PERIODIC, ADIABATIC = 0, 1, 2, 3, 4, 5
 
 GAMMA = 1.4
 
@@ -92,6 +94,27 @@ def sod128(n=128):
                     freestream=left, init="sod", steps=100, extra={"left": left, "right": right, "x_split": 0.5})
 
 
+def mach_shock_state(M, gamma=GAMMA):
+    """Post-shock primitive state of a Mach-M shock moving at speed M into (1.4, 0, 0, 1)
+    (eq. mach_shock_ic; the printed density is read as the density ratio, so the
+    post-shock density is 1.4 times it)."""
+    zeta = (2 * gamma * M * M - gamma + 1) / (gamma + 1)
+    ratio = (gamma + 1) * M * M / ((gamma - 1) * M * M + 2)
+    return (1.4 * ratio, (zeta - 1) / (gamma * M), 0.0, zeta)
+
+
+def moving_shock(M, n1=256, n2=16, x_split=0.25):
+    """A planar Mach-M shock at x = x_split moving right into gas at rest (Sec. 7,
+    eq. mach_shock_ic) on one affine patch [0, 1] x [0, (n2-1)/(n1-1)] with square cells;
+    x-ends hold the two states, y-sides are slip walls."""
+    post, pre = mach_shock_state(M), (1.4, 0.0, 0.0, 1.0)
+    ly = (n2 - 1) / (n1 - 1)
+    p = PatchDesc(AFFINE, n1, n2, (0.0, 1.0, 0.0, ly), (DIRICHLET, DIRICHLET, SLIPWALL, SLIPWALL),
+                  bc=(post, pre, post, post))
+    return Workload(f"shock_M{M:g}", [p], Params(d=5, C0=27, c_policy=2), freestream=pre, init="sod", steps=0,
+                    extra={"left": post, "right": pre, "x_split": x_split, "mach": M})
+
+
 def _cart_array(nx, ny, x0, x1, y0, y1, nper, overlap, fs, hole, sizes=None):
     """nx*ny affine patches tiling [x0,x1]x[y0,y1].
 
@@ -133,26 +156,29 @@ def _cart_array(nx, ny, x0, x1, y0, y1, nper, overlap, fs, hole, sizes=None):
     return patches
 
 
-def _ogrid(nth, nr, r0, r1, fs):
-    return PatchDesc(OGRID, nth, nr, (0.0, 0.0, r0, r1), (PERIODIC, PERIODIC, SLIPWALL, INTERNAL), bc=(fs,) * 4)
+def _ogrid(nth, nr, r0, r1, fs, wall=SLIPWALL):
+    return PatchDesc(OGRID, nth, nr, (0.0, 0.0, r0, r1), (PERIODIC, PERIODIC, wall, INTERNAL), bc=(fs,) * 4)
 
 
 def cyl_m3(scale=1.0):
     fs = (1.4, 3.0, 0.0, 1.0)
     nc = int(round(160 * scale))
-    og = _ogrid(int(round(512 * scale)), int(round(96 * scale)), 0.5, 1.5, fs)
+    og = _ogrid(int(round(512 * scale)), int(round(96 * scale)), 0.5, 1.5, fs, ADIABATIC)
     cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, nc, 10, fs, hole=(0.0, 0.0, 1.0))
     return Workload("cyl_m3" if scale == 1.0 else f"cyl_m3_x{scale}", [og] + cart,
                     Params(d=5, C0=27, c_policy=2), freestream=fs, init="freestream", steps=2000)
 
 
-def cyl_m2_half():
-    a = math.radians(2.0)
-    fs = (1.4, 2.0 * math.cos(a), 2.0 * math.sin(a), 1.0)
-    og = _ogrid(256, 48, 0.5, 1.5, fs)
+def cyl_m2_half(mach=2.0, alpha_deg=2.0):
+    """The Mach-3 cylinder geometry at half resolution under a Mach-2 free stream at 2
+    degrees angle of attack (the adjoint configuration); mach and alpha_deg vary the
+    free stream (and the Dirichlet states) for finite-difference checks."""
+    a = math.radians(alpha_deg)
+    fs = (1.4, mach * math.cos(a), mach * math.sin(a), 1.0)
+    og = _ogrid(256, 48, 0.5, 1.5, fs, ADIABATIC)
     cart = _cart_array(4, 4, -4.0, 8.0, -6.0, 6.0, 80, 10, fs, hole=(0.0, 0.0, 1.0))
     return Workload("cyl_m2_half", [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs,
-                    init="freestream", steps=400, extra={"mach": 2.0, "alpha_deg": 2.0})
+                    init="freestream", steps=400, extra={"mach": mach, "alpha_deg": alpha_deg})
 
 
 def seeded_sizes(nx, ny, nmin, nmax, seed, x0, x1, y0, y1, taper):
@@ -186,13 +212,14 @@ def cyl_m25_4096():
     return cyl_m25_array(64, 64, 512, 5, 0.95, 1024, 192, "cyl_m25_4096")
 
 
-def small_multipatch():
-    """A tiny O-grid + 2x2 affine array around a cylinder: the oracle finishes it in seconds."""
+def small_multipatch(wall=SLIPWALL):
+    """A tiny O-grid + 2x2 affine array around a cylinder: the oracle finishes it in seconds.
+    wall: SLIPWALL or ADIABATIC (no-slip adiabatic) on the cylinder."""
     fs = (1.4, 3.0, 0.0, 1.0)
-    og = _ogrid(128, 32, 0.5, 1.5, fs)
+    og = _ogrid(128, 32, 0.5, 1.5, fs, wall)
     cart = _cart_array(2, 2, -2.5, 2.5, -2.5, 2.5, 64, 10, fs, hole=(0.0, 0.0, 0.85))
-    return Workload("small_multipatch", [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs,
-                    init="freestream", steps=20)
+    name = "small_multipatch" if wall == SLIPWALL else "small_multipatch_adiabatic"
+    return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs, init="freestream", steps=20)
 
 
 WORKLOADS = {

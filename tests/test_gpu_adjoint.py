@@ -23,9 +23,10 @@ def mach2_small(mach=2.0, alpha_deg=2.0):
     return W.Workload(f"small_M{mach}", pts, w.params, fs, "freestream", 10)
 
 
-@pytest.mark.parametrize("name", ["sod64", "multi"])
+@pytest.mark.parametrize("name", ["sod64", "multi", "multi_adiabatic"])
 def test_adjoint_step_parity(gpu_lib, name):
-    w = W.sod128(64) if name == "sod64" else W.small_multipatch()
+    w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
+         "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC)}[name]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     st = sv.project(W.random_smooth_state(w, seed=41, amp=0.1))
@@ -44,6 +45,27 @@ def test_adjoint_step_parity(gpu_lib, name):
     if any(np.abs(g).max() > 0 for g in ref_gbc):
         errs = rel_err(from_dev(gbc, w), ref_gbc)
         assert max(errs) < 1e-11, errs
+
+
+def test_adjoint_step_with_filter_parity(gpu_lib):
+    w = W.small_multipatch(W.ADIABATIC)
+    ctx = gpu_lib.Context(w)
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=43, amp=0.1))
+    mu = [0.003 * (1 + np.cos(2 * g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    dt = 0.5 * sv.dt(st, mu)
+    rng = np.random.default_rng(6)
+    lam = [rng.normal(size=a.shape) for a in st]
+    ref_lam, ref_gbc = A.step_adjoint(sv, st, mu, dt, lam, filt=True)
+    lam_n = torch.empty_like(to_dev(st))
+    gbc = torch.zeros_like(lam_n)
+    dtt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    ctx.adjoint_step(to_dev(st), to_dev_scalar_field(mu), dtt, to_dev(lam), lam_n, gbc, gpu_lib.STEP_FILTER)
+    torch.cuda.synchronize()
+    errs = rel_err(from_dev(lam_n, w), ref_lam)
+    assert max(errs) < 1e-11, errs
+    errs = rel_err(from_dev(gbc, w), ref_gbc)
+    assert max(errs) < 1e-11, errs
 
 
 def test_drag_parity(gpu_lib):

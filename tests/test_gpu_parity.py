@@ -28,9 +28,10 @@ def workloads_small():
     return [W.sod128(64), W.small_multipatch()]
 
 
-@pytest.fixture(scope="module", params=["sod64", "multi"])
+@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic"])
 def case(request, gpu_lib):
-    w = W.sod128(64) if request.param == "sod64" else W.small_multipatch()
+    w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
+         "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC)}[request.param]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     return w, ctx, sv

@@ -60,6 +60,65 @@ def test_project_adjoint_dot_product(small):
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
 
 
+@pytest.fixture(scope="module")
+def small_adiabatic():
+    w = W.small_multipatch(W.ADIABATIC)
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=12, amp=0.05))
+    mu = [0.002 * (1 + np.cos(g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    return w, sv, st, mu
+
+
+def test_project_adjoint_dot_product_adiabatic_wall(small_adiabatic):
+    w, sv, st, mu = small_adiabatic
+    v = rand_like(st, 13)
+    lam = rand_like(st, 14)
+    jv = A.project_jvp_complex(sv, st, v)
+    lhs, rhs = dot(jv, lam), dot(v, A.project_T(sv, lam, None, st))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+def test_step_adjoint_dot_product_adiabatic_wall(small_adiabatic):
+    w, sv, st, mu = small_adiabatic
+    dt = 0.5 * sv.dt(st, mu)
+    v = rand_like(st, 15)
+    lam = rand_like(st, 16)
+    jv = A.step_jvp_complex(sv, st, mu, dt, v)
+    lam_n, _ = A.step_adjoint(sv, st, mu, dt, lam)
+    lhs, rhs = dot(jv, lam), dot(v, lam_n)
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+
+
+@pytest.mark.parametrize("N,C", [(10, 27), (37, 29), (64, 27)])
+def test_fc_filter_transpose(N, C):
+    rng = np.random.default_rng(N + 1)
+    x, y = rng.normal(size=(3, N)), rng.normal(size=(3, N))
+    lhs = np.sum(fc.fc_filter(x, 5, C, 10.0, 14) * y)
+    rhs = np.sum(x * fc.fc_filter_T(y, 5, C, 10.0, 14))
+    assert abs(lhs - rhs) < 1e-13 * np.abs(x).sum() * np.abs(y).max() * 10
+
+
+@pytest.mark.parametrize("fix", ["small", "small_adiabatic"])
+def test_filter_adjoint_dot_product(fix, request):
+    w, sv, st, mu = request.getfixturevalue(fix)
+    v = rand_like(st, 21)
+    lam = rand_like(st, 22)
+    jv = A.filter_jvp_complex(sv, st, v)
+    lhs, rhs = dot(jv, lam), dot(v, A.filter_T(sv, lam, st))
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs), (lhs, rhs)
+
+
+def test_step_adjoint_with_filter_dot_product(small_adiabatic):
+    w, sv, st, mu = small_adiabatic
+    dt = 0.5 * sv.dt(st, mu)
+    v = rand_like(st, 23)
+    lam = rand_like(st, 24)
+    jv = A.step_jvp_complex(sv, st, mu, dt, v, filt=True)
+    lam_n, _ = A.step_adjoint(sv, st, mu, dt, lam, filt=True)
+    lhs, rhs = dot(jv, lam), dot(v, lam_n)
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+
+
 def test_step_adjoint_dot_product(small):
     w, sv, st, mu = small
     dt = 0.5 * sv.dt(st, mu)

@@ -175,3 +175,34 @@ def test_stored_sod_reference_matches_oracle():
         st = sv.step(st, n)
         assert abs(sv.last_dt - ref["dt"][n]) <= 1e-15 * ref["dt"][n]
     assert ref["state"].shape == (4, 128, 128) and np.isfinite(ref["state"]).all()
+
+
+def test_adiabatic_weights():
+    # d = 2: p = a0 (p'(0) = 0) through theta_1; d = 3: p = a0 + a2 x^2 through
+    # theta_1, theta_2 gives a0 = (4 theta_1 - theta_2) / 3
+    assert S.adiabatic_weights(2) == (1.0,)
+    w3 = S.adiabatic_weights(3)
+    assert abs(w3[0] - 4 / 3) < 1e-15 and abs(w3[1] + 1 / 3) < 1e-15
+    for d in (2, 3, 4, 5, 6):
+        w = np.array(S.adiabatic_weights(d))
+        j = np.arange(1, d, dtype=float)
+        assert abs(w.sum() - 1.0) < 1e-13  # constants
+        for k in range(2, d):  # x^k has zero slope at 0 and value 0 there
+            assert abs(w @ j ** k) < 1e-11 * j.max() ** k
+
+
+def test_adiabatic_wall_condition():
+    # after the wall overwrite: zero momenta at the wall, and the temperature along each
+    # wall-normal line has zero slope at the wall (degree d-1 fit through the wall value
+    # and the d-1 inward values)
+    w = W.small_multipatch(W.ADIABATIC)
+    sv = S.Solver(w)
+    st = sv.apply_bc(W.random_smooth_state(w, seed=3, amp=0.1))
+    e = st[0]
+    assert np.all(e[1][0] == 0.0) and np.all(e[2][0] == 0.0)
+    th = euler.temperature(e, w.params.gamma)
+    d = w.params.d
+    x = np.arange(d, dtype=float)
+    for i in range(0, e.shape[2], 7):
+        c = np.polyfit(x, th[:d, i], d - 1)
+        assert abs(c[-2]) < 1e-9 * np.abs(th[:d, i]).max(), c  # slope at the wall
