@@ -18,6 +18,7 @@ _LIBPATH = os.path.join(_HERE, "_lib", "libfcsdnn.so")
 _lib = None
 
 FC_OK = 0
+FC_ERR_INVALID, FC_ERR_CUDA, FC_ERR_DONOR, FC_ERR_OVERLAP, FC_ERR_NONFINITE = 1, 2, 3, 4, 5
 STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID", 2: "FC_ERR_CUDA", 3: "FC_ERR_DONOR", 4: "FC_ERR_OVERLAP",
           5: "FC_ERR_NONFINITE", 6: "FC_ERR_TIMEOUT", 7: "FC_ERR_UNIMPLEMENTED", 8: "FC_ERR_OOM"}
 STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4, 8, 16

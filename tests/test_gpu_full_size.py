@@ -51,11 +51,17 @@ def full(gpu_lib):
             if 0 < nb < sizes[k] and k != big:
                 holed = k
                 break
+    blanked = None  # a patch entirely inside the hole: no lines, zero RHS
+    for k in aff:
+        x0, x1, y0, y1 = w.patches[k].geom
+        if max(x0 * x0, x1 * x1) + max(y0 * y0, y1 * y1) < 1.0:
+            blanked = k
+            break
     rng = np.random.default_rng(7)
     rand = [int(k) for k in rng.choice(aff, 2, replace=False)]
-    sample = sorted({0, big, small, holed, *rand} - {None})
+    sample = sorted({0, big, small, holed, blanked, *rand} - {None})
     offs = np.concatenate([[0], np.cumsum(sizes)])
-    return w, ctx, sv, sample, offs
+    return w, ctx, sv, sample, offs, blanked
 
 
 def _state(w, seed):
@@ -83,7 +89,7 @@ def _patch(t, offs, k, P, ncomp=4):
 
 @pytest.mark.parametrize("which", ["smooth", "half_inviscid"])
 def test_full_size_rhs_sampled(full, which):
-    w, ctx, sv, sample, offs = full
+    w, ctx, sv, sample, offs, blanked = full
     st, e = _state(w, seed=31)
     mu = _mu_fields(w)[which]
     m = torch.from_numpy(np.concatenate([a.ravel() for a in mu])).cuda()
@@ -99,10 +105,12 @@ def test_full_size_rhs_sampled(full, which):
         got.append(_patch(out, offs, k, P).reshape(4, p.n2, p.n1))
     err = rel_err_normwise(got, ref)
     assert err < RHS_TOL, (sample, err, rel_err(got, ref))
+    if blanked is not None:
+        assert np.all(_patch(out, offs, blanked, P) == 0.0)
 
 
 def test_full_size_filter_sampled(full):
-    w, ctx, sv, sample, offs = full
+    w, ctx, sv, sample, offs, blanked = full
     st, e = _state(w, seed=37)
     ctx.filter(e)
     torch.cuda.synchronize()

@@ -1,0 +1,50 @@
+"""Host-side validation of fc_init_patches: bad descriptors and geometries are rejected
+with a status before any device work (no GPU needed)."""
+import dataclasses
+
+import pytest
+
+from paper_2506_16076_gb300 import fcsdnn, workloads as W
+
+
+def _status(w):
+    with pytest.raises(fcsdnn.FcError) as ei:
+        fcsdnn.Context(w)
+    return ei.value.status
+
+
+def _box(n1, n2, side=(W.DIRICHLET,) * 4, geom=(0.0, 1.0, 0.0, 1.0)):
+    fs = (1.4, 1.0, 0.0, 1.0)
+    return W.PatchDesc(W.AFFINE, n1, n2, geom, side, bc=(fs,) * 4)
+
+
+def _wl(patches, **prm):
+    return W.Workload("edge", patches, W.Params(**prm), (1.4, 1.0, 0.0, 1.0), "freestream", 1)
+
+
+def test_too_few_points_is_invalid():
+    assert _status(_wl([_box(1, 16)])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_unknown_patch_kind_is_invalid():
+    p = dataclasses.replace(_box(16, 16), kind=7)
+    assert _status(_wl([p])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_wall_on_a_periodic_side_is_invalid():
+    w = W.small_multipatch()
+    og = w.patches[0]
+    bad = dataclasses.replace(og, side=(W.ADIABATIC, og.side[1], og.side[2], og.side[3]))
+    assert _status(dataclasses.replace(w, patches=[bad] + w.patches[1:])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_receivers_without_donor_are_rejected():
+    # two boxes with facing internal sides that do not overlap: their fringe points
+    # have no donor (donor-receiver condition, Sec. 3.4.1)
+    a = _box(32, 32, (W.DIRICHLET, W.INTERNAL, W.DIRICHLET, W.DIRICHLET), (0.0, 1.0, 0.0, 1.0))
+    b = _box(32, 32, (W.INTERNAL, W.DIRICHLET, W.DIRICHLET, W.DIRICHLET), (2.0, 3.0, 0.0, 1.0))
+    assert _status(_wl([a, b])) == fcsdnn.FC_ERR_DONOR
+
+
+def test_bad_parameters_are_invalid():
+    assert _status(_wl([_box(16, 16)], win_r=0)) == fcsdnn.FC_ERR_INVALID
