@@ -28,18 +28,24 @@ class Trajectory:
         self.flags = []  # STEP_FILTER or 0, per step
 
 
-def forward(ctx, e0, nsteps, K, flags=0, filter=False):
+def forward(ctx, e0, nsteps, K, flags=0, filter=False, store_mu=True, first_filtered=1):
     """Run nsteps steps from e0 (not modified); returns (e_N, Trajectory). filter: apply
-    the per-step filter on steps n >= 1."""
+    the per-step filter on steps n >= first_filtered. store_mu False keeps only the
+    checkpoints and the time steps: the backward run then recomputes each step's
+    viscosity from the replayed state (the classifier and the viscosity are
+    deterministic, so it is the same mu), trading one viscosity evaluation per step for
+    P doubles of memory per step."""
     e = e0.clone()
     tr = Trajectory(K)
     tr.checkpoints[0] = e0.clone()
+    mu = None
     for n in range(nsteps):
-        mu = torch.empty(ctx.P, dtype=torch.float64, device=e.device)
+        if store_mu or mu is None:
+            mu = torch.empty(ctx.P, dtype=torch.float64, device=e.device)
         dt = torch.zeros(1, dtype=torch.float64, device=e.device)
-        f = fcsdnn.STEP_FILTER if (filter and n >= 1) else 0
+        f = fcsdnn.STEP_FILTER if (filter and n >= first_filtered) else 0
         ctx.rk_step(e, dt, mu, (flags & ~fcsdnn.STEP_FILTER) | f)
-        tr.mus.append(mu)
+        tr.mus.append(mu if store_mu else None)
         tr.dts.append(dt)
         tr.flags.append(f)
         if (n + 1) % K == 0 and n + 1 < nsteps:
@@ -48,13 +54,24 @@ def forward(ctx, e0, nsteps, K, flags=0, filter=False):
 
 
 def replay(ctx, tr, e0, n0, n1):
-    """States e_{n0}..e_{n1-1} recomputed from e_{n0} with the recorded mu, dt and filter flag."""
+    """States e_{n0}..e_{n1-1} recomputed from e_{n0} with the recorded dt and filter flag
+    and the recorded (or recomputed) mu; returns (states, mus)."""
     out = [e0.clone()]
+    mus = []
     e = e0.clone()
-    for n in range(n0, n1 - 1):
-        ctx.rk_step(e, tr.dts[n], tr.mus[n], fcsdnn.STEP_FROZEN_MU | fcsdnn.STEP_FIXED_DT | tr.flags[n])
-        out.append(e.clone())
-    return out
+    for n in range(n0, n1):
+        mu = tr.mus[n]
+        if mu is None:  # the forward viscosity of step n: from its projected input state
+            mu = torch.empty(ctx.P, dtype=torch.float64, device=e.device)
+            ep = e.clone()
+            ctx.project(ep)
+            ctx.viscosity(ep, mu)
+            del ep
+        mus.append(mu)
+        if n < n1 - 1:
+            ctx.rk_step(e, tr.dts[n], mu, fcsdnn.STEP_FROZEN_MU | fcsdnn.STEP_FIXED_DT | tr.flags[n])
+            out.append(e.clone())
+    return out, mus
 
 
 def backward(ctx, tr, lam_N):
@@ -67,10 +84,11 @@ def backward(ctx, tr, lam_N):
     for si in range(len(starts) - 1, -1, -1):
         n0 = starts[si]
         n1 = starts[si + 1] if si + 1 < len(starts) else nsteps
-        states = replay(ctx, tr, tr.checkpoints[n0], n0, n1)
+        states, mus = replay(ctx, tr, tr.checkpoints[n0], n0, n1)
         for n in range(n1 - 1, n0 - 1, -1):
-            ctx.adjoint_step(states[n - n0], tr.mus[n], tr.dts[n], lam, nxt, gbc, tr.flags[n])
+            ctx.adjoint_step(states[n - n0], mus[n - n0], tr.dts[n], lam, nxt, gbc, tr.flags[n])
             lam, nxt = nxt, lam
+        del states, mus
     return lam, gbc
 
 

@@ -120,6 +120,20 @@ def test_drag_gradients_vs_central_differences(gpu_lib):
         assert abs(fd - ad) <= 1e-5 * abs(dJdrho).max().item(), (p, fd, ad)
 
 
+def test_lean_checkpointing_matches_stored_mu(gpu_lib):
+    # recomputing each step's viscosity from the replayed state gives the same adjoint
+    w = W.small_multipatch(W.ADIABATIC)
+    ctx = gpu_lib.Context(w)
+    e0 = to_dev(W.random_smooth_state(w, seed=19, amp=0.05))
+    g = torch.randn_like(e0)
+    _, tr = ADJ.forward(ctx, e0, 6, 3, filter=True)
+    lam_a, gbc_a = ADJ.backward(ctx, tr, g)
+    _, tr2 = ADJ.forward(ctx, e0, 6, 3, filter=True, store_mu=False)
+    assert all(m is None for m in tr2.mus)
+    lam_b, gbc_b = ADJ.backward(ctx, tr2, g)
+    assert torch.equal(lam_a, lam_b) and torch.equal(gbc_a, gbc_b)
+
+
 def test_autograd_function_matches_driver(gpu_lib):
     w = mach2_small()
     ctx = gpu_lib.Context(w)
