@@ -173,7 +173,8 @@ def peaks():
     return p
 
 
-KERNEL_SOURCES = ["fc_kernels.cu", "fc_line.cuh", "fc_internal.h"]
+# the kernels and the host code that chooses their plans and launch shapes
+KERNEL_SOURCES = ["fc_kernels.cu", "fc_line.cuh", "fc_internal.h", "fc_host.cpp"]
 
 
 def kernel_sources_sha():
