@@ -148,7 +148,12 @@ fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, do
 /* One time step of Algorithm 1 in place on e_dev: project, viscosity (unless
  * FROZEN_MU), filter (if FILTER), project, dt (unless FIXED_DT; written to
  * *dt_dev), then five SSPRK-4 stages, each followed by the boundary overwrite
- * and the exchange. mu_dev: P doubles, written (or read with FROZEN_MU). */
+ * and the exchange. mu_dev: P doubles, written (or read with FROZEN_MU).
+ * Batched (no PER_PATCH), the length classes of a pass and the curvilinear chain of a
+ * stage run on the context's own side streams, forked from and joined back into
+ * `stream` with events; the call is ordered on `stream` like a single-stream one.
+ * FCSDNN_CONCURRENT=0 in the environment at fc_init_patches keeps everything on
+ * `stream`. */
 fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
 
 /* Discrete adjoint of one fc_rk_step with mu and dt frozen (the smoothness
@@ -186,7 +191,10 @@ uint64_t fc_launch_count(const fc_ctx *ctx);
  * outside graph capture is bracketed by CUDA events on the call's stream.
  * fc_profile_read() synchronises the device, folds the recorded pairs into
  * per-group totals and returns the number of groups (-1 on error); fc_profile_get()
- * returns group k: its name (owned by the context), total milliseconds and launches. */
+ * returns group k: its name (owned by the context), total milliseconds and launches.
+ * While enabled, the batched passes run one after another on the call's stream (no
+ * overlap of length classes or of the curvilinear and affine chains), so each group's
+ * time is its own. */
 fc_status fc_profile_enable(fc_ctx *ctx, int enable);
 int fc_profile_read(fc_ctx *ctx);
 fc_status fc_profile_get(const fc_ctx *ctx, int k, const char **name, double *ms, int *launches);

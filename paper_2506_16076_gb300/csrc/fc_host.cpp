@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -165,8 +166,34 @@ struct fc_ctx {
   uint64_t glaunches = 0;
   cudaStream_t gstream = nullptr;
 
+  // concurrency inside a pass (length classes) and between the affine and curvilinear
+  // chains of a stage: side streams and fork / join events, created on first use
+  static constexpr int NSIDE = 3;
+  cudaStream_t side[NSIDE] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork_ev[2] = {nullptr, nullptr};
+  cudaEvent_t join_ev[NSIDE] = {nullptr, nullptr, nullptr};
+  bool side_ready = false;
+  bool concurrent = true;
+  bool ensure_side() {
+    if (side_ready) return true;
+    for (int k = 0; k < NSIDE; ++k)
+      if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    for (int k = 0; k < 2; ++k)
+      if (cudaEventCreateWithFlags(&fork_ev[k], cudaEventDisableTiming) != cudaSuccess) return false;
+    side_ready = true;
+    return true;
+  }
+
   ~fc_ctx() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    for (int k = 0; k < NSIDE; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (join_ev[k]) cudaEventDestroy(join_ev[k]);
+    }
+    for (int k = 0; k < 2; ++k)
+      if (fork_ev[k]) cudaEventDestroy(fork_ev[k]);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
   }
@@ -1194,6 +1221,12 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   T.gamma = prm->gamma;
   T.d = prm->d;
   set_kernel_attributes();
+  {  // FCSDNN_CONCURRENT=0 runs every batched pass on the caller's stream alone (A/B timing)
+    const char* v = getenv("FCSDNN_CONCURRENT");
+    c->concurrent = !(v && v[0] == '0');
+    // side streams and events now, not during a later graph capture
+    if (c->concurrent && !c->ensure_side()) return bad("could not create the side streams");
+  }
 
   // normaliser of eq. (multipatch_W_norm): window sums of the generation indicator, own + other patches
   {
@@ -1254,22 +1287,43 @@ struct Prof {
   }
 };
 
-// run one pass over a queue, batched (one launch per length class) or one launch per patch
+// run one pass over a queue, batched (one launch per length class) or one launch per patch.
+// Batched: the length classes of a pass touch disjoint lines, so classes after the first
+// run on side streams forked from st and joined back into it (their tails overlap;
+// inside a CUDA graph they become parallel branches). first_side: the first side
+// stream this pass may use (a chain already running on a side stream keeps it). While
+// the per-pass profile is on, passes run one after another so that each pass's time is
+// its own.
 template <class F>
-void run_queue(fc_ctx* c, const fc_ctx::Queue& q, bool per_patch, cudaStream_t st, const char* name, F&& launch) {
+void run_queue(fc_ctx* c, const fc_ctx::Queue& q, bool per_patch, cudaStream_t st, const char* name, F&& launch,
+               int first_side = 1) {
   if (q.n == 0) return;
   Prof pr(c, st, name);
   if (!per_patch) {
-    for (size_t k = 0; k < q.classes.size(); ++k) {
+    const int ncls = (int)q.classes.size();
+    const int nside = fc_ctx::NSIDE - first_side;
+    const bool fork = c->concurrent && !c->prof && ncls > 1 && nside > 0 && c->ensure_side();
+    if (fork) cudaEventRecord(c->fork_ev[0], st);
+    for (int k = 0; k < ncls; ++k) {
       const int b = q.classes[k].first, e = q.class_end[k];
-      launch(q.d + b, e - b, q.classes[k].second);
+      cudaStream_t s = st;
+      if (fork && k > 0) {
+        s = c->side[first_side + (k - 1) % nside];
+        if (k - 1 < nside) cudaStreamWaitEvent(s, c->fork_ev[0], 0);
+      }
+      launch(q.d + b, e - b, q.classes[k].second, s);
       c->launches++;
     }
+    if (fork)
+      for (int k = 0; k < std::min(ncls - 1, nside); ++k) {
+        cudaEventRecord(c->join_ev[first_side + k], c->side[first_side + k]);
+        cudaStreamWaitEvent(st, c->join_ev[first_side + k], 0);
+      }
   } else {
     for (size_t p = 0; p < q.pbeg.size(); ++p) {
       const int n = q.pend[p] - q.pbeg[p];
       if (n <= 0) continue;
-      launch(q.dpp + q.pbeg[p], n, q.plmax[p]);
+      launch(q.dpp + q.pbeg[p], n, q.plmax[p], st);
       c->launches++;
     }
   }
@@ -1278,16 +1332,34 @@ void run_queue(fc_ctx* c, const fc_ctx::Queue& q, bool per_patch, cudaStream_t s
 void stage(fc_ctx* c, const StageCoef& sc, const double* mu, bool per_patch, cudaStream_t st) {
   const DevTables& T = c->T;
   const double* e = sc.Ucur;
-  run_queue(c, c->q_gen1, per_patch, st, "gen_A",
-            [&](const Job* j, int n, int L) { launch_gen_A(T, j, n, L, e, c->d_G, st); });
+  // the curvilinear chain (passes A, B, C) and the affine chain (q1, q2) touch different
+  // patches: batched, the curvilinear chain runs on its own side stream
+  const bool overlap =
+      !per_patch && c->concurrent && !c->prof && c->q_gen1.n > 0 && c->q_cart1.n > 0 && c->ensure_side();
+  cudaStream_t sg = st;
+  int gside = 1;
+  if (overlap) {
+    cudaEventRecord(c->fork_ev[1], st);
+    cudaStreamWaitEvent(c->side[0], c->fork_ev[1], 0);
+    sg = c->side[0];
+    gside = fc_ctx::NSIDE;  // no class forks inside the curvilinear chain
+  }
+  run_queue(c, c->q_gen1, per_patch, sg, "gen_A",
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_A(T, j, n, L, e, c->d_G, s); }, gside);
   run_queue(c, c->q_cart1, per_patch, st, "cart_q1",
-            [&](const Job* j, int n, int L) { launch_cart_q1(T, j, n, L, e, mu, c->d_R1, st); });
-  run_queue(c, c->q_gen2, per_patch, st, "gen_B",
-            [&](const Job* j, int n, int L) { launch_gen_B(T, j, n, L, e, mu, c->d_J, c->d_G, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q1(T, j, n, L, e, mu, c->d_R1, s); });
+  run_queue(c, c->q_gen2, per_patch, sg, "gen_B",
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_B(T, j, n, L, e, mu, c->d_J, c->d_G, s); },
+            gside);
   run_queue(c, c->q_cart2, per_patch, st, "cart_q2",
-            [&](const Job* j, int n, int L) { launch_cart_q2(T, j, n, L, mu, c->d_R1, sc, st); });
-  run_queue(c, c->q_gen1, per_patch, st, "gen_C",
-            [&](const Job* j, int n, int L) { launch_gen_C(T, j, n, L, c->d_J, c->d_G, sc, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q2(T, j, n, L, mu, c->d_R1, sc, s); });
+  run_queue(c, c->q_gen1, per_patch, sg, "gen_C",
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_C(T, j, n, L, c->d_J, c->d_G, sc, s); },
+            gside);
+  if (overlap) {
+    cudaEventRecord(c->join_ev[0], c->side[0]);
+    cudaStreamWaitEvent(st, c->join_ev[0], 0);
+  }
   if (c->nfix) {
     Prof pr(c, st, "rk_fixup");
     launch_rk_fixup(T, c->d_fix, c->nfix, sc, st);
@@ -1326,13 +1398,13 @@ void filter(fc_ctx* c, double* e, bool per_patch, cudaStream_t st) {
   const DevTables& T = c->T;
   double* F = c->d_B3;
   run_queue(c, c->q_filt1, per_patch, st, "filter_q1",
-            [&](const Job* j, int n, int L) { launch_filter_q1(T, j, n, L, e, F, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_filter_q1(T, j, n, L, e, F, s); });
   if (c->nfcopy1) {
     launch_filter_copy_q1(T, c->d_fcopy1, c->nfcopy1, e, F, st);
     c->launches++;
   }
   run_queue(c, c->q_filt2, per_patch, st, "filter_q2",
-            [&](const Job* j, int n, int L) { launch_filter_q2(T, j, n, L, F, e, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_filter_q2(T, j, n, L, F, e, s); });
   if (c->nfcopy2) {
     launch_filter_copy_q2(T, c->d_fcopy2, c->nfcopy2, F, e, st);
     c->launches++;
@@ -1346,13 +1418,13 @@ void filterT(fc_ctx* c, const double* lam, const double* pre, const double* filt
   const DevTables& T = c->T;
   cudaMemcpyAsync(out, lam, sizeof(double) * 4 * (size_t)c->P, cudaMemcpyDeviceToDevice, st);
   run_queue(c, c->q_filt2, false, st, "filterT_q2",
-            [&](const Job* j, int n, int L) { launch_filterT_q2(T, j, n, L, lam, filt, MF, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_filterT_q2(T, j, n, L, lam, filt, MF, s); });
   if (c->nfcopy2) {
     launch_filterT_copy2(T, c->d_fcopy2, c->nfcopy2, lam, filt, MF, st);
     c->launches++;
   }
   run_queue(c, c->q_filt1, false, st, "filterT_q1",
-            [&](const Job* j, int n, int L) { launch_filterT_q1(T, j, n, L, MF, pre, out, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_filterT_q1(T, j, n, L, MF, pre, out, s); });
   if (c->nfcopy1) {
     launch_filterT_copy1(T, c->d_fcopy1, c->nfcopy1, MF, pre, out, st);
     c->launches++;
@@ -1416,15 +1488,15 @@ void adj_stage(fc_ctx* c, const double* u, const double* mu, const double* psi, 
   const DevTables& T = c->T;
   cudaMemsetAsync(c->d_R1, 0, sizeof(double) * 4 * (size_t)c->P, st);
   run_queue(c, c->q_gen1, false, st, "adj_gen_A",
-            [&](const Job* j, int n, int L) { launch_adj_gen_A(T, j, n, L, c->d_J, psi, c->d_G, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_A(T, j, n, L, c->d_J, psi, c->d_G, s); });
   run_queue(c, c->q_cart1, false, st, "adj_cart_q1",
-            [&](const Job* j, int n, int L) { launch_adj_cart(T, j, n, L, 0, u, mu, psi, c->d_R1, acc, dt, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_cart(T, j, n, L, 0, u, mu, psi, c->d_R1, acc, dt, s); });
   run_queue(c, c->q_gen2, false, st, "adj_gen_B",
-            [&](const Job* j, int n, int L) { launch_adj_gen_B(T, j, n, L, c->d_J, u, mu, psi, c->d_G, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_B(T, j, n, L, c->d_J, u, mu, psi, c->d_G, s); });
   run_queue(c, c->q_cart2, false, st, "adj_cart_q2",
-            [&](const Job* j, int n, int L) { launch_adj_cart(T, j, n, L, 1, u, mu, psi, c->d_R1, acc, dt, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_cart(T, j, n, L, 1, u, mu, psi, c->d_R1, acc, dt, s); });
   run_queue(c, c->q_gen1, false, st, "adj_gen_C",
-            [&](const Job* j, int n, int L) { launch_adj_gen_C(T, j, n, L, c->d_G, acc, dt, st); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_C(T, j, n, L, c->d_G, acc, dt, s); });
   if (c->nfix) {
     launch_adj_fixup(c->d_fix, c->nfix, c->d_R1, acc, c->P, dt, st);
     c->launches++;
