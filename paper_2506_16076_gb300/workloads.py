@@ -15,6 +15,7 @@ Workloads (stand-ins for the paper's meshes, which are not published):
   cyl_m25_32  [-8,16]x[-12,12] as 32x32 affine patches with seeded uneven sizes
               48..384 (refined toward the body) + 1024x192 O-grid, Mach 25
   cyl_m25_4096 64x64 affine patches with seeded sizes 64..512 + O-grid, Mach 25
+  cyl_m25_32_sub cyl_m25_32 split into the paper's 101 x 101 sub-patches (subpatched)
   The two seeded arrays use the rule n = nmin + round((nmax-nmin)*u*(1-a*dc/dmax)),
   u ~ U[0,1) from numpy.random.default_rng(seed), dc = distance from the patch
   centre to the cylinder centre; a is the taper coefficient.
@@ -222,7 +223,48 @@ def small_multipatch(wall=SLIPWALL):
     return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs, init="freestream", steps=20)
 
 
+def subpatched(w: Workload, n0=83, nv=9):
+    """The paper's sub-patch decomposition (Sec. 3.2.1, eqs. rect, discretization,
+    subpatchesQ) applied to the affine patches of a workload: a line of more than
+    n0 + 2 nv points is re-gridded to N = r (n0 + 1) - 1 + 2 nv points (the smallest r
+    with N >= n; same physical extent) and split into r overlapping sub-patches of
+    n0 + 2 nv points each, starting every n0 + 1 points (neighbours share 2 nv - 1 grid
+    lines). Sub-patch sides inside the parent patch are internal (the exchange copies
+    the coincident grid values); the parent's outer sides keep their types. Shorter
+    lines and the O-grid are kept as they are."""
+    m = n0 + 2 * nv
+    step = n0 + 1
+
+    def split(n, a, b):
+        if n <= m:
+            return [(n, a, b, True, True)]
+        r = -(-(n - m) // step) + 1  # smallest r with r (n0 + 1) - 1 + 2 nv >= n
+        N = r * step - 1 + 2 * nv
+        h = (b - a) / (N - 1)
+        return [(m, a + k * step * h, a + (k * step + m - 1) * h, k == 0, k == r - 1) for k in range(r)]
+
+    out = []
+    for p in w.patches:
+        if p.kind != AFFINE:
+            out.append(p)
+            continue
+        x0, x1, y0, y1 = p.geom
+        for (n2, c, d, lo2, hi2) in split(p.n2, y0, y1):
+            for (n1, a, b, lo1, hi1) in split(p.n1, x0, x1):
+                side = (p.side[0] if lo1 else INTERNAL, p.side[1] if hi1 else INTERNAL,
+                        p.side[2] if lo2 else INTERNAL, p.side[3] if hi2 else INTERNAL)
+                out.append(PatchDesc(AFFINE, n1, n2, (a, b, c, d), side, bc=p.bc, hole=p.hole))
+    return Workload(w.name + "_sub", out, w.params, w.freestream, w.init, w.steps,
+                    {**w.extra, "subpatch": (n0, nv)})
+
+
+def cyl_m25_32_sub():
+    """cyl_m25_32 with its patches split into the paper's 101 x 101 sub-patches."""
+    return subpatched(cyl_m25_32())
+
+
 WORKLOADS = {
+    "cyl_m25_32_sub": cyl_m25_32_sub,
     "sod128": sod128,
     "cyl_m3": cyl_m3,
     "cyl_m2_half": cyl_m2_half,
