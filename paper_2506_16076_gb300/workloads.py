@@ -13,7 +13,8 @@ Workloads (stand-ins for the paper's meshes, which are not published):
   cyl_m2_half same geometry at half resolution (256x48, 80x80), Mach 2 at 2 deg,
               no-slip adiabatic cylinder wall
   cyl_m25_32  [-8,16]x[-12,12] as 32x32 affine patches with seeded uneven sizes
-              48..384 (refined toward the body) + 1024x192 O-grid, Mach 25
+              48..384 (refined toward the body) + 1024x192 O-grid, Mach 25, no-slip
+              adiabatic wall, potential-flow start with a near-wall layer
   cyl_m25_4096 64x64 affine patches with seeded sizes 64..512 + O-grid, Mach 25
   cyl_m25_32_sub cyl_m25_32 split into the paper's 101 x 101 sub-patches (subpatched)
   The two seeded arrays use the rule n = nmin + round((nmax-nmin)*u*(1-a*dc/dmax)),
@@ -197,10 +198,10 @@ def seeded_sizes(nx, ny, nmin, nmax, seed, x0, x1, y0, y1, taper):
 def cyl_m25_array(nx, nmin, nmax, seed, taper, nth, nr, name):
     fs = (1.4, 25.0, 0.0, 1.0)
     sizes = seeded_sizes(nx, nx, nmin, nmax, seed, -8.0, 16.0, -12.0, 12.0, taper)
-    og = _ogrid(nth, nr, 0.5, 1.5, fs)
+    og = _ogrid(nth, nr, 0.5, 1.5, fs, ADIABATIC)
     cart = _cart_array(nx, nx, -8.0, 16.0, -12.0, 12.0, None, 19, fs, hole=(0.0, 0.0, 1.0), sizes=sizes)
     return Workload(name, [og] + cart, Params(d=5, C0=27, c_policy=2), freestream=fs, init="potential", steps=200,
-                    extra={"taper": taper, "seed": seed, "cyl_radius": 0.5, "cutoff": 3.0})
+                    extra={"taper": taper, "seed": seed, "cyl_radius": 0.5, "cutoff": 3.0, "wall_layer": 0.05})
 
 
 def cyl_m25_32():
@@ -308,18 +309,21 @@ def initial_state(w: Workload):
             left = x < w.extra["x_split"]
             prim = [np.where(left, L[k], R[k]) for k in range(4)]
         elif w.init == "potential":
-            prim = potential_flow_prim(x, y, w.freestream, w.extra["cyl_radius"], w.extra["cutoff"])
+            prim = potential_flow_prim(x, y, w.freestream, w.extra["cyl_radius"], w.extra["cutoff"],
+                                       w.extra.get("wall_layer", 0.0))
         else:
             prim = [np.full(x.shape, w.freestream[k]) for k in range(4)]
         out.append(prim_to_cons(*prim, gamma=w.params.gamma))
     return out
 
 
-def potential_flow_prim(x, y, fs, R, cutoff):
+def potential_flow_prim(x, y, fs, R, cutoff, wall_layer=0.0):
     """Free-stream density and pressure with the incompressible potential-flow velocity
     around a cylinder of radius R at the origin, u - i v = U (e^{-ia} - R^2 e^{ia} / z^2),
     whose wall-normal velocity vanishes on r = R. The disturbance is switched off smoothly
-    between r = cutoff and 2 cutoff so that the outer boundaries see the free stream."""
+    between r = cutoff and 2 cutoff so that the outer boundaries see the free stream.
+    wall_layer > 0: the velocity is multiplied by 1 - exp(-((r - R) / wall_layer)^2), so
+    that it also vanishes at the wall (a start consistent with a no-slip wall)."""
     rho, u0, v0, p = fs
     U = np.hypot(u0, v0)
     a = np.arctan2(v0, u0)
@@ -330,6 +334,8 @@ def potential_flow_prim(x, y, fs, R, cutoff):
     t = np.clip((r - cutoff) / cutoff, 0.0, 1.0)
     sw = np.where(t <= 0, 1.0, np.where(t >= 1, 0.0, 0.5 * (1 + np.cos(np.pi * t))))
     w = u0 - 1j * v0 + sw * dist
+    if wall_layer > 0:
+        w = w * np.where(r > R, 1.0 - np.exp(-(((r - R) / wall_layer) ** 2)), 0.0)
     return [np.full(x.shape, rho), w.real, -w.imag, np.full(x.shape, p)]
 
 
