@@ -84,8 +84,8 @@ def window_starts(g, direction):
     st = np.full((g.n2, g.n1), -1, np.int64)
     segs = g.seg1 if direction == 1 else g.seg2
     for (line, a, n, per) in segs:
-        if per:
-            idx = np.arange(n) - 3
+        if per:  # centred, wrapped: the start is stored modulo n (negative marks "no window")
+            idx = np.mod(np.arange(n) - 3, n)
         elif n < 7:
             continue
         else:

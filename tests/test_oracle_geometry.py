@@ -100,3 +100,19 @@ def test_sdnn_standin_on_synthetic_classes():
     assert (cls - 1 == y).mean() > 0.9
     flat = np.full((3, 7), 2.0)
     assert (V.classify(flat)[0] == 4).all()
+
+
+def test_every_point_of_a_periodic_line_has_its_centred_window():
+    # Sec. 5: each point's classifier input is the 7-point stencil centred on it; along
+    # a periodic q1 line it wraps, so the points next to the seam (i = 0, 1, 2 and
+    # n - 3 .. n - 1) keep a centred window too
+    og = W.small_multipatch().patches[0]
+    g = G.PatchGeo(og, W.Params(d=5, C0=27, c_policy=2))
+    st = V.window_starts(g, 1)
+    assert (st >= 0).all()
+    i = np.arange(g.n1)
+    assert np.array_equal(st[0], np.mod(i - 3, g.n1))
+    # the non-periodic q2 lines: windows clamped inside the line
+    s2 = V.window_starts(g, 2)
+    j = np.arange(g.n2)
+    assert np.array_equal(s2[:, 0], np.clip(j - 3, 0, g.n2 - 7))
