@@ -48,8 +48,10 @@ typedef enum {
   FC_ERR_OOM = 8            /* device allocation failed */
 } fc_status;
 
-/* patch kinds (Sec. 3.1): affine box (C/I-type), annulus around an obstacle with a periodic angle */
-enum { FC_PATCH_AFFINE = 0, FC_PATCH_OGRID = 1 };
+/* patch kinds (Sec. 3.1): affine box (C/I-type), annulus around an obstacle with a periodic
+ * angle, and a general curvilinear grid given point by point (S-type patches along any
+ * smooth boundary) */
+enum { FC_PATCH_AFFINE = 0, FC_PATCH_OGRID = 1, FC_PATCH_GRID = 2 };
 /* side types, side order (q1=0, q1=1, q2=0, q2=1) (Sec. 3.4 internal/external sides, Sec. 4.2).
  * SLIPWALL: the wall-normal momentum is set to 0 at every stage.
  * ADIABATIC: no-slip adiabatic wall (Sec. 4.2, Remarks adiabatic_th and adiabatic): both
@@ -68,7 +70,8 @@ enum {
 /* One patch (Sec. 3.1-3.2). AFFINE: geom = (x0, x1, y0, y1), q1 -> x, q2 -> y.
  * OGRID: geom = (xc, yc, r0, r1), q1 -> angle (periodic, n1 points), q2 -> radius.
  * bc[s] = primitive (rho, u, v, p) imposed on side s when it is DIRICHLET.
- * hole = (xc, yc, R): points with distance < R are blanked (R <= 0: none). */
+ * hole = (xc, yc, R): points of AFFINE and GRID patches with distance < R are blanked
+ * (R <= 0: none; OGRID patches ignore it). */
 typedef struct {
   int kind;
   int n1, n2;
@@ -76,6 +79,14 @@ typedef struct {
   int side[4];
   double bc[4][4];
   double hole[3];
+  /* GRID only (NULL otherwise; host arrays, read during fc_init_patches): the physical
+   * coordinates x, y of the grid points (n2 x n1, row-major, q1 fastest) and the metrics
+   * dq/dx as [4][n2 x n1] = (dq1/dx, dq1/dy, dq2/dx, dq2/dy) for the parameters
+   * q1 = i / (n1 - 1) (q1 = i / n1 when sides 0 and 1 are PERIODIC) and q2 = j / (n2 - 1)
+   * (Sec. 3.3). Other patches locate points of a GRID patch by Newton's method on its
+   * 3 x 3 quadratic interpolant, started at the nearest grid point. GRID sides may be
+   * INTERNAL, DIRICHLET, OUTFLOW, ADIABATIC or PERIODIC (q1 only); geom is unused. */
+  const double *x, *y, *metrics;
 } fc_patch_desc;
 
 /* Method parameters. Defaults of the paper: gamma 1.4 (Sec. 2.1), alpha_f 10,
@@ -174,7 +185,7 @@ fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev,
 fc_status fc_adjoint_step(fc_ctx *ctx, const double *e_n_dev, const double *mu_dev, const double *dt_dev,
                           const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, int flags, void *stream);
 
-/* Wall-pressure drag functional J = sum over the wall ring of the first curvilinear
+/* Wall-pressure drag functional J = sum over the wall ring of the first OGRID
  * patch with a slip or adiabatic wall of p n_x r0 dtheta (periodic trapezoid of the integral of
  * wall pressure times n_x, n the outward body normal); J_dev: device scalar.
  * dJde_dev (nullable, [4][P]): dJ/de, zero off the wall. */

@@ -42,7 +42,8 @@ class PatchGeo:
         self.desc = desc
         self.kind = desc.kind
         self.n1, self.n2 = desc.n1, desc.n2
-        self.periodic1 = desc.kind == W.OGRID
+        self.periodic1 = desc.kind == W.OGRID or (
+            desc.kind == W.GRID and desc.side[0] == W.PERIODIC and desc.side[1] == W.PERIODIC)
         # parameter spacings (eq. param-grid without the sub-patch vicinity; periodic: 1/n)
         self.h1 = 1.0 / self.n1 if self.periodic1 else 1.0 / (self.n1 - 1)
         self.h2 = 1.0 / (self.n2 - 1)
@@ -57,6 +58,9 @@ class PatchGeo:
 
     # Sec. 3.3: J = dq/dx
     def _metrics(self):
+        if self.kind == W.GRID:  # given with the grid (Sec. 3.3)
+            self.J = np.array(self.desc.metrics, dtype=np.float64)
+            return
         if self.kind == W.AFFINE:
             x0, x1, y0, y1 = self.desc.geom
             z = np.zeros((self.n2, self.n1))
@@ -71,7 +75,16 @@ class PatchGeo:
 
     def _spacings(self):
         """h_hat (max) and h_tilde (min) distance between index-adjacent points (Sec. 5.1, eq. CFL)."""
-        if self.kind == W.AFFINE:
+        if self.kind == W.GRID:  # from the points (wrapped along a periodic q1)
+            x, y = self.x, self.y
+            if self.periodic1:
+                d1 = np.hypot(np.roll(x, -1, axis=1) - x, np.roll(y, -1, axis=1) - y)
+            else:
+                d1 = np.hypot(x[:, 1:] - x[:, :-1], y[:, 1:] - y[:, :-1])
+            d2 = np.hypot(x[1:] - x[:-1], y[1:] - y[:-1])
+            self.hhat = float(max(d1.max(), d2.max()))
+            self.htil = float(min(d1.min(), d2.min()))
+        elif self.kind == W.AFFINE:
             x0, x1, y0, y1 = self.desc.geom
             hx, hy = (x1 - x0) / (self.n1 - 1), (y1 - y0) / (self.n2 - 1)
             self.hhat, self.htil = max(hx, hy), min(hx, hy)
@@ -83,7 +96,7 @@ class PatchGeo:
 
     def _blank(self):
         hx, hy, R = self.desc.hole
-        if R > 0 and self.kind == W.AFFINE:
+        if R > 0 and self.kind != W.OGRID:
             dx, dy = self.x - hx, self.y - hy
             self.blank = (dx * dx + dy * dy) < R * R
         else:
@@ -151,6 +164,8 @@ class PatchGeo:
 
     # inverse map: physical point -> fractional grid indices (s1, s2)
     def frac_index(self, x, y):
+        if self.kind == W.GRID:
+            return self._grid_inverse(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
         if self.kind == W.AFFINE:
             x0, x1, y0, y1 = self.desc.geom
             return (x - x0) / (x1 - x0) * (self.n1 - 1), (y - y0) / (y1 - y0) * (self.n2 - 1)
@@ -158,6 +173,82 @@ class PatchGeo:
         th = np.mod(np.arctan2(y - yc, x - xc), 2 * np.pi)
         r = np.hypot(x - xc, y - yc)
         return th / (2 * np.pi) * self.n1, (r - r0) / (r1 - r0) * (self.n2 - 1)
+
+    def _grid_inverse(self, x, y):
+        """GRID patches: Newton's method on the 3 x 3 quadratic (Lagrange) interpolant of
+        the grid around a stencil centre c, started at the nearest grid point (ties:
+        smallest flat index), which is also the first centre (clamped to [1, n - 2] along
+        a non-periodic direction). A direction's centre moves to rnd(s) (clamped) only when
+        the estimate is more than 0.75 from it, so that Newton cannot cycle between two
+        neighbouring stencils across a half-integer. At most 30 steps, stopping after a
+        step with |ds1| + |ds2| < 1e-11 (Newton's quadratic convergence leaves an error
+        at rounding level). Queries more than the largest spacing outside the bounding
+        box, and failed iterations, get indices far outside the grid."""
+        shape = np.shape(x)
+        xq, yq = np.ravel(x), np.ravel(y)
+        n1, n2 = self.n1, self.n2
+        X, Y = self.x.ravel(), self.y.ravel()
+        h = self.hhat
+        s1 = np.full(xq.shape, -1e9)
+        s2 = np.full(xq.shape, -1e9)
+        x0, x1, y0, y1 = X.min(), X.max(), Y.min(), Y.max()
+        near = (xq >= x0 - h) & (xq <= x1 + h) & (yq >= y0 - h) & (yq <= y1 + h)
+        idx = np.nonzero(near)[0]
+        if idx.size == 0:
+            return s1.reshape(shape), s2.reshape(shape)
+        k0 = np.array([int(np.argmin((X - xq[q]) ** 2 + (Y - yq[q]) ** 2)) for q in idx])
+        a1 = (k0 % n1).astype(np.float64)
+        a2 = (k0 // n1).astype(np.float64)
+        active = np.ones(idx.size, bool)
+        done = np.zeros(idx.size, bool)
+        xs, ys = xq[idx], yq[idx]
+
+        def centre1(a):
+            c = rnd(a)
+            return c if self.periodic1 else np.clip(c, 1, n1 - 2)
+
+        c1 = centre1(a1)
+        c2 = np.clip(rnd(a2), 1, n2 - 2)
+        for _ in range(30):
+            if not active.any():
+                break
+            c1 = np.where(np.abs(a1 - c1) > 0.75, centre1(a1), c1)
+            c2 = np.where(np.abs(a2 - c2) > 0.75, np.clip(rnd(a2), 1, n2 - 2), c2)
+            t1, t2 = a1 - c1, a2 - c2
+            L = [0.5 * t1 * (t1 - 1.0), 1.0 - t1 * t1, 0.5 * t1 * (t1 + 1.0)]
+            dL = [t1 - 0.5, -2.0 * t1, t1 + 0.5]
+            M = [0.5 * t2 * (t2 - 1.0), 1.0 - t2 * t2, 0.5 * t2 * (t2 + 1.0)]
+            dM = [t2 - 0.5, -2.0 * t2, t2 + 0.5]
+            Xv = np.zeros_like(a1); Yv = np.zeros_like(a1)
+            Xa = np.zeros_like(a1); Xb = np.zeros_like(a1); Ya = np.zeros_like(a1); Yb = np.zeros_like(a1)
+            for b in range(3):
+                jj = c2 + b - 1
+                for a in range(3):
+                    ii = c1 + a - 1
+                    if self.periodic1:
+                        ii = np.mod(ii, n1)
+                    k = jj * n1 + ii
+                    w, wa, wb = L[a] * M[b], dL[a] * M[b], L[a] * dM[b]
+                    Xv = Xv + w * X[k]; Yv = Yv + w * Y[k]
+                    Xa = Xa + wa * X[k]; Xb = Xb + wb * X[k]
+                    Ya = Ya + wa * Y[k]; Yb = Yb + wb * Y[k]
+            rx, ry = Xv - xs, Yv - ys
+            det = Xa * Yb - Xb * Ya
+            ok = active & (np.abs(det) > 0.0)
+            active &= ok
+            safe = np.where(ok, det, 1.0)
+            d1 = -(Yb * rx - Xb * ry) / safe
+            d2 = -(-Ya * rx + Xa * ry) / safe
+            a1 = np.where(active, a1 + d1, a1)
+            a2 = np.where(active, a2 + d2, a2)
+            active &= (np.abs(a1) < 1e12) & (np.abs(a2) < 1e12)
+            conv = active & (np.abs(d1) + np.abs(d2) < 1e-11)
+            done |= conv
+            active &= ~conv
+        res1 = np.where(done, np.mod(a1, n1) if self.periodic1 else a1, -1e9)
+        res2 = np.where(done, a2, -1e9)
+        s1[idx], s2[idx] = res1, res2
+        return s1.reshape(shape), s2.reshape(shape)
 
     def contains(self, s1, s2):
         ok2 = (s2 >= -CONTAIN_TOL) & (s2 <= self.n2 - 1 + CONTAIN_TOL)

@@ -46,6 +46,11 @@ struct HPatch {
   std::vector<int> depth;
   std::vector<Seg> seg1, seg2;
   double bx0, bx1, by0, by1;   // bounding box
+  // GRID patches: metrics [4][n2*n1] as given, and a uniform bucket grid over the points
+  std::vector<double> jm;
+  double hcell = 0;
+  int hnx = 0, hny = 0;
+  std::vector<int> hstart, hidx;  // points of bucket b: hidx[hstart[b] .. hstart[b+1])
 };
 
 template <class T>
@@ -95,6 +100,8 @@ struct fc_ctx {
   Queue q_cart1, q_cart2, q_gen1, q_gen2, q_filt1, q_filt2;
   int* d_fix = nullptr;
   int nfix = 0;
+  GFix* d_gfix = nullptr;
+  int ngfix = 0;
   int* d_fcopy1 = nullptr;
   int nfcopy1 = 0;
   int* d_fcopy2 = nullptr;
@@ -242,6 +249,10 @@ void grid_coords(HPatch& h) {
   const fc_patch_desc& d = h.d;
   h.x.resize((size_t)h.n1 * h.n2);
   h.y.resize(h.x.size());
+  if (d.kind == FC_PATCH_GRID) {
+    std::copy(d.x, d.x + h.x.size(), h.x.begin());
+    std::copy(d.y, d.y + h.y.size(), h.y.begin());
+  } else
   for (int j = 0; j < h.n2; ++j)
     for (int i = 0; i < h.n1; ++i) {
       const size_t k = (size_t)j * h.n1 + i;
@@ -261,9 +272,104 @@ void grid_coords(HPatch& h) {
   h.by1 = *std::max_element(h.y.begin(), h.y.end());
 }
 
+// GRID patches: the grid point nearest to (x, y) (ties: the smallest flat index), by
+// rings of buckets around the query's bucket; -1 if (x, y) is more than one bucket
+// outside the patch's bounding box
+long long grid_nearest(const HPatch& h, double x, double y) {
+  if (x < h.bx0 - h.hcell || x > h.bx1 + h.hcell || y < h.by0 - h.hcell || y > h.by1 + h.hcell) return -1;
+  const int cx = std::min(std::max((int)std::floor((x - h.bx0) / h.hcell), 0), h.hnx - 1);
+  const int cy = std::min(std::max((int)std::floor((y - h.by0) / h.hcell), 0), h.hny - 1);
+  long long best = -1;
+  double bd = 0;
+  for (int r = 0; r <= std::max(h.hnx, h.hny); ++r) {
+    for (int by = cy - r; by <= cy + r; ++by) {
+      if (by < 0 || by >= h.hny) continue;
+      for (int bx = cx - r; bx <= cx + r; ++bx) {
+        if (bx < 0 || bx >= h.hnx) continue;
+        if (std::max(std::abs(bx - cx), std::abs(by - cy)) != r) continue;
+        const int b = by * h.hnx + bx;
+        for (int q = h.hstart[b]; q < h.hstart[b + 1]; ++q) {
+          const long long k = h.hidx[q];
+          const double dx = h.x[k] - x, dy = h.y[k] - y, dd = dx * dx + dy * dy;
+          if (best < 0 || dd < bd || (dd == bd && k < best)) {
+            best = k;
+            bd = dd;
+          }
+        }
+      }
+    }
+    // every point of a bucket in ring r + 1 or beyond is at least r buckets away
+    if (best >= 0 && bd < (r * h.hcell) * (r * h.hcell)) break;
+  }
+  return best;
+}
+
+// GRID patches: fractional indices of (x, y) by Newton's method on the 3 x 3 quadratic
+// (Lagrange) interpolant of the grid around a stencil centre, started at the nearest
+// grid point, which is also the first centre (clamped to [1, n - 2] along a
+// non-periodic direction). A direction's centre moves to rnd(s) (clamped) only when the
+// estimate is more than 0.75 from it: Newton cannot cycle between two neighbouring
+// stencils across a half-integer. At most 30 steps, stopping after a step with
+// |ds1| + |ds2| < 1e-11 (quadratic convergence leaves an error at rounding level).
+// Returns false (and indices far outside the grid) when there is no nearby point or
+// the iteration breaks down.
+bool grid_inverse(const HPatch& h, double x, double y, double& s1, double& s2) {
+  s1 = s2 = -1e9;
+  const long long k0 = grid_nearest(h, x, y);
+  if (k0 < 0) return false;
+  double a1 = (double)(k0 % h.n1), a2 = (double)(k0 / h.n1);
+  auto centre1 = [&](double a) {
+    const long long c = rnd_half_up(a);
+    return h.periodic1 ? c : std::min<long long>(std::max<long long>(c, 1), h.n1 - 2);
+  };
+  auto centre2 = [&](double a) { return std::min<long long>(std::max<long long>(rnd_half_up(a), 1), h.n2 - 2); };
+  long long c1 = centre1(a1), c2 = centre2(a2);
+  for (int it = 0; it < 30; ++it) {
+    if (std::fabs(a1 - (double)c1) > 0.75) c1 = centre1(a1);
+    if (std::fabs(a2 - (double)c2) > 0.75) c2 = centre2(a2);
+    const double t1 = a1 - (double)c1, t2 = a2 - (double)c2;
+    const double L[3] = {0.5 * t1 * (t1 - 1.0), 1.0 - t1 * t1, 0.5 * t1 * (t1 + 1.0)};
+    const double dL[3] = {t1 - 0.5, -2.0 * t1, t1 + 0.5};
+    const double M[3] = {0.5 * t2 * (t2 - 1.0), 1.0 - t2 * t2, 0.5 * t2 * (t2 + 1.0)};
+    const double dM[3] = {t2 - 0.5, -2.0 * t2, t2 + 0.5};
+    double X = 0, Y = 0, Xa = 0, Xb = 0, Ya = 0, Yb = 0;
+    for (int b = 0; b < 3; ++b) {
+      const long long jj = c2 + b - 1;
+      for (int a = 0; a < 3; ++a) {
+        long long ii = c1 + a - 1;
+        if (h.periodic1) ii = ((ii % h.n1) + h.n1) % h.n1;
+        const size_t k = (size_t)jj * h.n1 + (size_t)ii;
+        const double w = L[a] * M[b], wa = dL[a] * M[b], wb = L[a] * dM[b];
+        X += w * h.x[k];
+        Y += w * h.y[k];
+        Xa += wa * h.x[k];
+        Xb += wb * h.x[k];
+        Ya += wa * h.y[k];
+        Yb += wb * h.y[k];
+      }
+    }
+    const double rx = X - x, ry = Y - y, det = Xa * Yb - Xb * Ya;
+    if (!(std::fabs(det) > 0.0)) return false;
+    const double d1 = -(Yb * rx - Xb * ry) / det, d2 = -(-Ya * rx + Xa * ry) / det;
+    a1 += d1;
+    a2 += d2;
+    if (!(std::fabs(a1) < 1e12 && std::fabs(a2) < 1e12)) return false;
+    if (std::fabs(d1) + std::fabs(d2) < 1e-11) {
+      s1 = h.periodic1 ? pymod(a1, (double)h.n1) : a1;
+      s2 = a2;
+      return true;
+    }
+  }
+  return false;
+}
+
 // fractional grid indices of a physical point (inverse of the patch map)
 inline void frac_index(const HPatch& h, double x, double y, double& s1, double& s2) {
   const fc_patch_desc& d = h.d;
+  if (d.kind == FC_PATCH_GRID) {
+    grid_inverse(h, x, y, s1, s2);
+    return;
+  }
   if (d.kind == FC_PATCH_AFFINE) {
     s1 = (x - d.geom[0]) / (d.geom[1] - d.geom[0]) * (h.n1 - 1);
     s2 = (y - d.geom[2]) / (d.geom[3] - d.geom[2]) * (h.n2 - 1);
@@ -300,11 +406,51 @@ void build_patch(HPatch& h, const fc_params& prm) {
   const fc_patch_desc& d = h.d;
   h.n1 = d.n1;
   h.n2 = d.n2;
-  h.periodic1 = d.kind == FC_PATCH_OGRID;
+  h.periodic1 = d.kind == FC_PATCH_OGRID ||
+                (d.kind == FC_PATCH_GRID && d.side[0] == FC_SIDE_PERIODIC && d.side[1] == FC_SIDE_PERIODIC);
   h.h1 = h.periodic1 ? 1.0 / h.n1 : 1.0 / (h.n1 - 1);
   h.h2 = 1.0 / (h.n2 - 1);
   grid_coords(h);
-  if (d.kind == FC_PATCH_AFFINE) {
+  if (d.kind == FC_PATCH_GRID) {
+    // spacings: largest / smallest distance between index-adjacent points (periodic: wrapped)
+    const size_t N = (size_t)h.n1 * h.n2;
+    h.jm.assign(d.metrics, d.metrics + 4 * N);
+    double mx = 0.0, mn = 1e300;
+    for (int j = 0; j < h.n2; ++j)
+      for (int i = 0; i < h.n1; ++i) {
+        const size_t k = (size_t)j * h.n1 + i;
+        if (i + 1 < h.n1 || h.periodic1) {
+          const size_t q = (size_t)j * h.n1 + (i + 1) % h.n1;
+          const double dd = std::hypot(h.x[q] - h.x[k], h.y[q] - h.y[k]);
+          mx = std::max(mx, dd);
+          mn = std::min(mn, dd);
+        }
+        if (j + 1 < h.n2) {
+          const size_t q = k + h.n1;
+          const double dd = std::hypot(h.x[q] - h.x[k], h.y[q] - h.y[k]);
+          mx = std::max(mx, dd);
+          mn = std::min(mn, dd);
+        }
+      }
+    h.hhat = mx;
+    h.htil = mn;
+    // bucket grid for nearest-point queries (bucket size: the largest spacing)
+    h.hcell = std::max(mx, 1e-300);
+    h.hnx = std::max(1, (int)std::ceil((h.bx1 - h.bx0) / h.hcell) + 1);
+    h.hny = std::max(1, (int)std::ceil((h.by1 - h.by0) / h.hcell) + 1);
+    std::vector<int> cnt((size_t)h.hnx * h.hny + 1, 0), bk(N);
+    for (size_t k = 0; k < N; ++k) {
+      const int bx = std::min((int)std::floor((h.x[k] - h.bx0) / h.hcell), h.hnx - 1);
+      const int by = std::min((int)std::floor((h.y[k] - h.by0) / h.hcell), h.hny - 1);
+      bk[k] = by * h.hnx + bx;
+      cnt[bk[k] + 1]++;
+    }
+    for (size_t b = 1; b < cnt.size(); ++b) cnt[b] += cnt[b - 1];
+    h.hstart = cnt;
+    h.hidx.assign(N, 0);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t k = 0; k < N; ++k) h.hidx[fill[bk[k]]++] = (int)k;
+  } else if (d.kind == FC_PATCH_AFFINE) {
     const double hx = (d.geom[1] - d.geom[0]) / (h.n1 - 1), hy = (d.geom[3] - d.geom[2]) / (h.n2 - 1);
     h.hhat = std::max(hx, hy);
     h.htil = std::min(hx, hy);
@@ -316,7 +462,7 @@ void build_patch(HPatch& h, const fc_params& prm) {
   }
   const size_t N = (size_t)h.n1 * h.n2;
   h.blank.assign(N, 0);
-  if (d.kind == FC_PATCH_AFFINE && d.hole[2] > 0) {
+  if (d.kind != FC_PATCH_OGRID && d.hole[2] > 0) {
     const double R2 = d.hole[2] * d.hole[2];
     for (size_t k = 0; k < N; ++k) {
       const double dx = h.x[k] - d.hole[0], dy = h.y[k] - d.hole[1];
@@ -768,12 +914,22 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   for (int p = 0; p < npatch; ++p) {
     HPatch& h = c->hp[p];
     h.d = patches[p];
-    if (h.d.n1 < 2 || h.d.n2 < 2 || (h.d.kind != FC_PATCH_AFFINE && h.d.kind != FC_PATCH_OGRID))
+    if (h.d.n1 < 2 || h.d.n2 < 2 ||
+        (h.d.kind != FC_PATCH_AFFINE && h.d.kind != FC_PATCH_OGRID && h.d.kind != FC_PATCH_GRID))
       return bad("bad patch descriptor " + std::to_string(p));
+    if (h.d.kind == FC_PATCH_GRID) {
+      if (!h.d.x || !h.d.y || !h.d.metrics || h.d.n1 < 3 || h.d.n2 < 3)
+        return bad("GRID patch " + std::to_string(p) + " needs x, y, metrics and at least 3 x 3 points");
+      for (int s = 0; s < 4; ++s)
+        if (h.d.side[s] == FC_SIDE_SLIPWALL || (h.d.side[s] == FC_SIDE_PERIODIC && s >= 2))
+          return bad("GRID patch " + std::to_string(p) + ": unsupported side type");
+      if ((h.d.side[0] == FC_SIDE_PERIODIC) != (h.d.side[1] == FC_SIDE_PERIODIC))
+        return bad("GRID patch " + std::to_string(p) + ": q1 is periodic on both sides or neither");
+    }
     build_patch(h, *prm);
     h.off = off;
     off += (long long)h.n1 * h.n2;
-    if (h.d.kind == FC_PATCH_OGRID) {
+    if (h.d.kind != FC_PATCH_AFFINE) {
       h.gbase = goff;
       goff += (long long)h.n1 * h.n2;
     }
@@ -954,7 +1110,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
       const HPatch& h = c->hp[p];
       for (int s = 0; s < 4; ++s) {
         if (h.d.side[s] != FC_SIDE_ADIABATIC) continue;
-        if (h.d.kind == FC_PATCH_OGRID && s < 2) return bad("an O-grid wall must be its q2 = 0 or q2 = 1 side");
+        if (h.periodic1 && s < 2) return bad("a wall of a patch periodic in q1 must be a q2 side");
         const int nline = s < 2 ? h.n1 : h.n2;
         if (nline < prm->d + 1) return bad("a wall-normal grid line is shorter than d + 1 points");
         const int step = s == 0 ? 1 : s == 1 ? -1 : s == 2 ? h.n1 : -h.n1;
@@ -1008,6 +1164,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   Builder B{c};
   std::vector<Job> jc1, jc2, jg1, jg2, jf1, jf2;
   std::vector<uint8_t> cov2((size_t)c->P, 0), fcov1((size_t)c->P, 0), fcov2((size_t)c->P, 0);
+  std::vector<GFix> gfix;
   for (int p = 0; p < npatch; ++p) {
     const HPatch& h = c->hp[p];
     const bool aff = h.d.kind == FC_PATCH_AFFINE;
@@ -1056,8 +1213,22 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
         fcov2[(size_t)J.base + (size_t)t * h.n1] = 1;
       }
     }
-    if (!aff)  // curvilinear patches: every point is finished by its q1 line in pass C
-      for (long long k = 0; k < (long long)h.n1 * h.n2; ++k) cov2[(size_t)(h.off + k)] = 1;
+    if (!aff) {
+      // curvilinear patches: pass C (q1 lines) finishes a point; points that only one
+      // direction's passes reach are completed by the GFix kernels
+      const long long N = (long long)h.n1 * h.n2;
+      std::vector<uint8_t> l1((size_t)N, 0), l2((size_t)N, 0);
+      for (const Seg& s : h.seg1)
+        if (s.periodic || s.n >= 2 * prm->d)
+          for (int t = 0; t < s.n; ++t) l1[(size_t)s.line * h.n1 + s.a + t] = 1;
+      for (const Seg& s : h.seg2)
+        if (s.n >= 2 * prm->d)
+          for (int t = 0; t < s.n; ++t) l2[(size_t)(s.a + t) * h.n1 + s.line] = 1;
+      for (long long k = 0; k < N; ++k) {
+        cov2[(size_t)(h.off + k)] = l1[k];
+        if (l1[k] != l2[k]) gfix.push_back(GFix{(int)(h.off + k), (int)(h.gbase + k), l2[k] ? 1 : 2, 0});
+      }
+    }
   }
   std::vector<int> fix, fc1, fc2;
   for (long long k = 0; k < c->P; ++k) {
@@ -1109,6 +1280,12 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   // ---- curvilinear metrics J = dq/dx (Sec. 3.3), layout [4][Pg]: J1x, J1y, J2x, J2y
   std::vector<double> Jm((size_t)4 * std::max<long long>(c->Pg, 1), 0.0);
   for (const HPatch& h : c->hp) {
+    if (h.d.kind == FC_PATCH_GRID) {
+      const long long N = (long long)h.n1 * h.n2;
+      for (int m = 0; m < 4; ++m)
+        for (long long k = 0; k < N; ++k) Jm[(size_t)(h.gbase + k) + (size_t)m * c->Pg] = h.jm[(size_t)m * N + k];
+      continue;
+    }
     if (h.d.kind != FC_PATCH_OGRID) continue;
     const double r0 = h.d.geom[2], r1 = h.d.geom[3];
     for (long long k = 0; k < (long long)h.n1 * h.n2; ++k) {
@@ -1178,7 +1355,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_ip, B.ip) &&
        c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
-       c->upload(&c->d_fix, fix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
+       c->upload(&c->d_fix, fix) && c->upload(&c->d_gfix, gfix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
        c->upload(&c->d_bc, bcs) && c->upload(&c->d_walls, walls) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
        c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
        c->upload(&c->d_dsrc, dsrc) && c->upload(&c->d_drecv, drecv) && c->upload(&c->d_dw, dw) &&
@@ -1186,6 +1363,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->ndon = (int)dsrc.size();
   c->nwall = (int)wall.size();
   c->nfix = (int)fix.size();
+  c->ngfix = (int)gfix.size();
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
   c->nbc = (int)bcs.size();
@@ -1346,6 +1524,10 @@ void stage(fc_ctx* c, const StageCoef& sc, const double* mu, bool per_patch, cud
   }
   run_queue(c, c->q_gen1, per_patch, sg, "gen_A",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_A(T, j, n, L, e, c->d_G, s); }, gside);
+  if (c->ngfix) {
+    launch_gen_fix(T, c->d_gfix, c->ngfix, e, mu, c->d_J, c->d_G, sg);
+    c->launches++;
+  }
   run_queue(c, c->q_cart1, per_patch, st, "cart_q1",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q1(T, j, n, L, e, mu, c->d_R1, s); });
   run_queue(c, c->q_gen2, per_patch, sg, "gen_B",
@@ -1489,10 +1671,18 @@ void adj_stage(fc_ctx* c, const double* u, const double* mu, const double* psi, 
   cudaMemsetAsync(c->d_R1, 0, sizeof(double) * 4 * (size_t)c->P, st);
   run_queue(c, c->q_gen1, false, st, "adj_gen_A",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_A(T, j, n, L, c->d_J, psi, c->d_G, s); });
+  if (c->ngfix) {
+    launch_adj_gen_fixA(T, c->d_gfix, c->ngfix, c->d_J, u, mu, c->d_G, st);
+    c->launches++;
+  }
   run_queue(c, c->q_cart1, false, st, "adj_cart_q1",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_cart(T, j, n, L, 0, u, mu, psi, c->d_R1, acc, dt, s); });
   run_queue(c, c->q_gen2, false, st, "adj_gen_B",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_B(T, j, n, L, c->d_J, u, mu, psi, c->d_G, s); });
+  if (c->ngfix) {
+    launch_adj_gen_fixB(T, c->d_gfix, c->ngfix, c->d_G, c->d_R1, st);
+    c->launches++;
+  }
   run_queue(c, c->q_cart2, false, st, "adj_cart_q2",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_cart(T, j, n, L, 1, u, mu, psi, c->d_R1, acc, dt, s); });
   run_queue(c, c->q_gen1, false, st, "adj_gen_C",

@@ -82,6 +82,15 @@ struct WallPt {
   double w[7];
 };
 
+// Curvilinear point that only one direction's line passes reach (hole-cut or short
+// segments): mode 1 = on a long q2 segment only, mode 2 = on a long q1 segment only.
+struct GFix {
+  int p;     // flat state index
+  int g;     // index into the curvilinear scratch / metrics
+  int mode;
+  int pad;
+};
+
 // Runge-Kutta stage combination applied in the last pass of a stage:
 //   out  = c0 U0 + c1 Ucur + c2 Uaux + cb dt L
 //   out2 = d2 Uaux + d1 Ucur + db dt L        (only when out2 != nullptr)
@@ -126,6 +135,11 @@ void launch_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, cons
 void launch_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, double* G,
                   const StageCoef& sc, cudaStream_t st);
 void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef& sc, cudaStream_t st);
+void launch_gen_fix(const DevTables& T, const GFix* f, int n, const double* e, const double* mu, const double* J,
+                    double* G, cudaStream_t st);
+void launch_adj_gen_fixA(const DevTables& T, const GFix* f, int n, const double* J, const double* u,
+                         const double* mu, double* G, cudaStream_t st);
+void launch_adj_gen_fixB(const DevTables& T, const GFix* f, int n, const double* G, double* R1, cudaStream_t st);
 void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st);
 void launch_bc_wall(const WallPt* w, int n, double* e, long long P, double gamma, cudaStream_t st);
 void launch_bc_wall_T(const WallPt* w, int n, const double* u, double* lam, long long P, double gamma,

@@ -397,6 +397,32 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_C(DevTables T, const Job* __restrict__ 
   }
 }
 
+// after pass A, at points that only one direction's passes reach (the derivative along
+// the other direction is 0 there, as on every point off a long segment):
+// mode 1 (no long q1 segment): D1e = 0 before pass B reads it;
+// mode 2 (no long q2 segment): H_x, H_y with D2e = 0, which pass C differentiates along q1
+__global__ void k_gen_fix(DevTables T, const GFix* __restrict__ f, int n, const double* __restrict__ e,
+                          const double* __restrict__ mu, const double* __restrict__ Jm, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GFix q = f[i];
+  const long long Pg = T.Pg, cs = T.P, g = q.g, p = q.p;
+  if (q.mode == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) gslot(G, Pg, 0, c)[g] = 0.0;
+    return;
+  }
+  double fx[4], fy[4];
+  flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, fx, fy);
+  const double m = mu[p], j1x = Jm[g], j1y = Jm[g + Pg];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double d1 = gslot(G, Pg, 0, c)[g];
+    gslot(G, Pg, 1, c)[g] = fma(-m, fma(j1x, d1, 0.0), fx[c]);
+    gslot(G, Pg, 2, c)[g] = fma(-m, fma(j1y, d1, 0.0), fy[c]);
+  }
+}
+
 // points no final line pass covers (blanked points, short segments): L = 0
 __global__ void k_rk_fixup(DevTables T, const int* __restrict__ idx, int n, StageCoef sc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1104,6 +1130,55 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restric
   }
 }
 
+// transposes of k_gen_fix, after adjoint pass A:
+// mode 1 (no long q1 segment): S1x = S1y = 0 before pass B completes eta there;
+// mode 2 (no long q2 segment): eta = -S1, partial = A_x^T eta_x + A_y^T eta_y and
+// g1 = mu (J1x eta_x + J1y eta_y), which pass C finishes along q1
+__global__ void k_adj_gen_fixA(DevTables T, const GFix* __restrict__ f, int n, const double* __restrict__ Jm,
+                               const double* __restrict__ u, const double* __restrict__ mu, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GFix q = f[i];
+  const long long Pg = T.Pg, cs = T.P, g = q.g, p = q.p;
+  if (q.mode == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      gslot(G, Pg, 0, c)[g] = 0.0;
+      gslot(G, Pg, 1, c)[g] = 0.0;
+    }
+    return;
+  }
+  double ex[4], ey[4], ax[4], ay[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    ex[c] = -gslot(G, Pg, 0, c)[g];
+    ey[c] = -gslot(G, Pg, 1, c)[g];
+    gslot(G, Pg, 0, c)[g] = ex[c];
+    gslot(G, Pg, 1, c)[g] = ey[c];
+  }
+  fluxT(0, u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs], T.gamma, ex, ax);
+  fluxT(1, u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs], T.gamma, ey, ay);
+  const double m = mu[p], j1x = Jm[g], j1y = Jm[g + Pg];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    gslot(G, Pg, 2, c)[g] = ax[c] + ay[c];
+    gslot(G, Pg, 3, c)[g] = m * fma(j1x, ex[c], j1y * ey[c]);
+  }
+}
+
+// after adjoint pass B, mode 1: no pass C finishes the point, so its partial goes to R1
+// (zeroed at the start of the stage), which the fixup adds to acc
+__global__ void k_adj_gen_fixB(DevTables T, const GFix* __restrict__ f, int n, const double* __restrict__ G,
+                               double* __restrict__ R1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GFix q = f[i];
+  if (q.mode != 1) return;
+  const long long Pg = T.Pg, cs = T.P;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) R1[q.p + c * cs] = gslot(G, Pg, 2, c)[q.g];
+}
+
 // points no column pass finishes: acc += dt R1 (R1 is zero where no row pass wrote it)
 __global__ void k_adj_fixup(const int* __restrict__ idx, int n, const double* __restrict__ R1, double* __restrict__ acc,
                             long long P, const double* __restrict__ dtp) {
@@ -1471,6 +1546,20 @@ void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, 
                       const double* dt, cudaStream_t st) {
   if (njobs <= 0) return;
   k_adj_gen_C<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, G, acc, dt);
+}
+void launch_gen_fix(const DevTables& T, const GFix* f, int n, const double* e, const double* mu, const double* J,
+                    double* G, cudaStream_t st) {
+  if (n <= 0) return;
+  k_gen_fix<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, e, mu, J, G);
+}
+void launch_adj_gen_fixA(const DevTables& T, const GFix* f, int n, const double* J, const double* u,
+                         const double* mu, double* G, cudaStream_t st) {
+  if (n <= 0) return;
+  k_adj_gen_fixA<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, J, u, mu, G);
+}
+void launch_adj_gen_fixB(const DevTables& T, const GFix* f, int n, const double* G, double* R1, cudaStream_t st) {
+  if (n <= 0) return;
+  k_adj_gen_fixB<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, G, R1);
 }
 void launch_adj_fixup(const int* idx, int n, const double* R1, double* acc, long long P, const double* dt,
                       cudaStream_t st) {

@@ -38,7 +38,8 @@ class FcError(RuntimeError):
 
 class PatchDescC(C.Structure):
     _fields_ = [("kind", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("geom", C.c_double * 4),
-                ("side", C.c_int * 4), ("bc", (C.c_double * 4) * 4), ("hole", C.c_double * 3)]
+                ("side", C.c_int * 4), ("bc", (C.c_double * 4) * 4), ("hole", C.c_double * 3),
+                ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)), ("metrics", C.POINTER(C.c_double))]
 
 
 class ParamsC(C.Structure):
@@ -157,6 +158,7 @@ class Context:
         prm = workload.params
         n = len(workload.patches)
         descs = (PatchDescC * n)()
+        keep = []
         for k, p in enumerate(workload.patches):
             dsc = descs[k]
             dsc.kind, dsc.n1, dsc.n2 = p.kind, p.n1, p.n2
@@ -167,6 +169,18 @@ class Context:
                     dsc.bc[m][q] = p.bc[m][q]
             for m in range(3):
                 dsc.hole[m] = p.hole[m]
+            if p.kind == W.GRID:  # host arrays, kept alive until fc_init_patches returns
+                ptrs = []
+                for a, m in ((p.x, 1), (p.y, 1), (p.metrics, 4)):
+                    if a is None:  # left null: the library rejects the descriptor
+                        ptrs.append(None)
+                        continue
+                    a = np.ascontiguousarray(a, dtype=np.float64)
+                    if a.size != m * p.n1 * p.n2:
+                        raise ValueError(f"GRID patch {k}: array of {a.size} values, expected {m * p.n1 * p.n2}")
+                    keep.append(a)
+                    ptrs.append(a.ctypes.data_as(C.POINTER(C.c_double)))
+                dsc.x, dsc.y, dsc.metrics = ptrs
         self._tab = fc_table_blob(prm.d)
         self._sd = sdnn_blob()
         P = ParamsC()

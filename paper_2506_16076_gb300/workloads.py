@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 # patch kinds
-AFFINE, OGRID = 0, 1
+AFFINE, OGRID, GRID = 0, 1, 2
 # side types (side order: q1=0, q1=1, q2=0, q2=1)
 INTERNAL, DIRICHLET, SLIPWALL, OUTFLOW, PERIODIC, ADIABATIC = 0, 1, 2, 3, 4, 5
 
@@ -42,6 +42,10 @@ class PatchDesc:
     side: tuple  # 4 side types
     bc: tuple = ((0.0, 0.0, 0.0, 0.0),) * 4  # Dirichlet primitive (rho,u,v,p) per side
     hole: tuple = (0.0, 0.0, -1.0)  # (xc, yc, R): blank points closer than R; R<=0: none
+    # GRID only: coordinates (n2, n1) and metrics dq/dx (4, n2, n1) = (q1_x, q1_y, q2_x, q2_y)
+    x: object = None
+    y: object = None
+    metrics: object = None
 
     @property
     def npts(self):
@@ -277,8 +281,74 @@ WORKLOADS = {
 
 # ---------------------------------------------------------------- grids (geometry only)
 
+def grid_patch(mapping, n1, n2, side, bc, periodic1=False, hole=(0.0, 0.0, -1.0)):
+    """A GRID patch from a smooth mapping (q1, q2) -> (x, y, x_q1, x_q2, y_q1, y_q2) on
+    q1 = i / (n1 - 1) (i / n1 if periodic1), q2 = j / (n2 - 1): coordinates and the
+    metrics dq/dx as the inverse of the mapping's Jacobian (geometry input only)."""
+    q1 = np.arange(n1) / (n1 if periodic1 else n1 - 1)
+    q2 = np.arange(n2) / (n2 - 1)
+    Q1, Q2 = np.meshgrid(q1, q2)
+    x, y, xa, xb, ya, yb = mapping(Q1, Q2)
+    det = xa * yb - xb * ya
+    metrics = np.stack([yb / det, -xb / det, -ya / det, xa / det])
+    return PatchDesc(GRID, n1, n2, (0.0, 0.0, 0.0, 0.0), side, bc=bc, hole=hole,
+                     x=np.ascontiguousarray(x), y=np.ascontiguousarray(y), metrics=np.ascontiguousarray(metrics))
+
+
+def affine_map(x0, x1, y0, y1, bump=0.0):
+    """(q1, q2) -> box [x0, x1] x [y0, y1], displaced inside by
+    bump * (x1 - x0, y1 - y0) * sin(pi q1) sin(pi q2) (zero on the box's edges)."""
+    def f(a, b):
+        lx, ly = x1 - x0, y1 - y0
+        s = bump * np.sin(np.pi * a) * np.sin(np.pi * b)
+        sa = bump * np.pi * np.cos(np.pi * a) * np.sin(np.pi * b)
+        sb = bump * np.pi * np.sin(np.pi * a) * np.cos(np.pi * b)
+        return (x0 + lx * (a + s), y0 + ly * (b + s), lx * (1.0 + sa), lx * sb, ly * sa, ly * (1.0 + sb))
+    return f
+
+
+def annulus_map(xc, yc, r0, r1, stretch=0.0, twist=0.0):
+    """(q1, q2) -> annulus r0 <= r <= r1 around (xc, yc), q1 periodic (angle), with
+    r = r0 + (r1 - r0) (q2 + stretch sin(pi q2)) and angle 2 pi q1 + twist sin(pi q2)^2
+    (grid lines leave both circles along the normal)."""
+    def f(a, b):
+        dr = r1 - r0
+        r = r0 + dr * (b + stretch * np.sin(np.pi * b))
+        rb = dr * (1.0 + stretch * np.pi * np.cos(np.pi * b))
+        th = 2.0 * np.pi * a + twist * np.sin(np.pi * b) ** 2
+        tha = 2.0 * np.pi
+        thb = twist * np.pi * np.sin(2.0 * np.pi * b)
+        c, s = np.cos(th), np.sin(th)
+        return (xc + r * c, yc + r * s, -r * s * tha, rb * c - r * s * thb, r * c * tha, rb * s + r * c * thb)
+    return f
+
+
+def as_grid(p: PatchDesc, bump=0.0, stretch=0.0, twist=0.0):
+    """The GRID form of an AFFINE or OGRID patch: the same map (plus the optional
+    smooth displacements of affine_map / annulus_map), sides, states and hole."""
+    if p.kind == AFFINE:
+        return grid_patch(affine_map(*p.geom, bump=bump), p.n1, p.n2, p.side, p.bc, hole=p.hole)
+    if p.kind == OGRID:
+        return grid_patch(annulus_map(*p.geom, stretch=stretch, twist=twist), p.n1, p.n2, p.side, p.bc,
+                          periodic1=True, hole=p.hole)
+    return p
+
+
+def small_multipatch_grid(curved=True):
+    """small_multipatch (adiabatic cylinder wall) with every patch given as a GRID patch;
+    curved: the annulus stretched and twisted and the boxes bulged inside, so that the
+    grids are non-orthogonal and the metrics vary from point to point."""
+    w = small_multipatch(ADIABATIC)
+    ps = [as_grid(p, bump=0.04 if curved else 0.0, stretch=0.15 if curved else 0.0,
+                  twist=0.3 if curved else 0.0) for p in w.patches]
+    name = "small_multipatch_grid" + ("_curved" if curved else "")
+    return Workload(name, ps, w.params, w.freestream, w.init, w.steps, dict(w.extra))
+
+
 def patch_xy(p: PatchDesc):
     """Physical coordinates (x, y), each shape (n2, n1), of a patch's grid points."""
+    if p.kind == GRID:
+        return np.array(p.x, dtype=np.float64), np.array(p.y, dtype=np.float64)
     i = np.arange(p.n1)
     j = np.arange(p.n2)
     if p.kind == AFFINE:

@@ -28,10 +28,14 @@ def workloads_small():
     return [W.sod128(64), W.small_multipatch()]
 
 
-@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic"])
+@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic", "grid", "grid_curved"])
 def case(request, gpu_lib):
+    # grid: the adiabatic multi-patch case with every patch given as a GRID patch (same
+    # maps); grid_curved: stretched, twisted annulus and bulged boxes (non-orthogonal)
     w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
-         "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC)}[request.param]()
+         "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC),
+         "grid": lambda: W.small_multipatch_grid(curved=False),
+         "grid_curved": W.small_multipatch_grid}[request.param]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     return w, ctx, sv
@@ -210,8 +214,9 @@ def test_sod_100_steps_parity(gpu_lib, nsteps):
     assert ctx.sync_status(e) == 0
 
 
-def test_multipatch_steps_parity(gpu_lib):
-    w = W.small_multipatch()
+@pytest.mark.parametrize("make", [W.small_multipatch, W.small_multipatch_grid], ids=["ogrid", "grid_curved"])
+def test_multipatch_steps_parity(gpu_lib, make):
+    w = make()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     st0 = W.initial_state(w)

@@ -48,3 +48,30 @@ def test_receivers_without_donor_are_rejected():
 
 def test_bad_parameters_are_invalid():
     assert _status(_wl([_box(16, 16)], win_r=0)) == fcsdnn.FC_ERR_INVALID
+
+
+def _grid_box(side=(W.DIRICHLET,) * 4, **kw):
+    return dataclasses.replace(W.as_grid(_box(16, 16, side)), **kw)
+
+
+def test_grid_patch_without_metrics_is_invalid():
+    assert _status(_wl([_grid_box(metrics=None)])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_grid_patch_with_a_slip_wall_is_invalid():
+    assert _status(_wl([_grid_box((W.SLIPWALL,) + (W.DIRICHLET,) * 3)])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_grid_patch_periodic_on_one_side_only_is_invalid():
+    assert _status(_wl([_grid_box((W.PERIODIC,) + (W.DIRICHLET,) * 3)])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_grid_patch_periodic_in_q2_is_invalid():
+    side = (W.DIRICHLET, W.DIRICHLET, W.PERIODIC, W.PERIODIC)
+    assert _status(_wl([_grid_box(side)])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_grid_arrays_of_the_wrong_size_are_rejected_by_the_binding():
+    p = _grid_box()
+    with pytest.raises(ValueError):
+        fcsdnn.Context(_wl([dataclasses.replace(p, metrics=p.metrics[:2])]))
