@@ -7,6 +7,10 @@ class), captured once as a CUDA graph and replayed. A point-update is one active
 (non-blanked) grid point receiving one RHS evaluation, so a step is 5 x active
 points point-updates.
 
+Before timing, fc_autotune times the candidate FFT stage orders of every continued
+length and the warps per CTA of every length class on the workload's own lines and
+keeps the fastest (--no-autotune: the cost model's choices).
+
   python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
 
 N > 1 (torchrun): independent replicas, one per GPU (the operator's only
@@ -41,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-patches", type=int, default=1)
     ap.add_argument("--no-per-patch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the cost model's FFT stage orders and the default warps per CTA (skip fc_autotune)")
     return ap.parse_args()
 
 
@@ -231,6 +237,11 @@ def main_ours(args):
     t0 = time.perf_counter()
     ctx = fcsdnn.Context(w)
     init_s = time.perf_counter() - t0
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = ctx.autotune()
+        tune["s"] = round(time.perf_counter() - t0, 2)
     e0 = torch.from_numpy(W.flatten(W.initial_state(w))).to(dev)
     e = e0.clone()
     dt = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -366,7 +377,8 @@ def main_ours(args):
         "config": {"workload": args.workload, "points": ctx.P, "active_points": ctx.active,
                    "patches": len(w.patches), "schedule": "batched, one launch per pass and length class, CUDA graph",
                    "l2": "inputs larger than L2 (state %.2f GB)" % (32 * ctx.P / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU", "init_s": round(init_s, 2)},
+                   "parallelism": "replicas" if world > 1 else "1 GPU", "init_s": round(init_s, 2),
+                   "autotune": tune},
         "per_patch": None if ms_pp is None else {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
                                                  "batched_speedup": ms_pp / (ms / args.steps)},
         "kernels_ms_per_step": {k: round(v[0] / 2, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},

@@ -167,6 +167,22 @@ fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, do
  * `stream`. */
 fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
 
+/* fc_autotune flags */
+enum { FC_TUNE_PLANS = 1, FC_TUNE_WARPS = 2 };
+/* Measured schedule choice for this context's lines (no paper counterpart: the paper's
+ * CPU code has no launch schedule). FC_TUNE_PLANS: for every continued length L, the
+ * stage orders of the FFT with the smallest modelled cost (up to 4, power-of-two radices
+ * first) are each timed on that length's own lines and the fastest kept (if at least 1%
+ * faster than the model's choice and its output agrees with it to 1e-10 relative).
+ * FC_TUNE_WARPS: for every power-of-two length class, 1, 2, 4 or 8 warps per CTA, timed
+ * on the class's q1 and q2 lines. The choices change rounding only, never the method.
+ * Synchronises `stream`, overwrites the context's scratch (stage buffers, R1, its
+ * internal mu), invalidates a captured step graph (the next FC_STEP_GRAPH step captures
+ * again) and allocates 1 MB of device memory. report (nullable, 6 host doubles):
+ * lengths examined, lengths changed, classes examined, classes changed, and the summed
+ * time (ms) of the timed line batches before and after. */
+fc_status fc_autotune(fc_ctx *ctx, int flags, double *report, void *stream);
+
 /* Discrete adjoint of one fc_rk_step with mu and dt frozen (the smoothness
  * classifier is not differentiable, so the viscosity of the forward step is held
  * fixed): lam_n_dev = (d e_{n+1} / d e_n)^T lam_np1_dev for the step that starts from

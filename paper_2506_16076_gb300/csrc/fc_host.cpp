@@ -20,6 +20,7 @@ using namespace fcx;
 namespace {
 
 constexpr double PI = 3.141592653589793;
+constexpr int AUTOTUNE_PLANS = 4;  // stage orders per continued length offered to the autotuner
 constexpr double CONTAIN_TOL = 1e-9;
 
 // SSPRK(5,4), Shu-Osher form (Sec. 4.1: the SSPRK-4 scheme the paper cites)
@@ -74,6 +75,11 @@ struct fc_ctx {
   long long P = 0, Pg = 0, active = 0;
   uint64_t launches = 0;
 
+  // FFT plans as uploaded and, per plan, the stage orders the autotuner may choose from
+  std::vector<Plan> plans_h;
+  std::vector<std::vector<Plan>> plan_cands;
+  double tune_report[6] = {0, 0, 0, 0, 0, 0};
+
   // device tables
   std::vector<void*> allocs;
   DevTables T{};
@@ -96,6 +102,7 @@ struct fc_ctx {
     std::vector<int> class_end;
     Job* dpp = nullptr;                          // per-patch order
     std::vector<int> pbeg, pend, plmax;
+    std::vector<Job> h;                          // host copy of the batched order
   };
   Queue q_cart1, q_cart2, q_gen1, q_gen2, q_filt1, q_filt2;
   int* d_fix = nullptr;
@@ -594,7 +601,12 @@ long long lane_cost(int L, const std::vector<int>& order) {
 // span apart cancel a line's large mean exactly (the weighted sums of the odd radices
 // do not), which keeps the transform of large-mean data (Mach-25 fluxes) accurate; an
 // unrestricted order was 3x less accurate on 1080-point lines for 3% less work.
-std::vector<int> factorize(int L) {
+std::vector<std::vector<int>> plan_orders(int L, int k);
+std::vector<int> factorize(int L) { return plan_orders(L, 1)[0]; }
+
+// The k stage orders of smallest lane_cost (stable: equal costs keep the enumeration
+// order, so the first is the cost model's choice): the candidates of the autotuner.
+std::vector<std::vector<int>> plan_orders(int L, int k) {
   int m = L;
   for (int p : {2, 3, 5, 7})
     while (m % p == 0) m /= p;
@@ -605,8 +617,7 @@ std::vector<int> factorize(int L) {
       rest.push_back(p);
       m /= p;
     }
-  std::vector<int> best;
-  long long best_cost = -1;
+  std::vector<std::pair<long long, std::vector<int>>> all;
   std::vector<int> cur;
   const int radices[6] = {8, 7, 5, 4, 3, 2};
   // multisets in non-increasing radix order, then the distinct orders of each
@@ -620,11 +631,7 @@ std::vector<int> factorize(int L) {
         do {
           std::vector<int> perm = p2;
           perm.insert(perm.end(), odd.begin(), odd.end());
-          const long long c = lane_cost(L, perm);
-          if (best_cost < 0 || c < best_cost) {
-            best_cost = c;
-            best = perm;
-          }
+          all.push_back({lane_cost(L, perm), perm});
         } while (std::next_permutation(odd.begin(), odd.end()));
       } while (std::next_permutation(p2.begin(), p2.end()));
       return;
@@ -637,8 +644,18 @@ std::vector<int> factorize(int L) {
       }
   };
   rec(smooth, 0);
-  best.insert(best.end(), rest.begin(), rest.end());
-  return best;
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<long long, std::vector<int>>& a, const std::pair<long long, std::vector<int>>& b) {
+                     return a.first < b.first;
+                   });
+  std::vector<std::vector<int>> out;
+  for (size_t i = 0; i < all.size() && (int)out.size() < std::max(k, 1); ++i) {
+    std::vector<int> o = all[i].second;
+    o.insert(o.end(), rest.begin(), rest.end());
+    out.push_back(o);
+  }
+  if (out.empty()) out.push_back(rest);  // L = 1 or a product of large primes only
+  return out;
 }
 
 bool smooth7(int n) {
@@ -752,24 +769,12 @@ struct Builder {
   std::vector<int> ip;
   std::map<int, int> fcm_of_C;
 
-  int plan(int L) {
-    auto it = plan_of_L.find(L);
-    if (it != plan_of_L.end()) return it->second;
-    Plan p{};
-    p.L = L;
-    std::vector<int> f = factorize(L);
-    p.nst = (int)f.size();
-    for (int s = 0; s < p.nst; ++s) p.rad[s] = f[s];
-    p.tw = (int)tw.size();
-    for (int e = 0; e < L; ++e) {
-      const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
-      double2 w;
-      w.x = (double)cosl(ang);
-      w.y = (double)sinl(ang);
-      tw.push_back(w);
-    }
-    // slot -> mode table of the in-place transforms: slot p = sum_s d_s L/(R_0..R_s)
-    // holds mode k = sum_s d_s R_0..R_{s-1}
+  std::vector<std::vector<Plan>> cands;  // per plan: stage orders for the autotuner, [0] = plans[i]
+
+  // slot -> mode table of an in-place transform with p's stage order, appended to the int pool:
+  // slot p = sum_s d_s L/(R_0..R_s) holds mode k = sum_s d_s R_0..R_{s-1}
+  void rev_table(Plan& p) {
+    const int L = p.L;
     p.rev = (int)ip.size();
     for (int slot = 0; slot < L; ++slot) {
       int rem = slot, k = 0, w = 1, span = L;
@@ -782,6 +787,26 @@ struct Builder {
       }
       ip.push_back(k);
     }
+  }
+
+  int plan(int L) {
+    auto it = plan_of_L.find(L);
+    if (it != plan_of_L.end()) return it->second;
+    Plan p{};
+    p.L = L;
+    const std::vector<std::vector<int>> orders = plan_orders(L, AUTOTUNE_PLANS);
+    const std::vector<int>& f = orders[0];  // a length below 2^24 has at most MAXST prime factors
+    p.nst = (int)f.size();
+    for (int s = 0; s < p.nst; ++s) p.rad[s] = f[s];
+    p.tw = (int)tw.size();
+    for (int e = 0; e < L; ++e) {
+      const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
+      double2 w;
+      w.x = (double)cosl(ang);
+      w.y = (double)sinl(ang);
+      tw.push_back(w);
+    }
+    rev_table(p);
     p.sig = (int)rp.size();
     const fc_params& prm = c->prm;
     for (int t = 0; t < L; ++t) {
@@ -791,6 +816,16 @@ struct Builder {
       rp.push_back((double)(expl(-(long double)prm.alpha_f * powl(z, prm.p_f)) / (long double)L));
     }
     plans.push_back(p);
+    std::vector<Plan> alt{p};
+    for (size_t o = 1; o < orders.size(); ++o) {
+      if ((int)orders[o].size() > MAXST) continue;
+      Plan q = p;
+      q.nst = (int)orders[o].size();
+      for (int s = 0; s < q.nst; ++s) q.rad[s] = orders[o][s];
+      rev_table(q);
+      alt.push_back(q);
+    }
+    cands.push_back(alt);
     plan_of_L[L] = (int)plans.size() - 1;
     return (int)plans.size() - 1;
   }
@@ -869,6 +904,7 @@ void make_queue(fc_ctx* c, fc_ctx::Queue& q, std::vector<Job>& jobs, const std::
     k = e;
   }
   ok = ok && c->upload(&q.d, jobs) && c->upload(&q.dpp, pp);
+  q.h = jobs;
 }
 
 }  // namespace
@@ -1360,6 +1396,8 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
        c->upload(&c->d_dsrc, dsrc) && c->upload(&c->d_drecv, drecv) && c->upload(&c->d_dw, dw) &&
        c->upload(&c->d_wall, wall) && c->upload(&c->d_wallw, wallw) && c->upload(&c->d_wallc, wallc);
+  c->plans_h = B.plans;
+  c->plan_cands = B.cands;
   c->ndon = (int)dsrc.size();
   c->nwall = (int)wall.size();
   c->nfix = (int)fix.size();
@@ -1786,6 +1824,147 @@ fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, vo
   if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_check(c, "graph launch");
   c->launches += c->glaunches;
   return cuda_check(c, "fc_rk_step");
+}
+
+fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
+  if (!c) return FC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "fc_autotune");
+  double rep[6] = {0, 0, 0, 0, 0, 0};
+  // synthetic inputs in the stage scratch: smooth-in-index waves, viscous everywhere (both rounds run)
+  double* e = c->d_B1;
+  const long long P = c->P;
+  for (int k = 0; k < 4; ++k) launch_fill_wave(e + k * P, P, 1.0 + k, 0.25, 0.37 + 0.11 * k, st);
+  launch_fill_wave(c->d_mu, P, 1e-3, 0.0, 0.0, st);
+  cudaEvent_t ea, eb;
+  cudaEventCreate(&ea);
+  cudaEventCreate(&eb);
+  constexpr int MAXT = 16384, MINT = 2048, REPS = 3;
+  Job* d_tj = nullptr;
+  if (!c->alloc(&d_tj, MAXT)) return fail(c, FC_ERR_OOM, c->err);
+  auto time_q1 = [&](const Job* jobs, int n, int Lmax) {
+    launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, st);  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < REPS; ++r) {
+      cudaEventRecord(ea, st);
+      launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, st);
+      cudaEventRecord(eb, st);
+      cudaEventSynchronize(eb);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ea, eb);
+      best = std::min(best, ms);
+    }
+    return (double)best;
+  };
+  // R1 of the first timed line, 4 components (strided copy)
+  auto sample = [&](const Job& J, std::vector<double>& out) {
+    out.assign(4 * (size_t)J.n, 0.0);
+    for (int k = 0; k < 4; ++k)
+      cudaMemcpy2D(out.data() + (size_t)k * J.n, sizeof(double), c->d_R1 + k * P + J.base,
+                   (size_t)J.stride * sizeof(double), sizeof(double), J.n, cudaMemcpyDeviceToHost);
+  };
+  fc_status status = FC_OK;
+  // (1) stage order of each continued length, timed on that length's lines
+  if (flags & FC_TUNE_PLANS) {
+    const fc_ctx::Queue* qs[6] = {&c->q_cart1, &c->q_cart2, &c->q_gen1, &c->q_gen2, &c->q_filt1, &c->q_filt2};
+    for (size_t pi = 0; pi < c->plans_h.size() && status == FC_OK; ++pi) {
+      const std::vector<Plan>& cand = c->plan_cands[pi];
+      if (cand.size() < 2) continue;
+      std::vector<Job> base;
+      for (const fc_ctx::Queue* q : qs) {
+        for (const Job& J : q->h)
+          if (J.plan == (int)pi) base.push_back(J);
+        if (!base.empty()) break;  // the first pass with lines of this length
+      }
+      if (base.empty()) continue;
+      std::vector<Job> tj;
+      while ((int)tj.size() < MINT)
+        for (const Job& J : base) {
+          if ((int)tj.size() >= MAXT) break;
+          tj.push_back(J);
+        }
+      cudaMemcpy(d_tj, tj.data(), tj.size() * sizeof(Job), cudaMemcpyHostToDevice);
+      const int L = c->plans_h[pi].L;
+      std::vector<double> ref, got;
+      double t0 = 0, tb = 0;
+      int best = 0;
+      for (size_t k = 0; k < cand.size(); ++k) {
+        cudaMemcpy(c->d_plans + pi, &cand[k], sizeof(Plan), cudaMemcpyHostToDevice);
+        const double t = time_q1(d_tj, (int)tj.size(), L);
+        sample(tj[0], k == 0 ? ref : got);
+        if (k == 0) {
+          t0 = tb = t;
+          continue;
+        }
+        double dmax = 0, rmax = 0;
+        for (size_t q = 0; q < ref.size(); ++q) {
+          dmax = std::max(dmax, std::fabs(got[q] - ref[q]));
+          rmax = std::max(rmax, std::fabs(ref[q]));
+        }
+        const bool agrees = std::isfinite(dmax) && dmax <= 1e-10 * std::max(rmax, 1e-300);
+        if (agrees && t < 0.99 * tb) {
+          tb = t;
+          best = (int)k;
+        }
+      }
+      c->plans_h[pi] = cand[best];
+      cudaMemcpy(c->d_plans + pi, &cand[best], sizeof(Plan), cudaMemcpyHostToDevice);
+      rep[0] += 1;
+      rep[1] += best != 0;
+      rep[4] += t0;
+      rep[5] += tb;
+      if (cudaGetLastError() != cudaSuccess) status = cuda_check(c, "fc_autotune (plans)");
+    }
+  }
+  // (2) warps per CTA of each length class, timed on the class's q1 and q2 lines
+  if ((flags & FC_TUNE_WARPS) && status == FC_OK) {
+    std::map<int, std::vector<std::pair<const fc_ctx::Queue*, int>>> byclass;  // class -> (queue, class slot)
+    for (const fc_ctx::Queue* q : {&c->q_cart1, &c->q_cart2})
+      for (size_t k = 0; k < q->classes.size(); ++k) byclass[length_class(q->classes[k].second)].push_back({q, (int)k});
+    for (auto& kv : byclass) {
+      const int cls = kv.first;
+      int Lcap = 1;
+      for (auto& qk : kv.second) Lcap = std::max(Lcap, qk.first->classes[qk.second].second);
+      auto total = [&]() {
+        double t = 0;
+        for (auto& qk : kv.second) {
+          const fc_ctx::Queue* q = qk.first;
+          const int b = q->classes[qk.second].first, en = q->class_end[qk.second];
+          t += time_q1(q->d + b, en - b, q->classes[qk.second].second);
+        }
+        return t;
+      };
+      c->T.lw[cls] = 0;
+      const int wdef = line_warps(c->T, Lcap);
+      const double t0 = total();
+      double tb = t0;
+      int best = 0;
+      for (int w : {1, 2, 4, 8}) {
+        if (w > line_warps_max(Lcap)) break;
+        c->T.lw[cls] = w;
+        const double t = total();
+        if (t < 0.99 * tb) {
+          tb = t;
+          best = w;
+        }
+      }
+      c->T.lw[cls] = best;
+      rep[2] += 1;
+      rep[3] += best != 0 && best != wdef;
+      rep[4] += t0;
+      rep[5] += tb;
+    }
+    if (cudaGetLastError() != cudaSuccess) status = cuda_check(c, "fc_autotune (warps)");
+  }
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  c->gflags = -1;  // launch shapes and plans changed: the next graph step captures again
+  for (int k = 0; k < 6; ++k) c->tune_report[k] = rep[k];
+  if (report)
+    for (int k = 0; k < 6; ++k) report[k] = rep[k];
+  if (status != FC_OK) return status;
+  return cuda_check(c, "fc_autotune");
 }
 
 fc_status fc_drag(fc_ctx* c, const double* e, double* J, double* dJde, void* stream) {

@@ -14,6 +14,7 @@ constexpr size_t SMEM_CAP = 200 * 1024;  // dynamic shared memory budget per CTA
 constexpr int SDNN_H = 16;      // hidden width of the stand-in classifier
 constexpr int MAX_GENERIC_RADIX = 128;  // largest prime factor of a continued length
 constexpr int CONT_TMP = 32;    // complex scratch per warp after the line buffer (detrended end data, d <= 8)
+constexpr int NCLASS = 24;      // length classes of the line queues: ceil(log2 Lmax)
 
 // Per-point flag word.
 enum : uint32_t {
@@ -122,6 +123,9 @@ struct DevTables {
   // exactly there), and the algorithmic flops of the skipped rounds: [q1, q2] each
   unsigned long long* skip_lines;
   double* skip_flops;
+  // warps per CTA of the line kernels per length class ceil(log2 Lmax) (0: the default);
+  // set by the autotuner
+  int lw[NCLASS];
 };
 
 // ---- launch wrappers (fc_kernels.cu) ----
@@ -183,8 +187,11 @@ void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, c
 void launch_drag(const int* wall, const double* w, const double* nx, int n, const double* e, long long P, double gam,
                  double* J, double* dJde, cudaStream_t st);
 void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
-size_t line_smem_bytes(int Lmax);
-int line_warps(int Lmax);
+int length_class(int Lmax);
+size_t line_smem_bytes(const DevTables& T, int Lmax);
+int line_warps(const DevTables& T, int Lmax);
+int line_warps_max(int Lmax);
+void launch_fill_wave(double* p, long long n, double a, double b, double w, cudaStream_t st);
 void set_kernel_attributes();
 
 }  // namespace fcx

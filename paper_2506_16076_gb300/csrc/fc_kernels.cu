@@ -39,13 +39,27 @@ static int line_warps_cap() {
   }();
   return cap;
 }
-int line_warps(int Lmax) {
-  const size_t per = (size_t)(2 * Lmax + CONT_TMP) * sizeof(double2);
-  int w = (int)(SMEM_CAP / per);
-  const int cap = line_warps_cap();
-  return w < 1 ? 1 : (w > cap ? cap : w);
+int length_class(int Lmax) {
+  int k = 0;
+  while (k + 1 < NCLASS && (1 << k) < Lmax) ++k;
+  return k;
 }
-size_t line_smem_bytes(int Lmax) { return (size_t)line_warps(Lmax) * (2 * Lmax + CONT_TMP) * sizeof(double2); }
+// most warps whose line buffers fit the shared-memory budget (at most MAXW)
+int line_warps_max(int Lmax) {
+  const size_t per = (size_t)(2 * Lmax + CONT_TMP) * sizeof(double2);
+  const int w = (int)(SMEM_CAP / per);
+  return w < 1 ? 1 : (w > MAXW ? MAXW : w);
+}
+// warps per CTA: the class's tuned value, else FCSDNN_LINE_WARPS / the default, within the budget
+int line_warps(const DevTables& T, int Lmax) {
+  const int tuned = T.lw[length_class(Lmax)];
+  const int want = tuned > 0 ? tuned : line_warps_cap();
+  const int w = line_warps_max(Lmax);
+  return want < w ? want : w;
+}
+size_t line_smem_bytes(const DevTables& T, int Lmax) {
+  return (size_t)line_warps(T, Lmax) * (2 * Lmax + CONT_TMP) * sizeof(double2);
+}
 
 __device__ __forceinline__ void flux_xy(double r, double mx, double my, double E, double gam, double* fx, double* fy) {
   const double ir = 1.0 / r;
@@ -1408,12 +1422,12 @@ __global__ void k_drag(const int* __restrict__ wall, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------- launch wrappers
-static inline int grid_lines(int njobs, int Lmax) {
-  const int w = line_warps(Lmax);
+static inline int grid_lines(const DevTables& T, int njobs, int Lmax) {
+  const int w = line_warps(T, Lmax);
   int g = (njobs + w - 1) / w;
   return g < 1 ? 1 : g;
 }
-#define LINE_CFG(njobs, Lmax) grid_lines(njobs, Lmax), line_warps(Lmax) * 32, line_smem_bytes(Lmax), st
+#define LINE_CFG(njobs, Lmax) grid_lines(T, njobs, Lmax), line_warps(T, Lmax) * 32, line_smem_bytes(T, Lmax), st
 static inline unsigned grid_pts(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
@@ -1574,6 +1588,15 @@ void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const
 void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, cudaStream_t st) {
   if (n <= 0) return;
   k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, P);
+}
+// p[i] = a + b sin(w i): synthetic inputs of the autotuner
+__global__ void k_fill_wave(double* __restrict__ p, long long n, double a, double b, double w) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = a + b * sin(w * (double)(i % 100003));
+}
+void launch_fill_wave(double* p, long long n, double a, double b, double w, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill_wave<<<grid_pts(n, 256), 256, 0, st>>>(p, n, a, b, w);
 }
 void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
   k_axpby<<<grid_pts(n, 256), 256, 0, st>>>(n, a, x, b, y);

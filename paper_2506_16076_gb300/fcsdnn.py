@@ -22,10 +22,11 @@ FC_ERR_INVALID, FC_ERR_CUDA, FC_ERR_DONOR, FC_ERR_OVERLAP, FC_ERR_NONFINITE = 1,
 STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID", 2: "FC_ERR_CUDA", 3: "FC_ERR_DONOR", 4: "FC_ERR_OVERLAP",
           5: "FC_ERR_NONFINITE", 6: "FC_ERR_TIMEOUT", 7: "FC_ERR_UNIMPLEMENTED", 8: "FC_ERR_OOM"}
 STEP_FILTER, STEP_FROZEN_MU, STEP_PER_PATCH, STEP_FIXED_DT, STEP_GRAPH = 1, 2, 4, 8, 16
+TUNE_PLANS, TUNE_WARPS = 1, 2
 
 # every symbol include/fcsdnn.h declares
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
-           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_adjoint_step", "fc_drag", "fc_sync_status",
+           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_autotune", "fc_adjoint_step", "fc_drag", "fc_sync_status",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
            "fc_pass_stats", "fc_line_stats", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
 
@@ -75,6 +76,7 @@ def load():
         "fc_project": (C.c_int, [vp, vp, vp]),
         "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
+        "fc_autotune": (C.c_int, [vp, ip, C.POINTER(C.c_double), vp]),
         "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "fc_drag": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_sync_status": (C.c_int, [vp, vp, ip, vp]),
@@ -234,6 +236,13 @@ class Context:
 
     def rk_step(self, e, dt, mu, flags=0):
         self._check(self.lib.fc_rk_step(self.ctx, _ptr(e), _ptr(dt), _ptr(mu), int(flags), _stream()))
+
+    def autotune(self, flags=TUNE_PLANS | TUNE_WARPS):
+        """Measured choice of FFT stage orders and warps per CTA (fc_autotune); returns its report."""
+        rep = (C.c_double * 6)()
+        self._check(self.lib.fc_autotune(self.ctx, int(flags), rep, _stream()))
+        keys = ("lengths", "lengths_changed", "classes", "classes_changed", "ms_before", "ms_after")
+        return {k: (int(v) if k[0] in "lc" else float(v)) for k, v in zip(keys, rep)}
 
     def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None, flags=0):
         self._check(self.lib.fc_adjoint_step(self.ctx, _ptr(e_n), _ptr(mu), _ptr(dt), _ptr(lam_np1), _ptr(lam_n),

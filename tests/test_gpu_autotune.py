@@ -1,0 +1,85 @@
+"""The measured schedule choice (fc_autotune: FFT stage orders per continued length and
+warps per CTA per length class) changes rounding only: after tuning, the operator still
+matches the oracle within the RHS tolerance, and the batched, per-patch and graph
+schedules stay bit-identical to each other (they share the tuned plans)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import solver as S
+from paper_2506_16076_gb300 import workloads as W
+from tests.gpu_helpers import from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tuned(gpu_lib):
+    w = W.small_multipatch(W.ADIABATIC)
+    ctx = gpu_lib.Context(w)
+    rep = ctx.autotune()
+    return w, ctx, S.Solver(w), rep
+
+
+def test_report(tuned):
+    w, ctx, sv, rep = tuned
+    assert rep["lengths"] >= 1 and rep["classes"] >= 1
+    assert 0 <= rep["lengths_changed"] <= rep["lengths"] and 0 <= rep["classes_changed"] <= rep["classes"]
+    assert 0.0 < rep["ms_after"] <= rep["ms_before"]
+
+
+def test_rhs_parity_after_tuning(tuned):
+    w, ctx, sv, rep = tuned
+    st = W.random_smooth_state(w, seed=11, amp=0.2)
+    mu = smooth_mu(w, seed=3, scale=0.01)
+    ref = sv.rhs(st, mu)
+    e = to_dev(st)
+    out = torch.empty_like(e)
+    ctx.rhs(e, out, to_dev_scalar_field(mu))
+    torch.cuda.synchronize()
+    errs = rel_err(from_dev(out, w), ref)
+    assert max(errs) < 1e-11, errs
+
+
+def test_schedules_agree_after_tuning(tuned, gpu_lib):
+    w, ctx, sv, rep = tuned
+    st = W.random_smooth_state(w, seed=31, amp=0.05)
+    outs = []
+    for flags in (0, gpu_lib.STEP_PER_PATCH, gpu_lib.STEP_GRAPH):
+        e = to_dev(st)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            mu = torch.zeros(e.shape[1], dtype=torch.float64, device="cuda")
+            for n in range(2):
+                ctx.rk_step(e, dt, mu, flags | (1 if n else 0))
+        s.synchronize()
+        outs.append(e.cpu())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_graph_steps_across_tuning(gpu_lib):
+    # a step graph captured before tuning and replayed after it (the context captures it
+    # again) gives the plain steps' result
+    w = W.small_multipatch()
+    ctx = gpu_lib.Context(w)
+    st = W.random_smooth_state(w, seed=5, amp=0.05)
+    s = torch.cuda.Stream()
+    res = []
+    for tune_between in (False, True):
+        e = to_dev(st)
+        with torch.cuda.stream(s):
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            mu = torch.zeros(e.shape[1], dtype=torch.float64, device="cuda")
+            ctx.rk_step(e, dt, mu, gpu_lib.STEP_GRAPH | 1)
+            if tune_between:
+                ctx.autotune()
+            ctx.rk_step(e, dt, mu, gpu_lib.STEP_GRAPH | 1)
+        s.synchronize()
+        e2 = to_dev(st)
+        with torch.cuda.stream(s):
+            ctx.rk_step(e2, dt, mu, 1)
+            ctx.rk_step(e2, dt, mu, 1)
+        s.synchronize()
+        res.append(torch.equal(e.cpu(), e2.cpu()))
+    assert all(res), res
