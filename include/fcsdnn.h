@@ -83,9 +83,13 @@ typedef struct {
    * coordinates x, y of the grid points (n2 x n1, row-major, q1 fastest) and the metrics
    * dq/dx as [4][n2 x n1] = (dq1/dx, dq1/dy, dq2/dx, dq2/dy) for the parameters
    * q1 = i / (n1 - 1) (q1 = i / n1 when sides 0 and 1 are PERIODIC) and q2 = j / (n2 - 1)
-   * (Sec. 3.3). Other patches locate points of a GRID patch by Newton's method on its
-   * 3 x 3 quadratic interpolant, started at the nearest grid point. GRID sides may be
-   * INTERNAL, DIRICHLET, OUTFLOW, ADIABATIC or PERIODIC (q1 only); geom is unused. */
+   * (Sec. 3.3). metrics NULL: computed on the device at init by inverting the Jacobian
+   * d(x, y)/d(q1, q2) from FC derivatives of x and y along the full grid lines (Fourier
+   * along a periodic q1; at least 2d points per non-periodic line; FC_ERR_INVALID if the
+   * Jacobian is singular anywhere). Other patches locate points of a GRID patch by
+   * Newton's method on its 3 x 3 quadratic interpolant, started at the nearest grid
+   * point. GRID sides may be INTERNAL, DIRICHLET, OUTFLOW, ADIABATIC or PERIODIC (q1
+   * only); geom is unused. */
   const double *x, *y, *metrics;
 } fc_patch_desc;
 

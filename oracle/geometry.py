@@ -47,6 +47,7 @@ class PatchGeo:
         # parameter spacings (eq. param-grid without the sub-patch vicinity; periodic: 1/n)
         self.h1 = 1.0 / self.n1 if self.periodic1 else 1.0 / (self.n1 - 1)
         self.h2 = 1.0 / (self.n2 - 1)
+        self.params = params
         self.x, self.y = W.patch_xy(desc)
         self._metrics()
         self._spacings()
@@ -58,8 +59,11 @@ class PatchGeo:
 
     # Sec. 3.3: J = dq/dx
     def _metrics(self):
-        if self.kind == W.GRID:  # given with the grid (Sec. 3.3)
-            self.J = np.array(self.desc.metrics, dtype=np.float64)
+        if self.kind == W.GRID:
+            if self.desc.metrics is not None:  # given with the grid (Sec. 3.3)
+                self.J = np.array(self.desc.metrics, dtype=np.float64)
+            else:
+                self.J = self._grid_metrics()
             return
         if self.kind == W.AFFINE:
             x0, x1, y0, y1 = self.desc.geom
@@ -72,6 +76,27 @@ class PatchGeo:
             c, s = dx / r, dy / r
             self.J = np.stack([-s / (2 * np.pi * r), c / (2 * np.pi * r), c / (r1 - r0), s / (r1 - r0)])
             self.cos, self.sin = c, s
+
+    def _grid_metrics(self):
+        """dq/dx of a GRID patch given without metrics (Sec. 3.3): the Jacobian
+        d(x, y)/d(q1, q2) by FC derivatives of the coordinates along the full grid lines
+        (Fourier along a periodic q1; the continuation length of each line by the run's C
+        policy), inverted point by point."""
+        from . import fc
+        p = self.params
+        d = p.d
+
+        def dq1(F):
+            if self.periodic1:
+                return fc.periodic_derivative(F, self.h1)
+            return fc.fc_derivative(F, self.h1, d, fc.choose_C(self.n1, p.C0, p.c_policy, d))
+
+        def dq2(F):
+            return fc.fc_derivative(F.T, self.h2, d, fc.choose_C(self.n2, p.C0, p.c_policy, d)).T
+
+        xa, ya, xb, yb = dq1(self.x), dq1(self.y), dq2(self.x), dq2(self.y)
+        det = xa * yb - xb * ya
+        return np.stack([yb / det, -xb / det, -ya / det, xa / det])
 
     def _spacings(self):
         """h_hat (max) and h_tilde (min) distance between index-adjacent points (Sec. 5.1, eq. CFL)."""

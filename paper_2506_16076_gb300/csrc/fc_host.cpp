@@ -421,7 +421,10 @@ void build_patch(HPatch& h, const fc_params& prm) {
   if (d.kind == FC_PATCH_GRID) {
     // spacings: largest / smallest distance between index-adjacent points (periodic: wrapped)
     const size_t N = (size_t)h.n1 * h.n2;
-    h.jm.assign(d.metrics, d.metrics + 4 * N);
+    if (d.metrics)
+      h.jm.assign(d.metrics, d.metrics + 4 * N);
+    else
+      h.jm.assign(4 * N, 0.0);  // computed on the device from the points after the upload
     double mx = 0.0, mn = 1e300;
     for (int j = 0; j < h.n2; ++j)
       for (int i = 0; i < h.n1; ++i) {
@@ -954,8 +957,11 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
         (h.d.kind != FC_PATCH_AFFINE && h.d.kind != FC_PATCH_OGRID && h.d.kind != FC_PATCH_GRID))
       return bad("bad patch descriptor " + std::to_string(p));
     if (h.d.kind == FC_PATCH_GRID) {
-      if (!h.d.x || !h.d.y || !h.d.metrics || h.d.n1 < 3 || h.d.n2 < 3)
-        return bad("GRID patch " + std::to_string(p) + " needs x, y, metrics and at least 3 x 3 points");
+      if (!h.d.x || !h.d.y || h.d.n1 < 3 || h.d.n2 < 3)
+        return bad("GRID patch " + std::to_string(p) + " needs x, y and at least 3 x 3 points");
+      const bool per1 = h.d.side[0] == FC_SIDE_PERIODIC;
+      if (!h.d.metrics && ((!per1 && h.d.n1 < 2 * prm->d) || h.d.n2 < 2 * prm->d))
+        return bad("GRID patch " + std::to_string(p) + " without metrics needs 2d points along every non-periodic line");
       for (int s = 0; s < 4; ++s)
         if (h.d.side[s] == FC_SIDE_SLIPWALL || (h.d.side[s] == FC_SIDE_PERIODIC && s >= 2))
           return bad("GRID patch " + std::to_string(p) + ": unsupported side type");
@@ -1266,6 +1272,50 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
       }
     }
   }
+  // GRID patches given without metrics: FC derivatives of x and y along the full grid
+  // lines (the same continuation rule as the data lines), assembled after the upload
+  std::vector<Job> mj1, mj2;
+  std::vector<GFix> mpts;
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
+    if (h.d.kind != FC_PATCH_GRID || h.d.metrics) continue;
+    for (int j = 0; j < h.n2; ++j) {
+      Job J{};
+      J.base = h.off + (long long)j * h.n1;
+      J.stride = 1;
+      J.n = h.n1;
+      J.patch = p;
+      J.scale = 1.0 / h.h1;
+      J.gbase = -1;
+      if (h.periodic1) {
+        J.C = 0;
+        J.fcm = -1;
+        J.plan = B.plan(h.n1);
+      } else {
+        J.C = B.choose_C(h.n1);
+        if (J.C < c->Cmin || J.C > c->Cmax) return bad("continuation length outside the FC tables");
+        J.fcm = B.fcm(J.C);
+        J.plan = B.plan(h.n1 + J.C);
+      }
+      mj1.push_back(J);
+    }
+    for (int i = 0; i < h.n1; ++i) {
+      Job J{};
+      J.base = h.off + i;
+      J.stride = h.n1;
+      J.n = h.n2;
+      J.patch = p;
+      J.scale = 1.0 / h.h2;
+      J.gbase = -1;
+      J.C = B.choose_C(h.n2);
+      if (J.C < c->Cmin || J.C > c->Cmax) return bad("continuation length outside the FC tables");
+      J.fcm = B.fcm(J.C);
+      J.plan = B.plan(h.n2 + J.C);
+      mj2.push_back(J);
+    }
+    for (long long k = 0; k < (long long)h.n1 * h.n2; ++k)
+      mpts.push_back(GFix{(int)(h.off + k), (int)(h.gbase + k), 0, 0});
+  }
   std::vector<int> fix, fc1, fc2;
   for (long long k = 0; k < c->P; ++k) {
     if (!cov2[k]) fix.push_back((int)k);
@@ -1437,6 +1487,33 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   T.gamma = prm->gamma;
   T.d = prm->d;
   set_kernel_attributes();
+  if (!mpts.empty()) {  // metrics of GRID patches given by their points only
+    std::vector<double> xy(2 * (size_t)c->P, 0.0);
+    for (const HPatch& h : c->hp)
+      if (h.d.kind == FC_PATCH_GRID && !h.d.metrics)
+        for (size_t k = 0; k < h.x.size(); ++k) {
+          xy[(size_t)h.off + k] = h.x[k];
+          xy[(size_t)c->P + (size_t)h.off + k] = h.y[k];
+        }
+    Job *d_mj1 = nullptr, *d_mj2 = nullptr;
+    GFix* d_mp = nullptr;
+    int* d_bad = nullptr;
+    int Lm1 = 1, Lm2 = 1;
+    for (const Job& J : mj1) Lm1 = std::max(Lm1, B.plans[J.plan].L);
+    for (const Job& J : mj2) Lm2 = std::max(Lm2, B.plans[J.plan].L);
+    if (!(c->upload(&d_mj1, mj1) && c->upload(&d_mj2, mj2) && c->upload(&d_mp, mpts) && c->alloc(&d_bad, 1)))
+      return bad("device allocation failed (GRID metrics)");
+    cudaMemset(c->d_B1, 0, sizeof(double) * 4 * (size_t)c->P);
+    cudaMemcpy(c->d_B1, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemset(d_bad, 0, sizeof(int));
+    launch_deriv_lines(c->T, d_mj1, (int)mj1.size(), Lm1, c->d_B1, c->d_B2, nullptr);
+    launch_deriv_lines(c->T, d_mj2, (int)mj2.size(), Lm2, c->d_B1, c->d_B3, nullptr);
+    launch_grid_metrics(d_mp, (int)mpts.size(), c->d_B2, c->d_B3, c->P, c->d_J, c->T.Pg, d_bad, nullptr);
+    int nbad = 0;
+    if (cudaMemcpy(&nbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bad(std::string("GRID metrics: ") + cudaGetErrorString(cudaGetLastError()));
+    if (nbad) return bad("a GRID patch has a singular or non-finite Jacobian (metrics from its points)");
+  }
   {  // FCSDNN_CONCURRENT=0 runs every batched pass on the caller's stream alone (A/B timing)
     const char* v = getenv("FCSDNN_CONCURRENT");
     c->concurrent = !(v && v[0] == '0');

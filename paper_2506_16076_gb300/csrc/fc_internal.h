@@ -191,6 +191,10 @@ int length_class(int Lmax);
 size_t line_smem_bytes(const DevTables& T, int Lmax);
 int line_warps(const DevTables& T, int Lmax);
 int line_warps_max(int Lmax);
+void launch_deriv_lines(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* src, double* dst,
+                        cudaStream_t st);
+void launch_grid_metrics(const GFix* pts, int n, const double* D1, const double* D2, long long P, double* Jm,
+                         long long Pg, int* bad, cudaStream_t st);
 void launch_fill_wave(double* p, long long n, double a, double b, double w, cudaStream_t st);
 void set_kernel_attributes();
 

@@ -437,6 +437,52 @@ __global__ void k_gen_fix(DevTables T, const GFix* __restrict__ f, int n, const 
   }
 }
 
+// FC derivatives of the 4 components of src along each job's line into dst (the
+// Jacobian of GRID patches given by their points: src = (x, y, 0, 0))
+__global__ void LINE_KERNEL_BOUNDS k_deriv_lines(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
+                                                 const double* __restrict__ src, double* __restrict__ dst) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
+  const long long cs = T.P;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    load4(A, L, J, src, cs, lane);
+    deriv2(A, Lmax, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      dst[p] = A[t].x;
+      dst[p + cs] = A[t].y;
+      dst[p + 2 * cs] = A[L + t].x;
+      dst[p + 3 * cs] = A[L + t].y;
+    }
+    FC_SYNC();
+  }
+}
+
+// metrics dq/dx = inverse of [[x_q1, x_q2], [y_q1, y_q2]] (D1 = (x_q1, y_q1), D2 = (x_q2, y_q2),
+// component stride P); a singular or non-finite Jacobian is counted in *bad
+__global__ void k_grid_metrics(const GFix* __restrict__ pts, int n, const double* __restrict__ D1,
+                               const double* __restrict__ D2, long long P, double* __restrict__ Jm, long long Pg,
+                               int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = pts[i].p, g = pts[i].g;
+  const double xa = D1[p], ya = D1[p + P], xb = D2[p], yb = D2[p + P];
+  const double det = __dsub_rn(__dmul_rn(xa, yb), __dmul_rn(xb, ya));
+  if (!(fabs(det) > 0.0) || !isfinite(det)) {
+    atomicAdd(bad, 1);
+    Jm[g] = Jm[g + Pg] = Jm[g + 2 * Pg] = Jm[g + 3 * Pg] = 0.0;
+    return;
+  }
+  Jm[g] = __ddiv_rn(yb, det);
+  Jm[g + Pg] = __ddiv_rn(-xb, det);
+  Jm[g + 2 * Pg] = __ddiv_rn(-ya, det);
+  Jm[g + 3 * Pg] = __ddiv_rn(xa, det);
+}
+
 // points no final line pass covers (blanked points, short segments): L = 0
 __global__ void k_rk_fixup(DevTables T, const int* __restrict__ idx, int n, StageCoef sc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1590,6 +1636,17 @@ void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, c
   k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, P);
 }
 // p[i] = a + b sin(w i): synthetic inputs of the autotuner
+void launch_deriv_lines(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* src, double* dst,
+                        cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_deriv_lines<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, src, dst);
+}
+void launch_grid_metrics(const GFix* pts, int n, const double* D1, const double* D2, long long P, double* Jm,
+                         long long Pg, int* bad, cudaStream_t st) {
+  if (n <= 0) return;
+  k_grid_metrics<<<grid_pts(n, 256), 256, 0, st>>>(pts, n, D1, D2, P, Jm, Pg, bad);
+}
+
 __global__ void k_fill_wave(double* __restrict__ p, long long n, double a, double b, double w) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = a + b * sin(w * (double)(i % 100003));
@@ -1622,6 +1679,7 @@ void set_kernel_attributes() {
   cudaFuncSetAttribute(k_adj_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filterT_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filterT_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_deriv_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st) {
   k_check_state<<<grid_pts(T.P, 256), 256, 0, st>>>(T, e, flag);

@@ -21,7 +21,7 @@ Workloads (stand-ins for the paper's meshes, which are not published):
   u ~ U[0,1) from numpy.random.default_rng(seed), dc = distance from the patch
   centre to the cylinder centre; a is the taper coefficient.
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 import math
 import numpy as np
 
@@ -323,25 +323,29 @@ def annulus_map(xc, yc, r0, r1, stretch=0.0, twist=0.0):
     return f
 
 
-def as_grid(p: PatchDesc, bump=0.0, stretch=0.0, twist=0.0):
+def as_grid(p: PatchDesc, bump=0.0, stretch=0.0, twist=0.0, metrics=True):
     """The GRID form of an AFFINE or OGRID patch: the same map (plus the optional
-    smooth displacements of affine_map / annulus_map), sides, states and hole."""
+    smooth displacements of affine_map / annulus_map), sides, states and hole.
+    metrics=False: the points only (the library computes the metrics)."""
     if p.kind == AFFINE:
-        return grid_patch(affine_map(*p.geom, bump=bump), p.n1, p.n2, p.side, p.bc, hole=p.hole)
-    if p.kind == OGRID:
-        return grid_patch(annulus_map(*p.geom, stretch=stretch, twist=twist), p.n1, p.n2, p.side, p.bc,
-                          periodic1=True, hole=p.hole)
-    return p
+        g = grid_patch(affine_map(*p.geom, bump=bump), p.n1, p.n2, p.side, p.bc, hole=p.hole)
+    elif p.kind == OGRID:
+        g = grid_patch(annulus_map(*p.geom, stretch=stretch, twist=twist), p.n1, p.n2, p.side, p.bc,
+                       periodic1=True, hole=p.hole)
+    else:
+        return p
+    return g if metrics else replace(g, metrics=None)
 
 
-def small_multipatch_grid(curved=True):
+def small_multipatch_grid(curved=True, metrics=True):
     """small_multipatch (adiabatic cylinder wall) with every patch given as a GRID patch;
     curved: the annulus stretched and twisted and the boxes bulged inside, so that the
-    grids are non-orthogonal and the metrics vary from point to point."""
+    grids are non-orthogonal and the metrics vary from point to point; metrics=False:
+    points only, the metrics left to the library."""
     w = small_multipatch(ADIABATIC)
     ps = [as_grid(p, bump=0.04 if curved else 0.0, stretch=0.15 if curved else 0.0,
-                  twist=0.3 if curved else 0.0) for p in w.patches]
-    name = "small_multipatch_grid" + ("_curved" if curved else "")
+                  twist=0.3 if curved else 0.0, metrics=metrics) for p in w.patches]
+    name = "small_multipatch_grid" + ("_curved" if curved else "") + ("" if metrics else "_points")
     return Workload(name, ps, w.params, w.freestream, w.init, w.steps, dict(w.extra))
 
 

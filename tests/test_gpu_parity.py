@@ -28,14 +28,16 @@ def workloads_small():
     return [W.sod128(64), W.small_multipatch()]
 
 
-@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic", "grid", "grid_curved"])
+@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic", "grid", "grid_curved", "grid_points"])
 def case(request, gpu_lib):
     # grid: the adiabatic multi-patch case with every patch given as a GRID patch (same
-    # maps); grid_curved: stretched, twisted annulus and bulged boxes (non-orthogonal)
+    # maps); grid_curved: stretched, twisted annulus and bulged boxes (non-orthogonal);
+    # grid_points: the curved grids given by their points only (metrics computed)
     w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
          "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC),
          "grid": lambda: W.small_multipatch_grid(curved=False),
-         "grid_curved": W.small_multipatch_grid}[request.param]()
+         "grid_curved": W.small_multipatch_grid,
+         "grid_points": lambda: W.small_multipatch_grid(metrics=False)}[request.param]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     return w, ctx, sv

@@ -54,10 +54,6 @@ def _grid_box(side=(W.DIRICHLET,) * 4, **kw):
     return dataclasses.replace(W.as_grid(_box(16, 16, side)), **kw)
 
 
-def test_grid_patch_without_metrics_is_invalid():
-    assert _status(_wl([_grid_box(metrics=None)])) == fcsdnn.FC_ERR_INVALID
-
-
 def test_grid_patch_with_a_slip_wall_is_invalid():
     assert _status(_wl([_grid_box((W.SLIPWALL,) + (W.DIRICHLET,) * 3)])) == fcsdnn.FC_ERR_INVALID
 
@@ -75,3 +71,10 @@ def test_grid_arrays_of_the_wrong_size_are_rejected_by_the_binding():
     p = _grid_box()
     with pytest.raises(ValueError):
         fcsdnn.Context(_wl([dataclasses.replace(p, metrics=p.metrics[:2])]))
+
+
+def test_grid_patch_without_metrics_needs_2d_points_per_line():
+    # metrics from the points need FC along every non-periodic line
+    p = dataclasses.replace(W.as_grid(_box(16, 16)), n1=8, n2=16, metrics=None)
+    p = dataclasses.replace(p, x=p.x[:, :8].copy(), y=p.y[:, :8].copy())
+    assert _status(_wl([p])) == fcsdnn.FC_ERR_INVALID

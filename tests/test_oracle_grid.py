@@ -162,3 +162,24 @@ def test_rhs_adjoint_dot_product_on_curved_grid():
     lhs = sum(float(np.vdot(a, b).real) for a, b in zip(jv, lam))
     rhs = sum(float(np.vdot(a, b).real) for a, b in zip(v, jtl))
     assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), 1.0), (lhs, rhs)
+
+
+def test_metrics_from_points_exact_on_the_closed_form_maps():
+    # FC differentiates the linear box maps and the trigonometric annulus map to rounding
+    w1 = W.small_multipatch_grid(curved=False)
+    w0 = W.small_multipatch_grid(curved=False, metrics=False)
+    for p1, p0 in zip(w1.patches, w0.patches):
+        assert p0.metrics is None
+        g1, g0 = geometry.PatchGeo(p1, PRM), geometry.PatchGeo(p0, PRM)
+        assert np.abs(g0.J - g1.J).max() <= 1e-12 * np.abs(g1.J).max()
+
+
+def test_metrics_from_points_converge_at_high_order():
+    errs = []
+    for n1, n2 in ((64, 16), (128, 32), (256, 64)):
+        p = _annulus(n1, n2)
+        g1 = geometry.PatchGeo(p, PRM)
+        g0 = geometry.PatchGeo(dataclasses.replace(p, metrics=None), PRM)
+        errs.append(np.abs(g0.J - g1.J).max() / np.abs(g1.J).max())
+    assert errs[0] / errs[1] > 12.0 and errs[1] / errs[2] > 12.0, errs
+    assert errs[2] < 1e-4, errs
