@@ -123,3 +123,37 @@ def test_full_size_filter_sampled(full):
         got.append(_patch(e, offs, k, P).reshape(4, p.n2, p.n1))
     errs = rel_err(got, ref)
     assert max(errs) < RHS_TOL, (sample, errs)
+
+
+@pytest.fixture(scope="module")
+def full_grid(gpu_lib):
+    # the same workload with its 1024 x 192 O-grid given as a GRID patch by its points only:
+    # metrics computed at init, receivers located in it by the Newton inverse
+    w = W.cyl_m25_32()
+    w.patches[0] = W.as_grid(w.patches[0], metrics=False)
+    ctx = gpu_lib.Context(w)
+    sv = S.Solver.__new__(S.Solver)
+    sv.prm = w.params
+    sizes = [p.n1 * p.n2 for p in w.patches]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    return w, ctx, sv, offs
+
+
+def test_full_size_grid_ogrid_rhs(full_grid):
+    w, ctx, sv, offs = full_grid
+    st, e = _state(w, seed=41)
+    mu = smooth_mu(w, seed=5, scale=1e-3)
+    m = torch.from_numpy(np.concatenate([a.ravel() for a in mu])).cuda()
+    out = torch.empty_like(e)
+    ctx.rhs(e, out, m)
+    torch.cuda.synchronize()
+    P = int(offs[-1])
+    got, ref = [], []
+    for k in (0, 1, len(w.patches) - 1):
+        p = w.patches[k]
+        g = geometry.PatchGeo(p, w.params)
+        ref.append(sv.rhs_patch(g, st[k], mu[k]))
+        got.append(_patch(out, offs, k, P).reshape(4, p.n2, p.n1))
+    err = rel_err_normwise(got, ref)
+    assert err < RHS_TOL, (err, rel_err(got, ref))
+
