@@ -14,7 +14,7 @@ keeps the fastest (--no-autotune: the cost model's choices).
   python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
 
 N > 1 (torchrun): independent replicas, one per GPU (the operator's only
-cross-patch coupling is the per-stage exchange; this build does not shard it).
+cross-patch coupling is the per-stage exchange, which is not sharded).
 --impl reference: the CPU oracle on the host cores, on a bounded sample of the
 same workload, same metric and unit.
 """
