@@ -323,6 +323,46 @@ def annulus_map(xc, yc, r0, r1, stretch=0.0, twist=0.0):
     return f
 
 
+def arc_map(xc, yc, r0, r1, th0, th1):
+    """(q1, q2) -> the annular sector th0 <= angle <= th1, r0 <= r <= r1 around (xc, yc):
+    an S-type patch along a circle (Sec. 3.1), angle along q1, radius along q2."""
+    def f(a, b):
+        dr, dth = r1 - r0, th1 - th0
+        r = r0 + dr * b
+        th = th0 + dth * a
+        c, s = np.cos(th), np.sin(th)
+        return (xc + r * c, yc + r * s, -r * s * dth, dr * c, r * c * dth, dr * s)
+    return f
+
+
+def s_type_ring(xc, yc, r0, r1, K, nth, nr, half, fs, wall):
+    """K non-periodic arc patches (GRID, S-type) covering the annulus r0 <= r <= r1 in
+    place of one periodic O-grid of nth angular points: arc k spans the angles
+    [k P - half, (k + 1) P + half] (P = nth / K spacings of 2 pi / nth), so neighbours
+    share 2 half + 1 angular grid lines; q1 ends internal, the wall at q2 = 0, the outer
+    circle internal. Every line is FC-continued (no Fourier shortcut)."""
+    assert nth % K == 0
+    dth = 2.0 * np.pi / nth
+    per = nth // K
+    out = []
+    for k in range(K):
+        th0, th1 = (k * per - half) * dth, ((k + 1) * per + half) * dth
+        out.append(grid_patch(arc_map(xc, yc, r0, r1, th0, th1), per + 2 * half + 1, nr,
+                              (INTERNAL, INTERNAL, wall, INTERNAL), (fs,) * 4))
+    return out
+
+
+def small_multipatch_stype(K=4, half=6):
+    """small_multipatch (adiabatic cylinder wall) with its periodic O-grid replaced by K
+    overlapping S-type arc patches of the same spacing (s_type_ring)."""
+    w = small_multipatch(ADIABATIC)
+    og = w.patches[0]
+    xc, yc, r0, r1 = og.geom
+    ring = s_type_ring(xc, yc, r0, r1, K, og.n1, og.n2, half, w.freestream, ADIABATIC)
+    return Workload("small_multipatch_stype", ring + w.patches[1:], w.params, w.freestream, w.init, w.steps,
+                    dict(w.extra))
+
+
 def as_grid(p: PatchDesc, bump=0.0, stretch=0.0, twist=0.0, metrics=True):
     """The GRID form of an AFFINE or OGRID patch: the same map (plus the optional
     smooth displacements of affine_map / annulus_map), sides, states and hole.
@@ -438,3 +478,17 @@ def random_smooth_state(w: Workload, seed, amp=0.05):
             prim.append(fs[c] * (1.0 + amp * pert) if c in (0, 3) else fs[c] + 3.0 * amp * pert)
         out.append(prim_to_cons(*prim, gamma=w.params.gamma))
     return out
+
+
+def cyl_m3_stype(K=8, half=8):
+    """cyl_m3 with its 512 x 96 periodic O-grid replaced by K overlapping S-type arc
+    patches of the same spacing (s_type_ring): every line FC-continued."""
+    w = cyl_m3()
+    og = w.patches[0]
+    xc, yc, r0, r1 = og.geom
+    ring = s_type_ring(xc, yc, r0, r1, K, og.n1, og.n2, half, w.freestream, ADIABATIC)
+    return Workload("cyl_m3_stype", ring + w.patches[1:], w.params, w.freestream, w.init, w.steps, dict(w.extra))
+
+
+WORKLOADS["small_multipatch_stype"] = small_multipatch_stype
+WORKLOADS["cyl_m3_stype"] = cyl_m3_stype

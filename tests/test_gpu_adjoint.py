@@ -23,11 +23,11 @@ def mach2_small(mach=2.0, alpha_deg=2.0):
     return W.Workload(f"small_M{mach}", pts, w.params, fs, "freestream", 10)
 
 
-@pytest.mark.parametrize("name", ["sod64", "multi", "multi_adiabatic", "grid_curved"])
+@pytest.mark.parametrize("name", ["sod64", "multi", "multi_adiabatic", "grid_curved", "s_type"])
 def test_adjoint_step_parity(gpu_lib, name):
     w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
          "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC),
-         "grid_curved": W.small_multipatch_grid}[name]()
+         "grid_curved": W.small_multipatch_grid, "s_type": W.small_multipatch_stype}[name]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     st = sv.project(W.random_smooth_state(w, seed=41, amp=0.1))

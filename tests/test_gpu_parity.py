@@ -28,16 +28,19 @@ def workloads_small():
     return [W.sod128(64), W.small_multipatch()]
 
 
-@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic", "grid", "grid_curved", "grid_points"])
+@pytest.fixture(scope="module", params=["sod64", "multi", "multi_adiabatic", "grid", "grid_curved", "grid_points",
+                                        "s_type"])
 def case(request, gpu_lib):
     # grid: the adiabatic multi-patch case with every patch given as a GRID patch (same
     # maps); grid_curved: stretched, twisted annulus and bulged boxes (non-orthogonal);
-    # grid_points: the curved grids given by their points only (metrics computed)
+    # grid_points: the curved grids given by their points only (metrics computed);
+    # s_type: the O-grid replaced by four overlapping non-periodic arc patches
     w = {"sod64": lambda: W.sod128(64), "multi": W.small_multipatch,
          "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC),
          "grid": lambda: W.small_multipatch_grid(curved=False),
          "grid_curved": W.small_multipatch_grid,
-         "grid_points": lambda: W.small_multipatch_grid(metrics=False)}[request.param]()
+         "grid_points": lambda: W.small_multipatch_grid(metrics=False),
+         "s_type": W.small_multipatch_stype}[request.param]()
     ctx = gpu_lib.Context(w)
     sv = S.Solver(w)
     return w, ctx, sv
@@ -216,7 +219,8 @@ def test_sod_100_steps_parity(gpu_lib, nsteps):
     assert ctx.sync_status(e) == 0
 
 
-@pytest.mark.parametrize("make", [W.small_multipatch, W.small_multipatch_grid], ids=["ogrid", "grid_curved"])
+@pytest.mark.parametrize("make", [W.small_multipatch, W.small_multipatch_grid, W.small_multipatch_stype],
+                         ids=["ogrid", "grid_curved", "s_type"])
 def test_multipatch_steps_parity(gpu_lib, make):
     w = make()
     ctx = gpu_lib.Context(w)

@@ -122,10 +122,11 @@ def test_grid_form_reproduces_the_closed_form_maps():
     assert abs(sv1.dt(st, mu) - sv0.dt(st, mu)) <= 1e-13 * sv0.dt(st, mu)
 
 
-def test_uniform_state_preserved_on_curved_grid():
-    w = W.small_multipatch_grid()
-    og = w.patches[0]
-    w.patches[0] = dataclasses.replace(og, side=(W.PERIODIC, W.PERIODIC, W.DIRICHLET, W.INTERNAL))
+@pytest.mark.parametrize("make", [W.small_multipatch_grid, W.small_multipatch_stype], ids=["curved", "s_type"])
+def test_uniform_state_preserved_on_curved_grid(make):
+    w = make()
+    w.patches = [dataclasses.replace(p, side=tuple(W.DIRICHLET if t == W.ADIABATIC else t for t in p.side))
+                 for p in w.patches]
     sv = S.Solver(w)
     assert not sv.conn.errors
     u = np.array(W.prim_to_cons(*w.freestream))
@@ -183,3 +184,17 @@ def test_metrics_from_points_converge_at_high_order():
         errs.append(np.abs(g0.J - g1.J).max() / np.abs(g1.J).max())
     assert errs[0] / errs[1] > 12.0 and errs[1] / errs[2] > 12.0, errs
     assert errs[2] < 1e-4, errs
+
+
+def test_s_type_ring_shares_grid_lines_and_connects():
+    # neighbouring arcs share 2 half + 1 angular grid lines: the receivers near an arc's
+    # end are located in its neighbour at integer angular indices (up to rounding)
+    w = W.small_multipatch_stype(K=4, half=6)
+    sv = S.Solver(w)
+    assert not sv.conn.errors
+    it = sv.conn.items[1]
+    sel = (it["donor"] == 0) & (it["j"] > 0)  # receivers of arc 1 fed by arc 0
+    assert sel.any()
+    s1 = it["a1"][sel] + it["t1"][sel]
+    assert np.abs(s1 - np.round(s1)).max() < 1e-9
+    assert np.array_equal(np.round(s1).astype(int) - 32, it["i"][sel])
