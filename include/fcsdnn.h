@@ -182,7 +182,7 @@ enum { FC_TUNE_PLANS = 1, FC_TUNE_WARPS = 2 };
  * on the class's q1 and q2 lines. The choices change rounding only, never the method.
  * Synchronises `stream`, overwrites the context's scratch (stage buffers, R1, its
  * internal mu), invalidates a captured step graph (the next FC_STEP_GRAPH step captures
- * again) and allocates 1 MB of device memory. report (nullable, 6 host doubles):
+ * again) and allocates 1 MB of device memory on its first call. report (nullable, 6 host doubles):
  * lengths examined, lengths changed, classes examined, classes changed, and the summed
  * time (ms) of the timed line batches before and after. */
 fc_status fc_autotune(fc_ctx *ctx, int flags, double *report, void *stream);

@@ -79,6 +79,7 @@ struct fc_ctx {
   std::vector<Plan> plans_h;
   std::vector<std::vector<Plan>> plan_cands;
   double tune_report[6] = {0, 0, 0, 0, 0, 0};
+  Job* d_tune_jobs = nullptr;  // the autotuner's timing batch (allocated on first use)
 
   // device tables
   std::vector<void*> allocs;
@@ -446,6 +447,9 @@ void build_patch(HPatch& h, const fc_params& prm) {
     h.htil = mn;
     // bucket grid for nearest-point queries (bucket size: the largest spacing)
     h.hcell = std::max(mx, 1e-300);
+    // at most about 4 buckets per point (a grid whose bounding box is large against its
+    // spacings gets coarser buckets; the search result does not depend on their size)
+    while ((h.bx1 - h.bx0) / h.hcell * ((h.by1 - h.by0) / h.hcell) > 4.0 * (double)N + 1024.0) h.hcell *= 2.0;
     h.hnx = std::max(1, (int)std::ceil((h.bx1 - h.bx0) / h.hcell) + 1);
     h.hny = std::max(1, (int)std::ceil((h.by1 - h.by0) / h.hcell) + 1);
     std::vector<int> cnt((size_t)h.hnx * h.hny + 1, 0), bk(N);
@@ -1917,8 +1921,8 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
   cudaEventCreate(&ea);
   cudaEventCreate(&eb);
   constexpr int MAXT = 16384, MINT = 2048, REPS = 3;
-  Job* d_tj = nullptr;
-  if (!c->alloc(&d_tj, MAXT)) return fail(c, FC_ERR_OOM, c->err);
+  if (!c->d_tune_jobs && !c->alloc(&c->d_tune_jobs, MAXT)) return fail(c, FC_ERR_OOM, c->err);
+  Job* d_tj = c->d_tune_jobs;
   auto time_q1 = [&](const Job* jobs, int n, int Lmax) {
     launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, st);  // warm-up
     float best = 1e30f;
@@ -1937,8 +1941,9 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
   auto sample = [&](const Job& J, std::vector<double>& out) {
     out.assign(4 * (size_t)J.n, 0.0);
     for (int k = 0; k < 4; ++k)
-      cudaMemcpy2D(out.data() + (size_t)k * J.n, sizeof(double), c->d_R1 + k * P + J.base,
-                   (size_t)J.stride * sizeof(double), sizeof(double), J.n, cudaMemcpyDeviceToHost);
+      cudaMemcpy2DAsync(out.data() + (size_t)k * J.n, sizeof(double), c->d_R1 + k * P + J.base,
+                        (size_t)J.stride * sizeof(double), sizeof(double), J.n, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
   };
   fc_status status = FC_OK;
   // (1) stage order of each continued length, timed on that length's lines
@@ -1960,13 +1965,14 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
           if ((int)tj.size() >= MAXT) break;
           tj.push_back(J);
         }
-      cudaMemcpy(d_tj, tj.data(), tj.size() * sizeof(Job), cudaMemcpyHostToDevice);
+      // copies on `stream` itself: it may be a non-blocking stream, unordered with the legacy one
+      cudaMemcpyAsync(d_tj, tj.data(), tj.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
       const int L = c->plans_h[pi].L;
       std::vector<double> ref, got;
       double t0 = 0, tb = 0;
       int best = 0;
       for (size_t k = 0; k < cand.size(); ++k) {
-        cudaMemcpy(c->d_plans + pi, &cand[k], sizeof(Plan), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(c->d_plans + pi, &cand[k], sizeof(Plan), cudaMemcpyHostToDevice, st);
         const double t = time_q1(d_tj, (int)tj.size(), L);
         sample(tj[0], k == 0 ? ref : got);
         if (k == 0) {
@@ -1985,7 +1991,7 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
         }
       }
       c->plans_h[pi] = cand[best];
-      cudaMemcpy(c->d_plans + pi, &cand[best], sizeof(Plan), cudaMemcpyHostToDevice);
+      cudaMemcpyAsync(c->d_plans + pi, &cand[best], sizeof(Plan), cudaMemcpyHostToDevice, st);
       rep[0] += 1;
       rep[1] += best != 0;
       rep[4] += t0;
