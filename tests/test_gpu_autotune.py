@@ -83,3 +83,24 @@ def test_graph_steps_across_tuning(gpu_lib):
         s.synchronize()
         res.append(torch.equal(e.cpu(), e2.cpu()))
     assert all(res), res
+
+
+def test_tuning_on_a_side_stream(gpu_lib):
+    # fc_autotune called on a non-default stream orders its own copies on that stream
+    w = W.small_multipatch_grid()
+    ctx = gpu_lib.Context(w)
+    sv = S.Solver(w)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rep = ctx.autotune()
+    s.synchronize()
+    assert rep["lengths"] >= 1
+    st = W.random_smooth_state(w, seed=13, amp=0.2)
+    mu = smooth_mu(w, seed=3, scale=0.01)
+    ref = sv.rhs(st, mu)
+    e = to_dev(st)
+    out = torch.empty_like(e)
+    ctx.rhs(e, out, to_dev_scalar_field(mu))
+    torch.cuda.synchronize()
+    errs = rel_err(from_dev(out, w), ref)
+    assert max(errs) < 1e-11, errs
