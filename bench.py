@@ -51,24 +51,27 @@ def parse():
 
 
 # ---------------------------------------------------------------- CPU oracle on a bounded sample
-def oracle_sample_workload(w, npatch):
-    """A bounded sample of the workload: its npatch largest affine patches, each run as a
-    stand-alone patch (sides made Dirichlet free stream, no hole), so the sample has the
-    workload's line lengths and per-point work without inter-patch coupling."""
+def oracle_sample_workload(w, npatch, max_points=None):
+    """A bounded sample of the workload: its npatch largest affine patches (of at most
+    max_points points each, when given and some patch qualifies), each run as a stand-alone
+    patch (sides made Dirichlet free stream, no hole), so the sample has the workload's
+    line lengths and per-point work without inter-patch coupling."""
     import dataclasses
     from paper_2506_16076_gb300 import workloads as W
     aff = [p for p in w.patches if p.kind == W.AFFINE]
     aff.sort(key=lambda p: -p.npts)
+    if max_points is not None and any(p.npts <= max_points for p in aff):
+        aff = [p for p in aff if p.npts <= max_points]
     pts = [dataclasses.replace(p, side=(W.DIRICHLET,) * 4, hole=(0.0, 0.0, -1.0)) for p in aff[:npatch]]
     return W.Workload(w.name + "_sample", pts, w.params, w.freestream, w.init, w.steps, w.extra)
 
 
-def oracle_bench(workload, steps, warmup, npatch, budget_s=None):
+def oracle_bench(workload, steps, warmup, npatch, budget_s=None, max_points=None):
     """Time full oracle steps on the sample; returns (point-updates/s, sample description, seconds)."""
     from oracle import solver as S
     from paper_2506_16076_gb300 import workloads as W
     w = W.WORKLOADS[workload]()
-    ws = oracle_sample_workload(w, npatch)
+    ws = oracle_sample_workload(w, npatch, max_points)
     sv = S.Solver(ws)
     st = W.initial_state(ws)
     active = sum(int((~g.blank).sum()) for g in sv.geos)
@@ -82,7 +85,8 @@ def oracle_bench(workload, steps, warmup, npatch, budget_s=None):
         if budget_s and time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    desc = (f"{len(ws.patches)} largest of the {len(w.patches)} patches of {workload} (stand-alone), "
+    cap = "" if max_points is None else f" of at most {max_points} points"
+    desc = (f"{len(ws.patches)} largest{cap} of the {len(w.patches)} patches of {workload} (stand-alone), "
             f"{active} active points, {done} full steps, long-double FC oracle")
     return active * 5 * done / el, desc, el, done
 
@@ -91,15 +95,15 @@ def cpu_threads():
     return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
 
 
-def run_oracle_subprocess(workload, steps, warmup, npatch, budget_s):
+def run_oracle_subprocess(workload, steps, warmup, npatch, budget_s, max_points=None):
     """Run the oracle in a fresh process (spawned before any GPU work of that process)."""
     env = dict(os.environ)
     n = str(os.cpu_count() or 1)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = n
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_bench(%r, %d, %d, %d, %r); print(json.dumps(r))" % (ROOT, workload, steps, warmup,
-                                                                                npatch, budget_s))
+            "r = bench.oracle_bench(%r, %d, %d, %d, %r, %r); print(json.dumps(r))" % (ROOT, workload, steps, warmup,
+                                                                                    npatch, budget_s, max_points))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -453,8 +457,12 @@ def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # each step a bounded sample: patches small enough that the K + W oracle steps take about
+    # two minutes at the slowest host rate seen for this oracle (3.5e4 point-updates/s, the
+    # Arm cores, where long double is quad precision in software)
+    max_points = max(4096, int(120.0 * 3.5e4 / 5.0 / max(1, args.steps + args.warmup)))
     v, desc, el, done, cores = run_oracle_subprocess(args.workload, args.steps, args.warmup, args.sample_patches,
-                                                     None)
+                                                     None, max_points)
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
            "ms_per_step": el / max(done, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
