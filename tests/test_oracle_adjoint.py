@@ -155,3 +155,20 @@ def test_drag_gradient_central_differences():
     fd = (J_of([a + h * b for a, b in zip(st0, v)]) - J_of([a - h * b for a, b in zip(st0, v)])) / (2 * h)
     ad = dot(lam, v)
     assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-3), (fd, ad)
+
+
+@pytest.mark.parametrize("make", [W.small_multipatch_grid, W.small_multipatch_stype], ids=["grid_curved", "s_type"])
+def test_step_adjoint_with_filter_dot_product_on_grid_patches(make):
+    # the adjoint of a filtered step on hole-cut curved GRID patches and on S-type arcs
+    # (exchange into and out of GRID donors, adiabatic wall on a GRID side)
+    w = make()
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=32, amp=0.05))
+    mu = [0.002 * (1 + np.cos(g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    dt = 0.5 * sv.dt(st, mu)
+    v = rand_like(st, 33)
+    lam = rand_like(st, 34)
+    jv = A.step_jvp_complex(sv, st, mu, dt, v, filt=True)
+    lam_n, _ = A.step_adjoint(sv, st, mu, dt, lam, filt=True)
+    lhs, rhs = dot(jv, lam), dot(v, lam_n)
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
