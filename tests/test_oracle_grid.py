@@ -198,3 +198,34 @@ def test_s_type_ring_shares_grid_lines_and_connects():
     s1 = it["a1"][sel] + it["t1"][sel]
     assert np.abs(s1 - np.round(s1)).max() < 1e-9
     assert np.array_equal(np.round(s1).astype(int) - 32, it["i"][sel])
+
+
+def test_s_type_arcs_agree_with_the_periodic_o_grid():
+    # the same annulus as four FC-continued arcs and as one Fourier-differentiated
+    # periodic O-grid (coincident points): on a smooth field the two RHS agree to the
+    # FC error, smallest away from the arc ends
+    w0 = W.small_multipatch(W.ADIABATIC)
+    w1 = W.small_multipatch_stype(K=4, half=6)
+    og = w0.patches[0]
+    g0 = geometry.PatchGeo(og, w0.params)
+    sv = S.Solver.__new__(S.Solver)
+    sv.prm = w0.params
+
+    def state(x, y):
+        rho = 1.4 * (1 + 0.1 * np.sin(1.3 * x + 0.7) * np.cos(0.9 * y))
+        u, v, p = 0.5 + 0.2 * np.cos(0.8 * y), 0.1 * np.sin(0.6 * x), 1.0 + 0.1 * np.cos(x - y)
+        return np.stack(W.prim_to_cons(rho, u, v, p))
+
+    def mu(x, y):
+        return 1e-3 * (1 + np.sin(x) ** 2)
+
+    r0 = sv.rhs_patch(g0, state(g0.x, g0.y), mu(g0.x, g0.y))
+    for k, p in enumerate(w1.patches[:4]):
+        g = geometry.PatchGeo(p, w1.params)
+        idx = np.mod(k * 32 - 6 + np.arange(p.n1), og.n1)
+        assert np.abs(g.x - g0.x[:, idx]).max() < 1e-13 and np.abs(g.y - g0.y[:, idx]).max() < 1e-13
+        r = sv.rhs_patch(g, state(g.x, g.y), mu(g.x, g.y))
+        ref = r0[:, :, idx]
+        scale = np.abs(ref).max()
+        assert np.abs(r[:, :, 8:-8] - ref[:, :, 8:-8]).max() < 2e-6 * scale
+        assert np.abs(r - ref).max() < 2e-4 * scale
