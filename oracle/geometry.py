@@ -3,10 +3,12 @@
 Test infrastructure only (see oracle/__init__.py).
 
 Sec. 3.1-3.2: each patch is the image of Q = [0,1]^2 under a smooth map M_p;
-its grid is the image of a Cartesian parameter grid (eq. param-grid). Two map
-kinds are used by the workloads: affine boxes (C/I-type patches) and an
-annulus around the cylinder whose angular direction is periodic (a reading:
-the paper would use S-type patches, eq. param_S).
+its grid is the image of a Cartesian parameter grid (eq. param-grid). Three
+kinds: affine boxes (C/I-type patches), an annulus around the cylinder whose
+angular direction is periodic (a reading: the paper would use S-type patches,
+eq. param_S), and GRID patches given by their points (S-type arcs and other
+curvilinear patches), with metrics given or computed by FC derivatives of the
+points and the inverse map by Newton's method on the local quadratic interpolant.
 Sec. 3.3: Jacobian J = dq/dx of the inverse map, grad_x = J^T grad_q
 (eq. general_curvilinear).
 Sec. 3.4: n-point fringe regions from the maximum-index-norm distance to the
