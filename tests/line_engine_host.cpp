@@ -1,0 +1,143 @@
+// Host build of the line engine (fc_line.cuh) and of the plan and table builder
+// (fc_host.cpp) for CPU tests of the kernels' arithmetic: the same source the GPU runs,
+// compiled as plain C++ with one "lane" per line (the warp-level barriers compile to
+// nothing on the host).
+//
+//   line_engine_host plans L1 L2 ...
+//     for every continued length L and every candidate stage order the autotuner may
+//     pick, the derivative of a random trigonometric polynomial of two packed sequences
+//     (forward transform, derivative multiplier, inverse transform) against its exact
+//     derivative; prints "L order max_rel_err" per candidate.
+//
+//   line_engine_host fc <in> <out>
+//     FC derivatives (continuation + transform) of lines read from <in>:
+//       int32 d, int32 ntab, double tab[ntab] (the packed FC-Gram tables), int32 nlines,
+//       then per line int32 N, int32 C, double h, double data[4][N];
+//     <out> gets, per line, int32 ncand and ncand x double deriv[4][N] (one result per
+//     candidate stage order of the continued length N + C).
+#include "../paper_2506_16076_gb300/csrc/fc_host.cpp"
+#include "../paper_2506_16076_gb300/csrc/fc_line.cuh"
+
+#include <cstdio>
+#include <random>
+
+namespace {
+
+// derivative of the 4 components of one line (two packed sequences) with plan P, as deriv2 does
+void derive(double2* A, int Lmax, const fcx::Plan& P, int n, int C, int fcm, double scale, int d,
+            const Builder& B) {
+  using namespace fcx;
+  if (fcm >= 0) continue_lines(A, P.L, n, C, d, B.rp.data() + fcm, 2, 0, 1, A + 2 * Lmax);
+  fft_inplace<false>(A, P, 2, B.tw.data(), 0, 1);
+  mul_deriv_rev(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.ip.data() + P.rev, 0, 1);
+  fft_inplace<true>(A, P, 2, B.tw.data(), 0, 1);
+}
+
+int run_plans(int argc, char** argv) {
+  using namespace fcx;
+  fc_ctx c;
+  Builder B{&c};
+  std::mt19937_64 rng(12345);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  for (int a = 2; a < argc; ++a) {
+    const int L = atoi(argv[a]);
+    const int pi = B.plan(L);
+    const std::vector<Plan> cands = B.cands[pi];
+    // random modes |k| < L/2 on both sequences (complex coefficients)
+    const int K = (L - 1) / 2;
+    std::vector<double> cr(2 * (2 * K + 1)), ci(2 * (2 * K + 1));
+    for (size_t q = 0; q < cr.size(); ++q) {
+      cr[q] = U(rng);
+      ci[q] = U(rng);
+    }
+    std::vector<double2> f(2 * L), df(2 * L);
+    double dmax = 0;
+    for (int s = 0; s < 2; ++s)
+      for (int t = 0; t < L; ++t) {
+        long double fx = 0, fy = 0, gx = 0, gy = 0;
+        for (int k = -K; k <= K; ++k) {
+          const long double ang = 2.0L * 3.14159265358979323846264338327950288L * k * t / L;
+          const long double cs = cosl(ang), sn = sinl(ang);
+          const long double ar = cr[s * (2 * K + 1) + k + K], ai = ci[s * (2 * K + 1) + k + K];
+          const long double vr = ar * cs - ai * sn, vi = ar * sn + ai * cs;  // c_k e^{i ang}
+          const long double w = 2.0L * 3.14159265358979323846264338327950288L * k / L;
+          fx += vr;
+          fy += vi;
+          gx += -w * vi;  // i w (vr + i vi)
+          gy += w * vr;
+        }
+        f[s * L + t] = cpx((double)fx, (double)fy);
+        df[s * L + t] = cpx((double)gx, (double)gy);
+        dmax = std::max(dmax, (double)std::max(fabsl(gx), fabsl(gy)));
+      }
+    for (const Plan& P : cands) {
+      std::vector<double2> A(2 * L + CONT_TMP);
+      for (int q = 0; q < 2 * L; ++q) A[q] = f[q];
+      derive(A.data(), L, P, L, 0, -1, 1.0, 0, B);
+      double err = 0;
+      for (int q = 0; q < 2 * L; ++q)
+        err = std::max(err, std::max(fabs(A[q].x - df[q].x), fabs(A[q].y - df[q].y)));
+      printf("%d ", L);
+      for (int s = 0; s < P.nst; ++s) printf("%s%d", s ? "." : "", P.rad[s]);
+      printf(" %.3e\n", err / dmax);
+    }
+  }
+  return 0;
+}
+
+int run_fc(const char* in, const char* out) {
+  using namespace fcx;
+  FILE* fi = fopen(in, "rb");
+  FILE* fo = fopen(out, "wb");
+  if (!fi || !fo) return 2;
+  int d = 0, ntab = 0, nlines = 0;
+  if (fread(&d, 4, 1, fi) != 1 || fread(&ntab, 4, 1, fi) != 1) return 3;
+  fc_ctx c;
+  c.fctab.resize(ntab);
+  if (fread(c.fctab.data(), 8, ntab, fi) != (size_t)ntab) return 3;
+  c.d = d;
+  c.Cmin = (int)c.fctab[1];
+  c.Cmax = (int)c.fctab[2];
+  Builder B{&c};
+  if (fread(&nlines, 4, 1, fi) != 1) return 3;
+  for (int l = 0; l < nlines; ++l) {
+    int N = 0, C = 0;
+    double h = 0;
+    if (fread(&N, 4, 1, fi) != 1 || fread(&C, 4, 1, fi) != 1 || fread(&h, 8, 1, fi) != 1) return 3;
+    std::vector<double> data(4 * (size_t)N);
+    if (fread(data.data(), 8, data.size(), fi) != data.size()) return 3;
+    const int fcm = B.fcm(C);
+    const int pi = B.plan(N + C);
+    const std::vector<Plan> cands = B.cands[pi];
+    const int L = N + C, nc = (int)cands.size();
+    fwrite(&nc, 4, 1, fo);
+    for (const Plan& P : cands) {
+      std::vector<double2> A(2 * L + CONT_TMP);
+      for (int t = 0; t < N; ++t) {
+        A[t] = cpx(data[t], data[N + t]);
+        A[L + t] = cpx(data[2 * N + t], data[3 * N + t]);
+      }
+      derive(A.data(), L, P, N, C, fcm, 1.0 / h, d, B);
+      std::vector<double> o(4 * (size_t)N);
+      for (int t = 0; t < N; ++t) {
+        o[t] = A[t].x;
+        o[N + t] = A[t].y;
+        o[2 * N + t] = A[L + t].x;
+        o[3 * N + t] = A[L + t].y;
+      }
+      fwrite(o.data(), 8, o.size(), fo);
+    }
+  }
+  fclose(fi);
+  fclose(fo);
+  return 0;
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc >= 2 && std::string(argv[1]) == "plans") return run_plans(argc, argv);
+  if (argc == 4 && std::string(argv[1]) == "fc") return run_fc(argv[2], argv[3]);
+  fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out>\n");
+  return 1;
+}

@@ -1,0 +1,124 @@
+"""The kernels' line arithmetic compiled for the host (tests/line_engine_host.cpp: the same
+fc_line.cuh and plan builder the GPU runs, one lane per line) checked on the CPU:
+
+- every candidate FFT stage order of every continued length the autotuner may choose
+  differentiates random trigonometric polynomials to rounding (exact spectral
+  derivative as the reference);
+- the FC derivative (detrended two-phase continuation, in-place transforms, digit-
+  reversed multiplier) of every candidate order matches the oracle's long-double FC
+  derivative (Sec. 2.2, eq. fc_der) on smooth lines, and differentiates polynomials of
+  degree below d exactly up to rounding.
+"""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import fc as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CUDA_INC = "/usr/local/cuda/include"
+CUDA_LIB = "/usr/local/cuda/lib64"
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    from paper_2506_16076_gb300 import build
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("g++ and the CUDA headers are needed to build the host harness")
+    lib = build.build()
+    out = str(tmp_path_factory.mktemp("le") / "line_engine_host")
+    cmd = [gxx, "-O2", "-std=c++17", "-w", f"-I{CUDA_INC}", "-o", out, os.path.join(ROOT, "tests", "line_engine_host.cpp"),
+           f"-L{os.path.dirname(lib)}", "-lfcsdnn", f"-L{CUDA_LIB}", "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    env = dict(os.environ)
+    env["LD_LIBRARY_PATH"] = ":".join([os.path.dirname(lib), CUDA_LIB, env.get("LD_LIBRARY_PATH", "")])
+    return out, env
+
+
+def _smooth7(n):
+    for p in (2, 3, 5, 7):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def test_every_candidate_stage_order_differentiates_exactly(harness):
+    exe, env = harness
+    lengths = [L for L in range(16, 1200) if _smooth7(L)] + [176, 297, 143 * 2]  # also generic primes 11, 13
+    r = subprocess.run([exe, "plans", *map(str, lengths)], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    rows = [ln.split() for ln in r.stdout.splitlines()]
+    assert len(rows) >= len(lengths)
+    worst = max(rows, key=lambda x: float(x[2]))
+    # FP64 transforms: a few units of rounding times log L
+    assert float(worst[2]) < 2e-14, worst
+
+
+def _run_fc(exe, env, tmp, lines, d=5):
+    from paper_2506_16076_gb300 import fcsdnn
+    tab = np.asarray(fcsdnn.fc_table_blob(d), dtype=np.float64)
+    fin, fout = os.path.join(tmp, "in.bin"), os.path.join(tmp, "out.bin")
+    with open(fin, "wb") as f:
+        f.write(struct.pack("<ii", d, tab.size))
+        f.write(tab.tobytes())
+        f.write(struct.pack("<i", len(lines)))
+        for (N, C, h, data) in lines:
+            f.write(struct.pack("<iid", N, C, h))
+            f.write(np.ascontiguousarray(data, dtype=np.float64).tobytes())
+    r = subprocess.run([exe, "fc", fin, fout], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    raw = open(fout, "rb").read()
+    pos, res = 0, []
+    for (N, C, h, data) in lines:
+        nc = struct.unpack_from("<i", raw, pos)[0]
+        pos += 4
+        outs = []
+        for _ in range(nc):
+            outs.append(np.frombuffer(raw, dtype=np.float64, count=4 * N, offset=pos).reshape(4, N))
+            pos += 8 * 4 * N
+        res.append(outs)
+    return res
+
+
+def test_fc_derivative_matches_the_oracle(harness, tmp_path):
+    exe, env = harness
+    rng = np.random.default_rng(8)
+    lines = []
+    for N in (10, 37, 64, 101, 160, 257, 384, 640):
+        C = F.choose_C(N, 27, 2, 5)
+        x = np.arange(N) / (N - 1)
+        comps = []
+        for _ in range(4):
+            a, b, c, k = rng.uniform(-1, 1, 4)
+            comps.append(5.0 + a * np.sin(3.0 * k * x + b) + c * np.exp(x) * np.cos(2.0 * x))
+        lines.append((N, C, 1.0 / (N - 1), np.stack(comps)))
+    res = _run_fc(exe, env, str(tmp_path), lines)
+    for (N, C, h, data), outs in zip(lines, res):
+        ref = F.fc_derivative(data, h, 5, C)
+        for o in outs:
+            err = np.abs(o - ref).max() / np.abs(ref).max()
+            # FP64 transforms of lines with a mean 5 times their variation: rounding at the
+            # top modes grows with the length (the floor measured for the GPU kernels)
+            assert err < 1e-12 * max(1.0, N / 256), (N, C, err)
+
+
+def test_fc_derivative_exact_on_polynomials(harness, tmp_path):
+    exe, env = harness
+    lines = []
+    for N in (10, 41, 128, 333):
+        C = F.choose_C(N, 27, 2, 5)
+        x = np.arange(N) / (N - 1)
+        data = np.stack([1.0 + 0 * x, 2.0 * x - 1.0, x ** 3 - 0.5 * x ** 2, x ** 4])
+        lines.append((N, C, 1.0 / (N - 1), data))
+    res = _run_fc(exe, env, str(tmp_path), lines)
+    for (N, C, h, data), outs in zip(lines, res):
+        x = np.arange(N) / (N - 1)
+        exact = np.stack([0 * x, 2.0 + 0 * x, 3 * x ** 2 - x, 4 * x ** 3])
+        for o in outs:
+            assert np.abs(o - exact).max() < 1e-11 * N, (N, np.abs(o - exact).max())
