@@ -10,10 +10,11 @@
 //     derivative; prints "L order max_rel_err" per candidate.
 //
 //   line_engine_host fc <in> <out>
-//     FC derivatives (continuation + transform) of lines read from <in>:
-//       int32 d, int32 ntab, double tab[ntab] (the packed FC-Gram tables), int32 nlines,
-//       then per line int32 N, int32 C, double h, double data[4][N];
-//     <out> gets, per line, int32 ncand and ncand x double deriv[4][N] (one result per
+//     FC derivatives or FC filters (continuation + transform) of lines read from <in>:
+//       int32 d, double alpha_f, int32 p_f, int32 ntab, double tab[ntab] (the packed
+//       FC-Gram tables), int32 nlines, then per line int32 op (0: derivative, 1: filter),
+//       int32 N, int32 C, double h, double data[4][N];
+//     <out> gets, per line, int32 ncand and ncand x double result[4][N] (one per
 //     candidate stage order of the continued length N + C).
 #include "../paper_2506_16076_gb300/csrc/fc_host.cpp"
 #include "../paper_2506_16076_gb300/csrc/fc_line.cuh"
@@ -23,13 +24,17 @@
 
 namespace {
 
-// derivative of the 4 components of one line (two packed sequences) with plan P, as deriv2 does
+// derivative (filter: the spectral filter) of the 4 components of one line (two packed
+// sequences) with plan P, as the kernels' deriv2 (filter2) does
 void derive(double2* A, int Lmax, const fcx::Plan& P, int n, int C, int fcm, double scale, int d,
-            const Builder& B) {
+            const Builder& B, bool filter = false) {
   using namespace fcx;
   if (fcm >= 0) continue_lines(A, P.L, n, C, d, B.rp.data() + fcm, 2, 0, 1, A + 2 * Lmax);
   fft_inplace<false>(A, P, 2, B.tw.data(), 0, 1);
-  mul_deriv_rev(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.ip.data() + P.rev, 0, 1);
+  if (filter)
+    mul_filter_rev(A, P.L, 2, B.rp.data() + P.sig, B.ip.data() + P.rev, 0, 1);
+  else
+    mul_deriv_rev(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.ip.data() + P.rev, 0, 1);
   fft_inplace<true>(A, P, 2, B.tw.data(), 0, 1);
 }
 
@@ -90,9 +95,14 @@ int run_fc(const char* in, const char* out) {
   FILE* fi = fopen(in, "rb");
   FILE* fo = fopen(out, "wb");
   if (!fi || !fo) return 2;
-  int d = 0, ntab = 0, nlines = 0;
-  if (fread(&d, 4, 1, fi) != 1 || fread(&ntab, 4, 1, fi) != 1) return 3;
+  int d = 0, ntab = 0, nlines = 0, pf = 0;
+  double af = 0;
+  if (fread(&d, 4, 1, fi) != 1 || fread(&af, 8, 1, fi) != 1 || fread(&pf, 4, 1, fi) != 1 ||
+      fread(&ntab, 4, 1, fi) != 1)
+    return 3;
   fc_ctx c;
+  c.prm.alpha_f = af;
+  c.prm.p_f = pf;
   c.fctab.resize(ntab);
   if (fread(c.fctab.data(), 8, ntab, fi) != (size_t)ntab) return 3;
   c.d = d;
@@ -101,9 +111,11 @@ int run_fc(const char* in, const char* out) {
   Builder B{&c};
   if (fread(&nlines, 4, 1, fi) != 1) return 3;
   for (int l = 0; l < nlines; ++l) {
-    int N = 0, C = 0;
+    int op = 0, N = 0, C = 0;
     double h = 0;
-    if (fread(&N, 4, 1, fi) != 1 || fread(&C, 4, 1, fi) != 1 || fread(&h, 8, 1, fi) != 1) return 3;
+    if (fread(&op, 4, 1, fi) != 1 || fread(&N, 4, 1, fi) != 1 || fread(&C, 4, 1, fi) != 1 ||
+        fread(&h, 8, 1, fi) != 1)
+      return 3;
     std::vector<double> data(4 * (size_t)N);
     if (fread(data.data(), 8, data.size(), fi) != data.size()) return 3;
     const int fcm = B.fcm(C);
@@ -117,7 +129,7 @@ int run_fc(const char* in, const char* out) {
         A[t] = cpx(data[t], data[N + t]);
         A[L + t] = cpx(data[2 * N + t], data[3 * N + t]);
       }
-      derive(A.data(), L, P, N, C, fcm, 1.0 / h, d, B);
+      derive(A.data(), L, P, N, C, fcm, 1.0 / h, d, B, op == 1);
       std::vector<double> o(4 * (size_t)N);
       for (int t = 0; t < N; ++t) {
         o[t] = A[t].x;

@@ -7,7 +7,9 @@ fc_line.cuh and plan builder the GPU runs, one lane per line) checked on the CPU
 - the FC derivative (detrended two-phase continuation, in-place transforms, digit-
   reversed multiplier) of every candidate order matches the oracle's long-double FC
   derivative (Sec. 2.2, eq. fc_der) on smooth lines, and differentiates polynomials of
-  degree below d exactly up to rounding.
+  degree below d exactly up to rounding;
+- the FC filter (Sec. 4.3.1, eq. filtering) of every candidate order matches the
+  oracle's.
 """
 import os
 import shutil
@@ -60,16 +62,19 @@ def test_every_candidate_stage_order_differentiates_exactly(harness):
     assert float(worst[2]) < 2e-14, worst
 
 
-def _run_fc(exe, env, tmp, lines, d=5):
+ALPHA_F, P_F = 10.0, 14  # the paper's filter parameters (Sec. 4.3.1)
+
+
+def _run_fc(exe, env, tmp, lines, d=5, op=0):
     from paper_2506_16076_gb300 import fcsdnn
     tab = np.asarray(fcsdnn.fc_table_blob(d), dtype=np.float64)
     fin, fout = os.path.join(tmp, "in.bin"), os.path.join(tmp, "out.bin")
     with open(fin, "wb") as f:
-        f.write(struct.pack("<ii", d, tab.size))
+        f.write(struct.pack("<idii", d, ALPHA_F, P_F, tab.size))
         f.write(tab.tobytes())
         f.write(struct.pack("<i", len(lines)))
         for (N, C, h, data) in lines:
-            f.write(struct.pack("<iid", N, C, h))
+            f.write(struct.pack("<iiid", op, N, C, h))
             f.write(np.ascontiguousarray(data, dtype=np.float64).tobytes())
     r = subprocess.run([exe, "fc", fin, fout], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, r.stderr
@@ -86,9 +91,8 @@ def _run_fc(exe, env, tmp, lines, d=5):
     return res
 
 
-def test_fc_derivative_matches_the_oracle(harness, tmp_path):
-    exe, env = harness
-    rng = np.random.default_rng(8)
+def _smooth_lines(seed):
+    rng = np.random.default_rng(seed)
     lines = []
     for N in (10, 37, 64, 101, 160, 257, 384, 640):
         C = F.choose_C(N, 27, 2, 5)
@@ -98,6 +102,23 @@ def test_fc_derivative_matches_the_oracle(harness, tmp_path):
             a, b, c, k = rng.uniform(-1, 1, 4)
             comps.append(5.0 + a * np.sin(3.0 * k * x + b) + c * np.exp(x) * np.cos(2.0 * x))
         lines.append((N, C, 1.0 / (N - 1), np.stack(comps)))
+    return lines
+
+
+def test_fc_filter_matches_the_oracle(harness, tmp_path):
+    exe, env = harness
+    lines = _smooth_lines(9)
+    res = _run_fc(exe, env, str(tmp_path), lines, op=1)
+    for (N, C, h, data), outs in zip(lines, res):
+        ref = F.fc_filter(data, 5, C, ALPHA_F, P_F)
+        for o in outs:
+            err = np.abs(o - ref).max() / np.abs(ref).max()
+            assert err < 1e-14 * max(1.0, N / 64), (N, C, err)
+
+
+def test_fc_derivative_matches_the_oracle(harness, tmp_path):
+    exe, env = harness
+    lines = _smooth_lines(8)
     res = _run_fc(exe, env, str(tmp_path), lines)
     for (N, C, h, data), outs in zip(lines, res):
         ref = F.fc_derivative(data, h, 5, C)
