@@ -16,6 +16,13 @@
 //       int32 N, int32 C, double h, double data[4][N];
 //     <out> gets, per line, int32 ncand and ncand x double result[4][N] (one per
 //     candidate stage order of the continued length N + C).
+//
+//   line_engine_host grid <in> <out>
+//     the host geometry of a GRID patch (fc_host.cpp build_patch, frac_index): <in> holds
+//       int32 n1, int32 n2, int32 periodic1, double x[n2][n1], double y[n2][n1],
+//       int32 nq, double xq[nq], double yq[nq];
+//     <out> gets double hhat, double htil, double s1[nq], double s2[nq] (the fractional
+//     indices of the query points; far outside the grid when not located).
 #include "../paper_2506_16076_gb300/csrc/fc_host.cpp"
 #include "../paper_2506_16076_gb300/csrc/fc_line.cuh"
 
@@ -145,11 +152,50 @@ int run_fc(const char* in, const char* out) {
   return 0;
 }
 
+int run_grid(const char* in, const char* out) {
+  FILE* fi = fopen(in, "rb");
+  FILE* fo = fopen(out, "wb");
+  if (!fi || !fo) return 2;
+  int n1 = 0, n2 = 0, per = 0, nq = 0;
+  if (fread(&n1, 4, 1, fi) != 1 || fread(&n2, 4, 1, fi) != 1 || fread(&per, 4, 1, fi) != 1) return 3;
+  const size_t N = (size_t)n1 * n2;
+  std::vector<double> x(N), y(N);
+  if (fread(x.data(), 8, N, fi) != N || fread(y.data(), 8, N, fi) != N || fread(&nq, 4, 1, fi) != 1) return 3;
+  std::vector<double> xq(nq), yq(nq);
+  if (fread(xq.data(), 8, nq, fi) != (size_t)nq || fread(yq.data(), 8, nq, fi) != (size_t)nq) return 3;
+  HPatch h;
+  std::memset(&h.d, 0, sizeof(h.d));
+  h.d.kind = FC_PATCH_GRID;
+  h.d.n1 = n1;
+  h.d.n2 = n2;
+  for (int s = 0; s < 4; ++s) h.d.side[s] = (per && s < 2) ? FC_SIDE_PERIODIC : FC_SIDE_DIRICHLET;
+  h.d.hole[2] = -1.0;
+  h.d.x = x.data();
+  h.d.y = y.data();
+  fc_params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.d = 5;
+  prm.n_f = 5;
+  prm.n_v = 9;
+  prm.depth_cap = 64;
+  build_patch(h, prm);
+  fwrite(&h.hhat, 8, 1, fo);
+  fwrite(&h.htil, 8, 1, fo);
+  std::vector<double> s1(nq), s2(nq);
+  for (int q = 0; q < nq; ++q) frac_index(h, xq[q], yq[q], s1[q], s2[q]);
+  fwrite(s1.data(), 8, nq, fo);
+  fwrite(s2.data(), 8, nq, fo);
+  fclose(fi);
+  fclose(fo);
+  return 0;
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
   if (argc >= 2 && std::string(argv[1]) == "plans") return run_plans(argc, argv);
   if (argc == 4 && std::string(argv[1]) == "fc") return run_fc(argv[2], argv[3]);
-  fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out>\n");
+  if (argc == 4 && std::string(argv[1]) == "grid") return run_grid(argv[2], argv[3]);
+  fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out> | grid <in> <out>\n");
   return 1;
 }

@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 from oracle import fc as F
+from paper_2506_16076_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CUDA_INC = "/usr/local/cuda/include"
@@ -143,3 +144,56 @@ def test_fc_derivative_exact_on_polynomials(harness, tmp_path):
         exact = np.stack([0 * x, 2.0 + 0 * x, 3 * x ** 2 - x, 4 * x ** 3])
         for o in outs:
             assert np.abs(o - exact).max() < 1e-11 * N, (N, np.abs(o - exact).max())
+
+
+def _run_grid(exe, env, tmp, p, xq, yq):
+    fin, fout = os.path.join(tmp, "g.bin"), os.path.join(tmp, "go.bin")
+    periodic = int(p.side[0] == W.PERIODIC)
+    with open(fin, "wb") as f:
+        f.write(struct.pack("<iii", p.n1, p.n2, periodic))
+        f.write(np.ascontiguousarray(p.x, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(p.y, dtype=np.float64).tobytes())
+        f.write(struct.pack("<i", len(xq)))
+        f.write(np.asarray(xq, dtype=np.float64).tobytes())
+        f.write(np.asarray(yq, dtype=np.float64).tobytes())
+    r = subprocess.run([exe, "grid", fin, fout], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    v = np.fromfile(fout, dtype=np.float64)
+    nq = len(xq)
+    return v[0], v[1], v[2:2 + nq], v[2 + nq:2 + 2 * nq]
+
+
+@pytest.mark.parametrize("kind", ["annulus", "bulged_box", "thin_strip"])
+def test_host_grid_inverse_matches_the_oracle(harness, tmp_path, kind):
+    # the library's host geometry of a GRID patch (bucketed nearest point, Newton on the
+    # local quadratic interpolant) locates points exactly where the oracle does
+    from oracle import geometry
+    exe, env = harness
+    fs = (1.4, 1.0, 0.0, 1.0)
+    if kind == "annulus":
+        p = W.grid_patch(W.annulus_map(0.0, 0.0, 0.5, 1.5, 0.15, 0.3), 96, 24,
+                         (W.PERIODIC, W.PERIODIC, W.DIRICHLET, W.DIRICHLET), (fs,) * 4, periodic1=True)
+    elif kind == "bulged_box":
+        p = W.grid_patch(W.affine_map(-1.0, 2.0, -0.5, 1.0, bump=0.05), 61, 33, (W.DIRICHLET,) * 4, (fs,) * 4)
+    else:  # a long thin diagonal strip: its bounding box is large against its spacings
+        def strip(a, b):
+            return (10.0 * a + 0.02 * b, 10.0 * a - 0.02 * b, 10.0 + 0 * a, 0.02 + 0 * a, 10.0 + 0 * a,
+                    -0.02 + 0 * a)
+        p = W.grid_patch(strip, 2000, 4, (W.DIRICHLET,) * 4, (fs,) * 4)
+    g = geometry.PatchGeo(p, W.Params(d=5, C0=27, c_policy=2))
+    rng = np.random.default_rng(4)
+    x0, x1, y0, y1 = g.bbox()
+    wx, wy = x1 - x0, y1 - y0
+    xq = np.concatenate([rng.uniform(x0 - 0.1 * wx, x1 + 0.1 * wx, 400), g.x.ravel()[::37]])
+    yq = np.concatenate([rng.uniform(y0 - 0.1 * wy, y1 + 0.1 * wy, 400), g.y.ravel()[::37]])
+    hhat, htil, s1, s2 = _run_grid(exe, env, str(tmp_path), p, xq, yq)
+    assert abs(hhat - g.hhat) <= 1e-15 * g.hhat and abs(htil - g.htil) <= 1e-15 * g.htil
+    o1, o2 = g.frac_index(xq, yq)
+    found_o, found_h = o1 > -1e8, s1 > -1e8
+    assert np.array_equal(found_o, found_h)
+    assert found_o.sum() > 20
+    d1 = s1[found_o] - o1[found_o]
+    if g.periodic1:
+        d1 = np.mod(d1 + 0.5 * g.n1, g.n1) - 0.5 * g.n1
+    assert np.abs(d1).max() < 1e-10 and np.abs(s2[found_o] - o2[found_o]).max() < 1e-10
+    assert np.array_equal(g.contains(o1, o2), g.contains(s1, s2))
