@@ -17,6 +17,13 @@
 //     <out> gets, per line, int32 ncand and ncand x double result[4][N] (one per
 //     candidate stage order of the continued length N + C).
 //
+//   line_engine_host policy C0 policy Cmax N0 N1
+//     the continuation length the library picks for every line length N0..N1
+//     (choose_continuation), one "N C" pair per line.
+//
+//   line_engine_host adw d
+//     the no-slip adiabatic wall weights (adiabatic_weights) for d, one per line.
+//
 //   line_engine_host grid <in> <out>
 //     the host geometry of a GRID patch (fc_host.cpp build_patch, frac_index): <in> holds
 //       int32 n1, int32 n2, int32 periodic1, double x[n2][n1], double y[n2][n1],
@@ -190,12 +197,30 @@ int run_grid(const char* in, const char* out) {
   return 0;
 }
 
+int run_policy(char** argv) {
+  fc_params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.C0 = atoi(argv[2]);
+  prm.c_policy = atoi(argv[3]);
+  prm.d = 5;
+  const int Cmax = atoi(argv[4]);
+  for (int N = atoi(argv[5]); N <= atoi(argv[6]); ++N) printf("%d %d\n", N, choose_continuation(N, prm, Cmax));
+  return 0;
+}
+
+int run_adw(char** argv) {
+  for (double w : adiabatic_weights(atoi(argv[2]))) printf("%.17g\n", w);
+  return 0;
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
   if (argc >= 2 && std::string(argv[1]) == "plans") return run_plans(argc, argv);
   if (argc == 4 && std::string(argv[1]) == "fc") return run_fc(argv[2], argv[3]);
   if (argc == 4 && std::string(argv[1]) == "grid") return run_grid(argv[2], argv[3]);
-  fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out> | grid <in> <out>\n");
+  if (argc == 7 && std::string(argv[1]) == "policy") return run_policy(argv);
+  if (argc == 3 && std::string(argv[1]) == "adw") return run_adw(argv);
+  fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out> | grid <in> <out> | policy ... | adw d\n");
   return 1;
 }

@@ -197,3 +197,27 @@ def test_host_grid_inverse_matches_the_oracle(harness, tmp_path, kind):
         d1 = np.mod(d1 + 0.5 * g.n1, g.n1) - 0.5 * g.n1
     assert np.abs(d1).max() < 1e-10 and np.abs(s2[found_o] - o2[found_o]).max() < 1e-10
     assert np.array_equal(g.contains(o1, o2), g.contains(s1, s2))
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2])
+def test_host_continuation_length_matches_the_oracle(harness, policy):
+    # both sides implement the C rules (the paper leaves C free, Sec. 2.2) independently
+    exe, env = harness
+    lo, hi = F.table_range(5)
+    r = subprocess.run([exe, "policy", "27", str(policy), str(hi), "10", "2100"], capture_output=True, text=True,
+                       env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    got = dict(tuple(map(int, ln.split())) for ln in r.stdout.splitlines())
+    bad = [(N, C, F.choose_C(N, 27, policy, 5)) for N, C in got.items() if C != F.choose_C(N, 27, policy, 5)]
+    assert not bad, bad[:10]
+
+
+@pytest.mark.parametrize("d", [3, 4, 5, 6])
+def test_host_adiabatic_weights_match_the_oracle(harness, d):
+    from oracle import solver as S
+    exe, env = harness
+    r = subprocess.run([exe, "adw", str(d)], capture_output=True, text=True, env=env, timeout=60)
+    assert r.returncode == 0, r.stderr
+    got = np.array([float(v) for v in r.stdout.split()])
+    ref = np.array([float(v) for v in S.adiabatic_weights(d)])
+    assert got.shape == ref.shape and np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max()
