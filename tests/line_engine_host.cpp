@@ -17,6 +17,12 @@
 //     <out> gets, per line, int32 ncand and ncand x double result[4][N] (one per
 //     candidate stage order of the continued length N + C).
 //
+//   line_engine_host patch <in> <out>
+//     the host geometry of one patch (build_patch): <in> holds int32 kind, n1, n2,
+//     double geom[4], int32 side[4], double hole[3], and for GRID double x[n2][n1],
+//     y[n2][n1]; <out> gets double hhat, htil, then uint8 blank, receiver, generating,
+//     no-derivative [n2][n1] and int32 depth [n2][n1].
+//
 //   line_engine_host policy C0 policy Cmax N0 N1
 //     the continuation length the library picks for every line length N0..N1
 //     (choose_continuation), one "N C" pair per line.
@@ -197,6 +203,47 @@ int run_grid(const char* in, const char* out) {
   return 0;
 }
 
+int run_patch(const char* in, const char* out) {
+  FILE* fi = fopen(in, "rb");
+  FILE* fo = fopen(out, "wb");
+  if (!fi || !fo) return 2;
+  HPatch h;
+  std::memset(&h.d, 0, sizeof(h.d));
+  int hdr[3];
+  if (fread(hdr, 4, 3, fi) != 3 || fread(h.d.geom, 8, 4, fi) != 4 || fread(h.d.side, 4, 4, fi) != 4 ||
+      fread(h.d.hole, 8, 3, fi) != 3)
+    return 3;
+  h.d.kind = hdr[0];
+  h.d.n1 = hdr[1];
+  h.d.n2 = hdr[2];
+  const size_t N = (size_t)hdr[1] * hdr[2];
+  std::vector<double> x, y;
+  if (h.d.kind == FC_PATCH_GRID) {
+    x.resize(N);
+    y.resize(N);
+    if (fread(x.data(), 8, N, fi) != N || fread(y.data(), 8, N, fi) != N) return 3;
+    h.d.x = x.data();
+    h.d.y = y.data();
+  }
+  fc_params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.d = 5;
+  prm.n_f = 5;
+  prm.n_v = 9;
+  prm.depth_cap = 64;
+  build_patch(h, prm);
+  fwrite(&h.hhat, 8, 1, fo);
+  fwrite(&h.htil, 8, 1, fo);
+  fwrite(h.blank.data(), 1, N, fo);
+  fwrite(h.recv.data(), 1, N, fo);
+  fwrite(h.gen.data(), 1, N, fo);
+  fwrite(h.nodiff.data(), 1, N, fo);
+  fwrite(h.depth.data(), 4, N, fo);
+  fclose(fi);
+  fclose(fo);
+  return 0;
+}
+
 int run_policy(char** argv) {
   fc_params prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -220,6 +267,7 @@ int main(int argc, char** argv) {
   if (argc == 4 && std::string(argv[1]) == "fc") return run_fc(argv[2], argv[3]);
   if (argc == 4 && std::string(argv[1]) == "grid") return run_grid(argv[2], argv[3]);
   if (argc == 7 && std::string(argv[1]) == "policy") return run_policy(argv);
+  if (argc == 4 && std::string(argv[1]) == "patch") return run_patch(argv[2], argv[3]);
   if (argc == 3 && std::string(argv[1]) == "adw") return run_adw(argv);
   fprintf(stderr, "usage: line_engine_host plans L... | fc <in> <out> | grid <in> <out> | policy ... | adw d\n");
   return 1;

@@ -221,3 +221,50 @@ def test_host_adiabatic_weights_match_the_oracle(harness, d):
     got = np.array([float(v) for v in r.stdout.split()])
     ref = np.array([float(v) for v in S.adiabatic_weights(d)])
     assert got.shape == ref.shape and np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max()
+
+
+def _patches_for_geometry():
+    w = W.small_multipatch()
+    wc = W.small_multipatch_grid(curved=True)
+    st = W.small_multipatch_stype()
+    m25 = W.cyl_m25_32()
+    holed = [p for p in m25.patches[1:] if p.hole[2] > 0 and 0 < int(
+        np.sum(np.hypot(*W.patch_xy(p)) < p.hole[2])) < p.npts][:2]
+    return {"ogrid": w.patches[0], "box_hole": w.patches[1], "grid_annulus": wc.patches[0],
+            "grid_bulged_hole": wc.patches[2], "s_type_arc": st.patches[0], "m25_holed_a": holed[0],
+            "m25_holed_b": holed[1]}
+
+
+@pytest.mark.parametrize("name", list(_patches_for_geometry().keys()))
+def test_host_patch_geometry_matches_the_oracle(harness, tmp_path, name):
+    # blanking, the fringe/depth distances (eq. fringe_region), receivers, generating
+    # points and no-derivative points of the library's build_patch against the oracle's
+    from oracle import geometry
+    exe, env = harness
+    p = _patches_for_geometry()[name]
+    fin, fout = os.path.join(str(tmp_path), "p.bin"), os.path.join(str(tmp_path), "po.bin")
+    with open(fin, "wb") as f:
+        f.write(struct.pack("<iii", p.kind, p.n1, p.n2))
+        f.write(struct.pack("<4d", *p.geom))
+        f.write(struct.pack("<4i", *p.side))
+        f.write(struct.pack("<3d", *p.hole))
+        if p.kind == W.GRID:
+            f.write(np.ascontiguousarray(p.x, dtype=np.float64).tobytes())
+            f.write(np.ascontiguousarray(p.y, dtype=np.float64).tobytes())
+    r = subprocess.run([exe, "patch", fin, fout], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    raw = open(fout, "rb").read()
+    N = p.n1 * p.n2
+    hhat, htil = struct.unpack_from("<2d", raw, 0)
+    off = 16
+    arrs = {}
+    for k in ("blank", "receiver", "gen", "nodiff"):
+        arrs[k] = np.frombuffer(raw, dtype=np.uint8, count=N, offset=off).reshape(p.n2, p.n1).astype(bool)
+        off += N
+    depth = np.frombuffer(raw, dtype=np.int32, count=N, offset=off).reshape(p.n2, p.n1)
+    g = geometry.PatchGeo(p, W.Params(d=5, C0=27, c_policy=2))
+    assert abs(hhat - g.hhat) <= 1e-14 * g.hhat and abs(htil - g.htil) <= 1e-14 * g.htil
+    for k in ("blank", "receiver", "gen", "nodiff"):
+        assert np.array_equal(arrs[k], getattr(g, k)), k
+    nb = ~g.blank
+    assert np.array_equal(depth[nb], g.depth[nb])
