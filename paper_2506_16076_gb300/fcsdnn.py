@@ -151,7 +151,11 @@ def _stream():
 
 
 class Context:
-    """One fc_ctx: geometry and device workspaces of a workload."""
+    """One fc_ctx: geometry and device workspaces of a workload.
+
+    States are device tensors of 4 * P doubles in the library's layout (component-major,
+    patches concatenated in workload order, each row-major with q1 fastest); every call
+    runs on the current torch stream."""
 
     def __init__(self, workload: W.Workload):
         lib = load()
@@ -174,7 +178,7 @@ class Context:
             if p.kind == W.GRID:  # host arrays, kept alive until fc_init_patches returns
                 ptrs = []
                 for a, m in ((p.x, 1), (p.y, 1), (p.metrics, 4)):
-                    if a is None:  # left null: the library rejects the descriptor
+                    if a is None:  # null: metrics are then computed by the library; x, y are required
                         ptrs.append(None)
                         continue
                     a = np.ascontiguousarray(a, dtype=np.float64)
