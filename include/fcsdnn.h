@@ -253,9 +253,10 @@ fc_status fc_pass_stats(const fc_ctx *ctx, const char *pass, double *flops, doub
  * rhs_dev = L[e_dev] on the box [box[0], box[1]] x [box[2], box[3]] (host array) with
  * n1 x n2 points (q1 fastest, state layout as above, P = n1 n2), viscosity mu_dev,
  * FC order d and C continuation points on every line; table: host array of the
- * d x d Q, C x d A_l and C x d A_r blocks (one C block of the fc_params tables).
+ * d x d Q, C x d A_l and C x d A_r blocks (one C block of the fc_params tables), of
+ * table_len = d d + 2 C d values (any other length: FC_ERR_INVALID).
  * No boundary condition is applied (as in fc_rhs). The scratch is one static device
- * array of about 18 MB held by every GPU that loads the library until exit; limits:
+ * array of 9.6 MB (9,597,184 bytes) held by every GPU that loads the library until exit; limits:
  * n1 n2 <= 262144, n + C <= 1024, C <= 128, d <= 8 (beyond them the call prints the
  * limits to stderr and returns FC_ERR_INVALID). All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU (other streams, other host
@@ -263,7 +264,8 @@ fc_status fc_pass_stats(const fc_ctx *ctx, const char *pass, double *flops, doub
  * that device current; make that first call before any stream capture. The call
  * synchronises the stream once (table upload from host memory). */
 fc_status fc_rhs_patch_noalloc(const double *e_dev, const double *mu_dev, double *rhs_dev, int n1, int n2,
-                               const double *box, int d, int C, const double *table, double gamma, void *stream);
+                               const double *box, int d, int C, const double *table, int table_len, double gamma,
+                               void *stream);
 
 const char *fc_last_error(const fc_ctx *ctx);
 void fc_destroy(fc_ctx *ctx);

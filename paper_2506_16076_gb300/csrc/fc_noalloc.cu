@@ -68,8 +68,8 @@ std::vector<int> na_factorize(int L) {
 }  // namespace
 
 extern "C" fc_status fc_rhs_patch_noalloc(const double* e_dev, const double* mu_dev, double* rhs_dev, int n1, int n2,
-                                          const double* box, int d, int C, const double* table, double gamma,
-                                          void* stream) {
+                                          const double* box, int d, int C, const double* table, int table_len,
+                                          double gamma, void* stream) {
   if (!e_dev || !mu_dev || !rhs_dev || !box || !table) return FC_ERR_INVALID;
   if ((long long)n1 * n2 > NA_MAX_POINTS || n1 + C > NA_MAX_L || n2 + C > NA_MAX_L || C > NA_MAX_C || d > NA_MAX_D) {
     fprintf(stderr,
@@ -79,6 +79,11 @@ extern "C" fc_status fc_rhs_patch_noalloc(const double* e_dev, const double* mu_
     return FC_ERR_INVALID;
   }
   if (n1 < 2 * d || n2 < 2 * d || C < 1 || d < 2 || !(box[1] > box[0]) || !(box[3] > box[2])) return FC_ERR_INVALID;
+  if (table_len != d * d + 2 * C * d) {  // one (Q, A_l, A_r) block of this d and C, nothing else
+    fprintf(stderr, "fc_rhs_patch_noalloc: table holds %d values, the d = %d, C = %d block needs %d\n", table_len, d,
+            C, d * d + 2 * C * d);
+    return FC_ERR_INVALID;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return FC_ERR_CUDA;
   if (!g_scratch[dev]) {  // set-up, once per device, with that device current

@@ -90,7 +90,7 @@ def load():
         "fc_line_stats": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), ip]),
         "fc_rhs_patch_noalloc": (C.c_int, [vp, vp, vp, ip, ip, C.POINTER(C.c_double), ip, ip,
-                                           C.POINTER(C.c_double), C.c_double, vp]),
+                                           C.POINTER(C.c_double), ip, C.c_double, vp]),
         "fc_last_error": (C.c_char_p, [vp]),
         "fc_destroy": (None, [vp]),
     }
@@ -293,16 +293,34 @@ class Context:
         self._check(self.lib.fc_profile_reset(self.ctx))
 
 
+def _check_field(t, name, numel):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and t.numel() == numel):
+        raise FcError(FC_ERR_INVALID, f"{name} must be a contiguous CUDA float64 tensor of {numel} elements")
+
+
 def rhs_patch_noalloc(e, mu, out, n1, n2, box, d, ncont, gamma=W.GAMMA):
     """fc_rhs_patch_noalloc: RHS of one stand-alone affine patch, no device allocation."""
     lib = load()
+    n1, n2, d, ncont = int(n1), int(n2), int(d), int(ncont)
     tab = fc_table_blob(d)
-    cmin = int(tab[1])
+    cmin, cmax = int(tab[1]), int(tab[2])
+    if not cmin <= ncont <= cmax:
+        raise FcError(FC_ERR_INVALID, f"C = {ncont} is outside the tabulated range [{cmin}, {cmax}] for d = {d}")
+    if n1 <= 0 or n2 <= 0:
+        raise FcError(FC_ERR_INVALID, f"bad patch size {n1} x {n2}")
+    _check_field(e, "e", 4 * n1 * n2)
+    _check_field(out, "out", 4 * n1 * n2)
+    _check_field(mu, "mu", n1 * n2)
     off = 3 + sum(d * d + 2 * c * d for c in range(cmin, ncont))
     block = np.ascontiguousarray(tab[off:off + d * d + 2 * ncont * d])
     bx = np.ascontiguousarray(np.asarray(box, dtype=np.float64))
-    st = lib.fc_rhs_patch_noalloc(_ptr(e), _ptr(mu), _ptr(out), int(n1), int(n2),
-                                  bx.ctypes.data_as(C.POINTER(C.c_double)), int(d), int(ncont),
-                                  block.ctypes.data_as(C.POINTER(C.c_double)), float(gamma), _stream())
+    if bx.shape != (4,):
+        raise FcError(FC_ERR_INVALID, "box must hold (x0, x1, y0, y1)")
+    st = lib.fc_rhs_patch_noalloc(_ptr(e), _ptr(mu), _ptr(out), n1, n2,
+                                  bx.ctypes.data_as(C.POINTER(C.c_double)), d, ncont,
+                                  block.ctypes.data_as(C.POINTER(C.c_double)), int(block.size), float(gamma),
+                                  _stream())
     if st != FC_OK:
         raise FcError(st, "fc_rhs_patch_noalloc failed (see stderr)")

@@ -126,7 +126,7 @@ def test_fc_filter_keeps_smooth_lines():
     assert np.abs(G - F).max() < 1e-11  # continuation high modes are tiny but not zero
 
 
-def test_choose_C_policies():
+def test_choose_C_policy_1_is_minimal():
     assert fc.choose_C(128, 27, 0) == 27
     for N in range(10, 1100):
         C = fc.choose_C(N, 27, 1)

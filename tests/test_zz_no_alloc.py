@@ -1,13 +1,16 @@
 """The allocation-free single-patch RHS entry point against the context-based fc_rhs.
 
-Callers that cannot allocate device memory use fc_rhs_patch_noalloc: its scratch is a
-static device array, so the check here is that it reproduces fc_rhs of the same patch
-(within the RHS tolerance of the other GPU tests) on two calls in a row, i.e. that the
-shared array carries nothing from one call into the next."""
+Callers that cannot allocate device memory (code inside a host memory manager that owns
+all device memory, plug-ins whose host forbids allocation) use fc_rhs_patch_noalloc: its
+scratch is a static device array, so the check here is that it reproduces fc_rhs of the
+same patch (within the RHS tolerance of the other GPU tests) on two calls in a row, i.e.
+that the shared array carries nothing from one call into the next; on a rectangular box
+it is also held to the oracle."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import solver as S
 from paper_2506_16076_gb300 import workloads as W
 from tests.gpu_helpers import from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
 
@@ -32,6 +35,50 @@ def test_noalloc_rhs_matches_context_rhs(gpu_lib):
         torch.cuda.synchronize()
         errs = rel_err(from_dev(out, w), from_dev(ref, w))
         assert max(errs) < 1e-11, errs
+
+
+def _box(n1, n2, box, C):
+    fs = (1.0, 0.0, 0.0, 1.0)
+    p = W.PatchDesc(W.AFFINE, n1, n2, box, (W.DIRICHLET,) * 4, bc=(fs,) * 4)
+    return W.Workload(f"box{n1}x{n2}", [p], W.Params(d=5, C0=C, c_policy=0), freestream=fs, init="freestream",
+                      steps=1)
+
+
+@pytest.mark.parametrize("n1,n2,box,C", [
+    (160, 72, (-0.3, 1.9, 0.25, 0.9), 33),  # rectangular, non-unit box, another C
+    (997, 37, (0.0, 2.0, -0.5, 0.5), 27),   # the largest continued length, n1 + C = 1024
+])
+def test_noalloc_rectangular_and_longest(gpu_lib, n1, n2, box, C):
+    w = _box(n1, n2, box, C)
+    ctx = gpu_lib.Context(w)
+    for seed in (7, 8):  # two calls in a row
+        st = W.random_smooth_state(w, seed=seed, amp=0.2)
+        mu = smooth_mu(w, seed=seed, scale=0.01)
+        e, m = to_dev(st), to_dev_scalar_field(mu)
+        ref = torch.empty_like(e)
+        ctx.rhs(e, ref, m)
+        out = torch.full_like(e, float("nan"))
+        gpu_lib.rhs_patch_noalloc(e, m, out, n1, n2, box, 5, C, w.params.gamma)
+        torch.cuda.synchronize()
+        got = from_dev(out, w)
+        errs = rel_err(got, from_dev(ref, w))
+        assert max(errs) < 1e-11, errs
+        if n1 < 500:
+            errs = rel_err(got, S.Solver(w).rhs(st, mu))
+            assert max(errs) < 1e-11, errs
+
+
+def test_noalloc_rejects_bad_arguments(gpu_lib):
+    n1, n2 = 64, 48
+    e = torch.zeros(4, n1 * n2, dtype=torch.float64, device="cuda")
+    m = torch.zeros(n1 * n2, dtype=torch.float64, device="cuda")
+    box = (0.0, 1.0, 0.0, 1.0)
+    with pytest.raises(gpu_lib.FcError):  # C outside the tabulated range
+        gpu_lib.rhs_patch_noalloc(e, m, e.clone(), n1, n2, box, 5, 200)
+    with pytest.raises(gpu_lib.FcError):  # state of the wrong size
+        gpu_lib.rhs_patch_noalloc(e[:, :-1].contiguous(), m, e.clone(), n1, n2, box, 5, 27)
+    with pytest.raises(gpu_lib.FcError):  # viscosity of the wrong dtype
+        gpu_lib.rhs_patch_noalloc(e, m.float(), e.clone(), n1, n2, box, 5, 27)
 
 
 def test_noalloc_rejects_oversized_patch(gpu_lib):
