@@ -119,6 +119,13 @@ typedef struct {
   int fc_tables_len;
   const float *sdnn_w;
   int sdnn_len;
+  /* Free stream (rho, u, v, p) of the problem (Sec. 7, eq. mach_flow_ic), or rho <= 0 for
+   * none. It drives the Dirichlet data: a DIRICHLET side whose bc density is 0 holds the
+   * free stream. Dirichlet points that hold it (that way, or through a bc equal to it) are
+   * the free-stream points whose adjoint fc_adjoint_step turns into dJ/dM and dJ/dalpha,
+   * M = |(u, v)| / a the Mach number and alpha = atan2(v, u) the angle of attack, at fixed
+   * density and pressure (sound speed a = sqrt(gamma p / rho)). */
+  double freestream[4];
 } fc_params;
 
 /* fc_rk_step flags */
@@ -200,10 +207,27 @@ fc_status fc_autotune(fc_ctx *ctx, int flags, double *report, void *stream);
  * (linearised at the state it was applied to: theta and E rebuild Jacobians around
  * the line filters, whose transposes fold the continuation back like the derivative's).
  * gbc_dev (nullable, [4][P]) accumulates the adjoint that reaches the Dirichlet
- * points, i.e. the sensitivity of the step result to the imposed states. The first
- * call allocates 11 state-sized device buffers, and 2 more with the filter. */
+ * points, i.e. the sensitivity of the step result to the imposed states.
+ * dparam_dev (nullable, 2 device doubles) accumulates, in a fixed order, the part of
+ * dJ/d(M, alpha) that enters through the free-stream Dirichlet states during this step:
+ * the sum over the free-stream points of that adjoint times d e_fs / d(M, alpha)
+ * (FC_ERR_INVALID when fc_params.freestream is not set). The first call allocates 11
+ * state-sized device buffers, and 2 more with the filter. */
 fc_status fc_adjoint_step(fc_ctx *ctx, const double *e_n_dev, const double *mu_dev, const double *dt_dev,
-                          const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, int flags, void *stream);
+                          const double *lam_np1_dev, double *lam_n_dev, double *gbc_dev, double *dparam_dev,
+                          int flags, void *stream);
+
+/* Sensitivities to the initial data of a functional J whose gradient with respect to the
+ * initial state e_0 is lam0_dev ([4][P], e.g. lam_n of the adjoint step of step 0):
+ * drho_dev (nullable, P doubles) = dJ/drho_0 point by point at fixed velocity and
+ *   pressure, i.e. lam0 . d e_0 / d rho = lam_rho + lam_mx u + lam_my v + lam_E |u|^2 / 2
+ *   (0 on blanked points);
+ * dparam_dev (nullable, 2 doubles) accumulates dJ/d(M, alpha) through e_0 when e_0 is the
+ *   uniform free stream of fc_params.freestream on every non-blanked point (the sum over
+ *   those points of lam0 . d e_fs / d(M, alpha); FC_ERR_INVALID without a free stream).
+ * Both sums and all accumulations are in a fixed order: results are reproducible. */
+fc_status fc_initial_sensitivity(fc_ctx *ctx, const double *e0_dev, const double *lam0_dev, double *drho_dev,
+                                 double *dparam_dev, void *stream);
 
 /* Wall-pressure drag functional J = sum over the wall ring of the first OGRID
  * patch with a slip or adiabatic wall of p n_x r0 dtheta (periodic trapezoid of the integral of

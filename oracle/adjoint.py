@@ -337,3 +337,67 @@ def wall_drag_grad(sv, states):
             out[k][3, 0, :] = w * g1
             return out
     raise ValueError("no wall")
+
+
+# ---- sensitivities to the problem parameters (build addition; Sec. 7, eq. mach_flow_ic) ------
+
+def freestream_state(mach, alpha, rho, p, gamma):
+    """Conserved free stream (rho, M a cos alpha, M a sin alpha, p) with a = sqrt(gamma p / rho)."""
+    from . import euler
+    a = np.sqrt(gamma * p / rho)
+    return euler.cons_from_prim(rho, mach * a * np.cos(alpha), mach * a * np.sin(alpha), p, gamma)
+
+
+def freestream_jacobian(fs, gamma, h=1e-30):
+    """d e_fs / dM and d e_fs / dalpha at fixed density and pressure, by complex-step
+    differentiation of freestream_state (fs = primitive (rho, u, v, p))."""
+    rho, u, v, p = fs
+    a = np.sqrt(gamma * p / rho)
+    M, al = np.hypot(u, v) / a, np.arctan2(v, u)
+    dM = np.imag(freestream_state(M + 1j * h, al, rho, p, gamma)) / h
+    dA = np.imag(freestream_state(M, al + 1j * h, rho, p, gamma)) / h
+    return np.real(dM), np.real(dA)
+
+
+def dirichlet_param_sensitivity(sv, gbc, fs):
+    """(dJ/dM, dJ/dalpha) carried by the Dirichlet adjoint gbc of free-stream sides: the sum
+    over the Dirichlet points of sides whose state is fs of gbc . d e_fs / d(M, alpha)."""
+    dM, dA = freestream_jacobian(fs, sv.prm.gamma)
+    out = np.zeros(2)
+    for g, lam in zip(sv.geos, gbc):
+        mask = np.zeros((g.n2, g.n1), bool)
+        for s in range(4):
+            if g.desc.side[s] == W.DIRICHLET and tuple(g.desc.bc[s]) == tuple(fs):
+                if s == 0:
+                    mask[:, 0] = True
+                elif s == 1:
+                    mask[:, -1] = True
+                elif s == 2:
+                    mask[0, :] = True
+                else:
+                    mask[-1, :] = True
+        mask &= ~g.blank
+        out[0] += np.einsum("c,cji->", dM, np.where(mask, lam, 0.0))
+        out[1] += np.einsum("c,cji->", dA, np.where(mask, lam, 0.0))
+    return out
+
+
+def initial_sensitivity(sv, states, lams, fs):
+    """dJ/drho_0 at fixed velocity and pressure (complex step of the conserved state in rho)
+    per patch, and the (dJ/dM, dJ/dalpha) part through a uniform free-stream e_0: the sum
+    over non-blanked points of lam . d e_fs / d(M, alpha)."""
+    from . import euler
+    gam = sv.prm.gamma
+    h = 1e-30
+    drho = []
+    for g, e, lam in zip(sv.geos, states, lams):
+        rho, u, v, p = euler.primitives(e, gam)
+        de = np.imag(euler.cons_from_prim(rho + 1j * h, u, v, p, gam)) / h
+        drho.append(np.where(g.blank, 0.0, np.einsum("cji,cji->ji", lam, de)))
+    dM, dA = freestream_jacobian(fs, gam)
+    par = np.zeros(2)
+    for g, lam in zip(sv.geos, lams):
+        live = np.where(g.blank, 0.0, lam)
+        par[0] += np.einsum("c,cji->", dM, live)
+        par[1] += np.einsum("c,cji->", dA, live)
+    return drho, par

@@ -11,12 +11,9 @@ backwards through the segment.
 
 Orchestration only: every step and adjoint step runs in the CUDA library.
 """
-import math
-
 import torch
 
 from . import fcsdnn
-from . import workloads as W
 
 
 class Trajectory:
@@ -74,8 +71,10 @@ def replay(ctx, tr, e0, n0, n1):
     return out, mus
 
 
-def backward(ctx, tr, lam_N):
-    """lam_0 = (d e_N / d e_0)^T lam_N and the accumulated Dirichlet sensitivity gbc."""
+def backward(ctx, tr, lam_N, dparam=None):
+    """lam_0 = (d e_N / d e_0)^T lam_N and the accumulated Dirichlet sensitivity gbc; dparam
+    (2 device doubles, optional) accumulates dJ/d(Mach, angle) through the free-stream
+    Dirichlet states of every step."""
     nsteps = len(tr.dts)
     lam = lam_N.clone()
     nxt = torch.empty_like(lam)
@@ -86,7 +85,7 @@ def backward(ctx, tr, lam_N):
         n1 = starts[si + 1] if si + 1 < len(starts) else nsteps
         states, mus = replay(ctx, tr, tr.checkpoints[n0], n0, n1)
         for n in range(n1 - 1, n0 - 1, -1):
-            ctx.adjoint_step(states[n - n0], mus[n - n0], tr.dts[n], lam, nxt, gbc, tr.flags[n])
+            ctx.adjoint_step(states[n - n0], mus[n - n0], tr.dts[n], lam, nxt, gbc, tr.flags[n], dparam)
             lam, nxt = nxt, lam
         del states, mus
     return lam, gbc
@@ -115,32 +114,17 @@ def drag(ctx, e):
     return J, g
 
 
-def freestream_state_derivs(fs, gamma=W.GAMMA):
-    """d(conserved free stream)/d(Mach, angle, rho) for (rho, M cos a, M sin a, p) with sound speed
-    sqrt(gamma p / rho); returns 4-vectors (torch) for Mach and angle at fixed rho, p."""
-    rho, u, v, p = fs
-    M = math.hypot(u, v)
-    a = math.atan2(v, u)
-    c = math.sqrt(gamma * p / rho)
-    dM = torch.tensor([0.0, rho * c * math.cos(a), rho * c * math.sin(a), rho * c * c * M], dtype=torch.float64)
-    da = torch.tensor([0.0, -rho * c * M * math.sin(a), rho * c * M * math.cos(a), 0.0], dtype=torch.float64)
-    return dM, da
-
-
 def drag_gradients(w, ctx, e0, nsteps, K, filter=False):
     """J after nsteps from the free-stream state e0 and dJ/dMach, dJ/dangle, dJ/drho_0(x).
 
     Mach and angle enter through the initial state and the Dirichlet free-stream
-    states; rho_0 perturbs the initial density at fixed velocity and pressure."""
+    states (fc_adjoint_step and fc_initial_sensitivity accumulate both parts on the
+    device); rho_0 perturbs the initial density at fixed velocity and pressure."""
     eN, tr = forward(ctx, e0, nsteps, K, filter=filter)
     J, dJde = drag(ctx, eN)
-    lam0, gbc = backward(ctx, tr, dJde)
-    dM, da = freestream_state_derivs(w.freestream, w.params.gamma)
-    dev = e0.device
-    tot = (lam0 + gbc).sum(dim=1).cpu()
-    dJdM = float(tot @ dM)
-    dJda = float(tot @ da)
-    rho = e0[0]
-    u, v = e0[1] / rho, e0[2] / rho
-    dJdrho = lam0[0] + lam0[1] * u + lam0[2] * v + lam0[3] * 0.5 * (u * u + v * v)
+    dparam = torch.zeros(2, dtype=torch.float64, device=e0.device)
+    lam0, _ = backward(ctx, tr, dJde, dparam)
+    dJdrho = torch.empty(e0.shape[1], dtype=torch.float64, device=e0.device)
+    ctx.initial_sensitivity(e0, lam0, dJdrho, dparam)
+    dJdM, dJda = dparam.tolist()
     return J.item(), dJdM, dJda, dJdrho, tr

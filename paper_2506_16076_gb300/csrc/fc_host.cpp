@@ -116,6 +116,12 @@ struct fc_ctx {
   int nfcopy2 = 0;
   BcPt* d_bc = nullptr;
   int nbc = 0;
+  // free stream (fc_params.freestream) and the parameter adjoint of its Dirichlet points
+  bool has_fs = false;
+  FsJac fsj{};
+  double* d_bcacc = nullptr;  // [nbc][2] per-record sums of one adjoint step
+  double* d_part = nullptr;   // [SENS_BLOCKS][2] partial sums of fc_initial_sensitivity
+  double* cur_acc = nullptr;  // d_bcacc while an adjoint step accumulates dparam, else null
   WallPt* d_walls = nullptr;  // no-slip adiabatic wall points
   int nwalls = 0;
   Recv* d_recv = nullptr;
@@ -948,6 +954,20 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     return bad("SDNN weights missing or of the wrong size");
   if (prm->win_r < 1 || prm->win_r > 32 || prm->n_f < 1 || prm->n_v < 1 || prm->depth_cap < 2) return bad("bad params");
   c->sdnn.assign(prm->sdnn_w, prm->sdnn_w + prm->sdnn_len);
+  if (prm->freestream[0] > 0.0) {  // d e_fs / d(M, alpha) at fixed rho and p (eq. mach_flow_ic)
+    const double rho = prm->freestream[0], u = prm->freestream[1], v = prm->freestream[2];
+    const double pr = prm->freestream[3];
+    if (!(pr > 0.0) || !std::isfinite(u) || !std::isfinite(v)) return bad("bad free stream");
+    const double a = std::sqrt(prm->gamma * pr / rho), M = std::hypot(u, v) / a, al = std::atan2(v, u);
+    const double ca = std::cos(al), sa = std::sin(al);
+    const double dM[4] = {0.0, rho * a * ca, rho * a * sa, rho * a * a * M};
+    const double dA[4] = {0.0, -rho * a * M * sa, rho * a * M * ca, 0.0};
+    for (int k = 0; k < 4; ++k) {
+      c->fsj.dM[k] = dM[k];
+      c->fsj.dA[k] = dA[k];
+    }
+    c->has_fs = true;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   (void)st;
 
@@ -1135,14 +1155,19 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     for (int s = 0; s < 4; ++s) {
       if (h.d.side[s] != FC_SIDE_DIRICHLET) continue;
       side_pts(s, pts);
-      const double* q = h.d.bc[s];
+      // a bc of density 0 holds the free stream; a bc equal to it is a free-stream side too
+      bool fs = h.d.bc[s][0] == 0.0;
+      if (fs && !c->has_fs) return bad("a Dirichlet side holds the free stream (bc density 0) but none is set");
+      const double* q = fs ? prm->freestream : h.d.bc[s];
+      if (c->has_fs && !fs) fs = q[0] == prm->freestream[0] && q[1] == prm->freestream[1] &&
+                                 q[2] == prm->freestream[2] && q[3] == prm->freestream[3];
       const double rho = q[0], u = q[1], v = q[2], pr = q[3];
       const double val[4] = {rho, rho * u, rho * v, pr / (prm->gamma - 1.0) + 0.5 * rho * (u * u + v * v)};
       for (size_t k : pts) {
         if (h.blank[k]) continue;
         BcPt& b = m[k];
         b.idx = (int)(h.off + (long long)k);
-        b.mode |= 8;
+        b.mode = (b.mode & ~16) | 8 | (fs ? 16 : 0);
         for (int cc = 0; cc < 4; ++cc) b.val[cc] = val[cc];
       }
     }
@@ -1779,7 +1804,7 @@ void projectT(fc_ctx* c, double* lam, double* gbc, const double* u, cudaStream_t
   Prof pr(c, st, "bc_exchange_T");
   launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv, c->nrecv, lam, c->P, st);
   launch_bc_wall_T(c->d_walls, c->nwalls, u, lam, c->P, c->prm.gamma, st);
-  launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->P, st);
+  launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->cur_acc, c->fsj, c->P, st);
   c->launches += (c->ndon > 0) + (c->nrecv > 0) + (c->nwalls > 0) + (c->nbc > 0);
 }
 
@@ -2207,9 +2232,27 @@ fc_status fc_line_stats(fc_ctx* c, long long* lines_q1, long long* lines_q2, dou
 }
 
 fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const double* dt, const double* lam_np1,
-                          double* lam_n, double* gbc, int flags, void* stream) {
+                          double* lam_n, double* gbc, double* dparam, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
+  if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
   cudaStream_t st = (cudaStream_t)stream;
+  if (dparam && !c->d_bcacc && c->nbc > 0) {
+    if (!c->alloc(&c->d_bcacc, 2 * (size_t)c->nbc)) return FC_ERR_OOM;
+    if (cudaMemsetAsync(c->d_bcacc, 0, sizeof(double) * 2 * (size_t)c->nbc, st) != cudaSuccess)
+      return cuda_check(c, "fc_adjoint_step");
+  }
+  struct AccScope {  // the boundary transposes of this step feed dparam
+    fc_ctx* c;
+    AccScope(fc_ctx* c_, bool on) : c(c_) { c->cur_acc = on ? c->d_bcacc : nullptr; }
+    ~AccScope() { c->cur_acc = nullptr; }
+  } acc_scope(c, dparam != nullptr);
+  auto finish = [&]() {
+    if (dparam) {
+      launch_pair_reduce(c->d_bcacc, c->nbc, dparam, st);
+      c->launches += c->nbc > 0;
+    }
+    return cuda_check(c, "fc_adjoint_step");
+  };
   if (!c->adj_ready) {
     const size_t n4 = 4 * (size_t)c->P;
     bool ok = true;
@@ -2303,10 +2346,28 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
     filterT(c, A0, c->d_FX, c->d_FY, PSb, PSa, st);
     projectT(c, PSa, gbc, c->d_FX, st);
     cudaMemcpyAsync(lam_n, PSa, bytes4, cudaMemcpyDeviceToDevice, st);
-    return cuda_check(c, "fc_adjoint_step");
+    return finish();
   }
   cudaMemcpyAsync(lam_n, A0, bytes4, cudaMemcpyDeviceToDevice, st);
-  return cuda_check(c, "fc_adjoint_step");
+  return finish();
+}
+
+fc_status fc_initial_sensitivity(fc_ctx* c, const double* e0, const double* lam0, double* drho, double* dparam,
+                                 void* stream) {
+  if (!c || !e0 || !lam0) return FC_ERR_INVALID;
+  if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
+  if (!drho && !dparam) return FC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dparam && !c->d_part) {
+    if (!c->alloc(&c->d_part, 2 * (size_t)SENS_BLOCKS)) return FC_ERR_OOM;
+  }
+  launch_init_sens(c->d_info, c->P, e0, lam0, drho, dparam ? c->d_part : nullptr, c->fsj, st);
+  c->launches++;
+  if (dparam) {
+    launch_pair_reduce(c->d_part, SENS_BLOCKS, dparam, st);
+    c->launches++;
+  }
+  return cuda_check(c, "fc_initial_sensitivity");
 }
 
 }  // extern "C"

@@ -69,7 +69,8 @@ struct Recv {
 // Boundary overwrite of one point.
 struct BcPt {
   int idx;
-  int mode;         // bit0: zero rho u, bit1: zero rho v, bit2: remove normal (nx, ny), bit3: Dirichlet
+  int mode;         // bit0: zero rho u, bit1: zero rho v, bit2: remove normal (nx, ny), bit3: Dirichlet,
+                    // bit4: the Dirichlet state is the free stream (its adjoint feeds dJ/d(M, alpha))
   double nx, ny;
   double val[4];    // Dirichlet conserved state
 };
@@ -183,7 +184,20 @@ void launch_adj_fixup(const int* idx, int n, const double* R1, double* acc, long
                       cudaStream_t st);
 void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const double* dw, int nd, const Recv* r,
                        int nr, double* lam, long long P, cudaStream_t st);
-void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, cudaStream_t st);
+// d e_fs / dM and d e_fs / dalpha of the conserved free stream at fixed density and pressure
+struct FsJac {
+  double dM[4], dA[4];
+};
+// acc (nullable, [n][2]): per boundary record, += its Dirichlet adjoint . (dM, dA) on free-stream points
+void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, double* acc, FsJac fj, long long P,
+                 cudaStream_t st);
+// out[0..1] += the sums over i < n of acc[2 i], acc[2 i + 1] in a fixed order; acc is zeroed
+void launch_pair_reduce(double* acc, int n, double* out, cudaStream_t st);
+constexpr int SENS_BLOCKS = 1024;
+// drho (nullable) = lam0 . d e / d rho at fixed u, v, p; part (nullable, [SENS_BLOCKS][2]): per-block
+// sums of lam0 . (dM, dA) over non-blanked points
+void launch_init_sens(const uint32_t* info, long long P, const double* e0, const double* lam0, double* drho,
+                      double* part, FsJac fj, cudaStream_t st);
 void launch_drag(const int* wall, const double* w, const double* nx, int n, const double* e, long long P, double gam,
                  double* J, double* dJde, cudaStream_t st);
 void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);

@@ -1273,17 +1273,26 @@ __global__ void k_zero_points(const Recv* __restrict__ r, int n, double* __restr
 }
 // boundary transpose: Dirichlet points hand their adjoint to gbc and are zeroed; slip walls
 // zero (affine) or project out (curvilinear) the wall-normal momentum adjoint
+// (acc: the free-stream points' adjoint dotted with d e_fs / d(M, alpha), per record, in call order)
 __global__ void k_bc_T(const BcPt* __restrict__ bc, int n, double* __restrict__ lam, double* __restrict__ gbc,
-                       long long P) {
+                       double* __restrict__ acc, FsJac fj, long long P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const BcPt b = bc[i];
   const long long p = b.idx;
   if (b.mode & 8) {
+    double sm = 0.0, sa = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      if (gbc) gbc[p + c * P] += lam[p + c * P];
+      const double l = lam[p + c * P];
+      if (gbc) gbc[p + c * P] += l;
+      sm = fma(l, fj.dM[c], sm);
+      sa = fma(l, fj.dA[c], sa);
       lam[p + c * P] = 0.0;
+    }
+    if (acc && (b.mode & 16)) {
+      acc[2 * i] += sm;
+      acc[2 * i + 1] += sa;
     }
     return;
   }
@@ -1294,6 +1303,74 @@ __global__ void k_bc_T(const BcPt* __restrict__ bc, int n, double* __restrict__ 
     const double mn = mx * b.nx + my * b.ny;
     lam[p + P] = mx - mn * b.nx;
     lam[p + 2 * P] = my - mn * b.ny;
+  }
+}
+// out[0..1] += the pair sums of acc over n records, in a fixed order (one block of 512
+// threads: strided partial sums, then a fixed tree); acc is zeroed for the next step
+__global__ void __launch_bounds__(512) k_pair_reduce(double* __restrict__ acc, int n, double* __restrict__ out) {
+  __shared__ double s0[512], s1[512];
+  const int t = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = t; i < n; i += 512) {
+    a += acc[2 * i];
+    b += acc[2 * i + 1];
+    acc[2 * i] = 0.0;
+    acc[2 * i + 1] = 0.0;
+  }
+  s0[t] = a;
+  s1[t] = b;
+  __syncthreads();
+  for (int h = 256; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] += s0[0];
+    out[1] += s1[0];
+  }
+}
+// sensitivities to the initial data: drho = lam . d e / d rho at fixed u, v, p
+// (lam_rho + lam_mx u + lam_my v + lam_E |u|^2 / 2), and per-block sums of lam . (dM, dA)
+// over non-blanked points (grid-stride in a fixed order, fixed tree per block)
+__global__ void __launch_bounds__(256) k_init_sens(const uint32_t* __restrict__ info, long long P,
+                                                   const double* __restrict__ e, const double* __restrict__ lam,
+                                                   double* __restrict__ drho, double* __restrict__ part, FsJac fj) {
+  __shared__ double s0[256], s1[256];
+  const int t = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (long long p = (long long)blockIdx.x * 256 + t; p < P; p += (long long)gridDim.x * 256) {
+    const bool blank = (info[p] & PT_BLANK) != 0;
+    const double l0 = lam[p], l1 = lam[p + P], l2 = lam[p + 2 * P], l3 = lam[p + 3 * P];
+    if (drho) {
+      double r = 0.0;
+      if (!blank) {
+        const double rho = e[p], u = e[p + P] / rho, v = e[p + 2 * P] / rho;
+        r = l0 + l1 * u + l2 * v + l3 * (0.5 * (u * u + v * v));
+      }
+      drho[p] = r;
+    }
+    if (!blank) {
+      a += l0 * fj.dM[0] + l1 * fj.dM[1] + l2 * fj.dM[2] + l3 * fj.dM[3];
+      b += l0 * fj.dA[0] + l1 * fj.dA[1] + l2 * fj.dA[2] + l3 * fj.dA[3];
+    }
+  }
+  if (!part) return;
+  s0[t] = a;
+  s1[t] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      s0[t] += s0[t + h];
+      s1[t] += s1[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    part[2 * blockIdx.x] = s0[0];
+    part[2 * blockIdx.x + 1] = s1[0];
   }
 }
 // ---- transpose of the linearised per-step filter (Sec. 4.3.1) -----------------------------
@@ -1631,9 +1708,18 @@ void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const
   if (nd > 0) k_exchange_T<<<grid_pts(nd, 256), 256, 0, st>>>(dptr, dsrc, drecv, dw, nd, lam, P);
   if (nr > 0) k_zero_points<<<grid_pts(nr, 256), 256, 0, st>>>(r, nr, lam, P);
 }
-void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, long long P, cudaStream_t st) {
+void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, double* acc, FsJac fj, long long P,
+                 cudaStream_t st) {
   if (n <= 0) return;
-  k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, P);
+  k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, acc, fj, P);
+}
+void launch_pair_reduce(double* acc, int n, double* out, cudaStream_t st) {
+  if (n <= 0) return;
+  k_pair_reduce<<<1, 512, 0, st>>>(acc, n, out);
+}
+void launch_init_sens(const uint32_t* info, long long P, const double* e0, const double* lam0, double* drho,
+                      double* part, FsJac fj, cudaStream_t st) {
+  k_init_sens<<<SENS_BLOCKS, 256, 0, st>>>(info, P, e0, lam0, drho, part, fj);
 }
 // p[i] = a + b sin(w i): synthetic inputs of the autotuner
 void launch_deriv_lines(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* src, double* dst,

@@ -26,7 +26,8 @@ TUNE_PLANS, TUNE_WARPS = 1, 2
 
 # every symbol include/fcsdnn.h declares
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
-           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_autotune", "fc_adjoint_step", "fc_drag", "fc_sync_status",
+           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_autotune", "fc_adjoint_step",
+           "fc_initial_sensitivity", "fc_drag", "fc_sync_status",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
            "fc_pass_stats", "fc_line_stats", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
 
@@ -48,7 +49,7 @@ class ParamsC(C.Structure):
                 ("alpha_f", C.c_double), ("p_f", C.c_int), ("cfl", C.c_double), ("n_f", C.c_int),
                 ("n_v", C.c_int), ("win_r", C.c_int), ("loc", C.c_int), ("R", C.c_double * 4),
                 ("depth_cap", C.c_int), ("fc_tables", C.POINTER(C.c_double)), ("fc_tables_len", C.c_int),
-                ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int)]
+                ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int), ("freestream", C.c_double * 4)]
 
 
 def library_path():
@@ -77,7 +78,8 @@ def load():
         "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
         "fc_autotune": (C.c_int, [vp, ip, C.POINTER(C.c_double), vp]),
-        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
+        "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
+        "fc_initial_sensitivity": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "fc_drag": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_sync_status": (C.c_int, [vp, vp, ip, vp]),
         "fc_launch_count": (C.c_uint64, [vp]),
@@ -198,6 +200,8 @@ class Context:
         P.fc_tables_len = len(self._tab)
         P.sdnn_w = self._sd.ctypes.data_as(C.POINTER(C.c_float))
         P.sdnn_len = len(self._sd)
+        for m in range(4):
+            P.freestream[m] = workload.freestream[m]
         ctx = C.c_void_p()
         st = lib.fc_init_patches(C.byref(ctx), descs, n, C.byref(P), None)
         if st != FC_OK:
@@ -248,9 +252,17 @@ class Context:
         keys = ("lengths", "lengths_changed", "classes", "classes_changed", "ms_before", "ms_after")
         return {k: (int(v) if k[0] in "lc" else float(v)) for k, v in zip(keys, rep)}
 
-    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None, flags=0):
+    def adjoint_step(self, e_n, mu, dt, lam_np1, lam_n, gbc=None, flags=0, dparam=None):
+        """fc_adjoint_step; dparam (2 device doubles) accumulates dJ/d(Mach, angle) through the
+        free-stream Dirichlet states."""
         self._check(self.lib.fc_adjoint_step(self.ctx, _ptr(e_n), _ptr(mu), _ptr(dt), _ptr(lam_np1), _ptr(lam_n),
-                                             _ptr(gbc), int(flags), _stream()))
+                                             _ptr(gbc), _ptr(dparam), int(flags), _stream()))
+
+    def initial_sensitivity(self, e0, lam0, drho=None, dparam=None):
+        """fc_initial_sensitivity: dJ/drho_0 into drho (P doubles) and, for a uniform free-stream
+        e0, its dJ/d(Mach, angle) part accumulated into dparam (2 doubles)."""
+        self._check(self.lib.fc_initial_sensitivity(self.ctx, _ptr(e0), _ptr(lam0), _ptr(drho), _ptr(dparam),
+                                                    _stream()))
 
     def drag(self, e, J, dJde=None):
         self._check(self.lib.fc_drag(self.ctx, _ptr(e), _ptr(J), _ptr(dJde), _stream()))

@@ -52,3 +52,44 @@ def rel_err_normwise(gpu, orc):
     """max over points and components of |gpu - orc|, over max |orc| (all components)."""
     top = max(np.abs(o).max() for o in orc)
     return max(np.abs(g - o).max() for g, o in zip(gpu, orc)) / max(top, 1e-300)
+
+
+def fp64_floor(sv, fn):
+    """Error of an FP64 evaluation of the same operator (continued data rounded to
+    double, numpy's double-precision FFT, multipliers in double) against the long-double
+    oracle: the accuracy any FP64 implementation can be expected to reach. For lines of
+    ~1000-2000 points it exceeds 1e-11 (the derivative amplifies rounding at the highest
+    modes)."""
+    from oracle import fc
+
+    def deriv64(Fc, beta):
+        L = Fc.shape[-1]
+        fac = 2j * np.pi * fc.mode_numbers(L) / float(beta)
+        if L % 2 == 0:
+            fac[L // 2] = 0.0
+        return np.fft.ifft(fac * np.fft.fft(np.asarray(Fc, dtype=np.float64), axis=-1), axis=-1).real
+
+    def filter64(Fc, alpha, p):
+        L = Fc.shape[-1]
+        k = fc.mode_numbers(L)
+        if L % 2 == 0:
+            k[L // 2] = L / 2
+        return np.fft.ifft(fc.sigma(k, L, alpha, p) * np.fft.fft(np.asarray(Fc, dtype=np.float64), axis=-1),
+                           axis=-1).real
+
+    saved = fc.spectral_derivative, fc.spectral_filter
+    fc.spectral_derivative, fc.spectral_filter = deriv64, filter64
+    try:
+        return fn()
+    finally:
+        fc.spectral_derivative, fc.spectral_filter = saved
+
+
+def ulp_floor(fn, states, seed=0):
+    """Per-component sensitivity of an operator to one unit of FP64 rounding in its input:
+    rel_err of fn(states perturbed by a relative 2^-52 uniform noise) against fn(states).
+    Any FP64 implementation whose pointwise arithmetic rounds in another order differs from
+    the oracle by about this much."""
+    rng = np.random.default_rng(seed)
+    pert = [s * (1.0 + 2.0 ** -52 * rng.uniform(-1.0, 1.0, s.shape)) for s in states]
+    return rel_err(fn(pert), fn(states))

@@ -69,6 +69,59 @@ def test_adjoint_step_with_filter_parity(gpu_lib):
     assert max(errs) < 1e-11, errs
 
 
+@pytest.mark.parametrize("filt", [0, 1])
+def test_parameter_sensitivity_parity(gpu_lib, filt):
+    # dJ/d(Mach, angle) through the free-stream Dirichlet states of one adjoint step
+    # (accumulated over two calls) and through a uniform free-stream initial state, and
+    # dJ/drho_0, against the oracle adjoint
+    w = mach2_small()
+    ctx = gpu_lib.Context(w)
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=47, amp=0.1))
+    mu = [0.003 * (1 + np.cos(2 * g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    dt = 0.5 * sv.dt(st, mu)
+    rng = np.random.default_rng(8)
+    lam = [rng.normal(size=a.shape) for a in st]
+    ref_lam, ref_gbc = A.step_adjoint(sv, st, mu, dt, lam, filt=bool(filt))
+    ref_par = A.dirichlet_param_sensitivity(sv, ref_gbc, w.freestream)
+    dM, dA = A.freestream_jacobian(w.freestream, w.params.gamma)
+    size = [sum(np.einsum("c,cji->", np.abs(v), np.abs(g)) for g in ref_gbc) for v in (dM, dA)]
+    lam_n = torch.empty_like(to_dev(st))
+    dparam = torch.zeros(2, dtype=torch.float64, device="cuda")
+    dtt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ctx.adjoint_step(to_dev(st), to_dev_scalar_field(mu), dtt, to_dev(lam), lam_n, None,
+                         gpu_lib.STEP_FILTER if filt else 0, dparam)
+    torch.cuda.synchronize()
+    got = dparam.cpu().numpy()
+    for k in range(2):
+        assert abs(got[k] - 2 * ref_par[k]) <= 1e-11 * 2 * size[k], (k, got, ref_par, size)
+    # initial data: the oracle's adjoint state and a uniform free-stream e_0
+    e0 = W.initial_state(w)
+    drho_o, par0 = A.initial_sensitivity(sv, e0, ref_lam, w.freestream)
+    drho = torch.empty(ctx.P, dtype=torch.float64, device="cuda")
+    dp0 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ctx.initial_sensitivity(to_dev(e0), to_dev(ref_lam), drho, dp0)
+    torch.cuda.synchronize()
+    got_rho = from_dev(drho, w, 1)
+    scale = max(np.abs(d).max() for d in drho_o)
+    assert max(np.abs(a - b).max() for a, b in zip(got_rho, drho_o)) <= 1e-13 * scale
+    size0 = [sum(np.einsum("c,cji->", np.abs(v), np.abs(l)) for l in ref_lam) for v in (dM, dA)]
+    got0 = dp0.cpu().numpy()
+    for k in range(2):
+        assert abs(got0[k] - par0[k]) <= 1e-12 * size0[k], (k, got0, par0)
+
+
+def test_parameter_sensitivity_needs_a_free_stream(gpu_lib):
+    w = W.sod128(32)
+    w = dataclasses.replace(w, freestream=(0.0, 0.0, 0.0, 0.0))
+    ctx = gpu_lib.Context(w)
+    e = to_dev(W.initial_state(w))
+    lam = torch.zeros_like(e)
+    with pytest.raises(gpu_lib.FcError):
+        ctx.initial_sensitivity(e, lam, None, torch.zeros(2, dtype=torch.float64, device="cuda"))
+
+
 def test_drag_parity(gpu_lib):
     w = mach2_small()
     ctx = gpu_lib.Context(w)

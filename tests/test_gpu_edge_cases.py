@@ -10,42 +10,11 @@ import torch
 
 from oracle import solver as S
 from paper_2506_16076_gb300 import workloads as W
-from tests.gpu_helpers import from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
+from tests.gpu_helpers import fp64_floor, from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
 
 pytestmark = pytest.mark.gpu
 
 RHS_TOL = 1e-11
-
-
-def fp64_floor(sv, fn):
-    """Error of an FP64 evaluation of the same operator (continued data rounded to
-    double, numpy's double-precision FFT, multipliers in double) against the long-double
-    oracle: the accuracy any FP64 implementation can be expected to reach. For lines of
-    ~1000-2000 points it exceeds 1e-11 (the derivative amplifies rounding at the highest
-    modes)."""
-    from oracle import fc
-
-    def deriv64(Fc, beta):
-        L = Fc.shape[-1]
-        fac = 2j * np.pi * fc.mode_numbers(L) / float(beta)
-        if L % 2 == 0:
-            fac[L // 2] = 0.0
-        return np.fft.ifft(fac * np.fft.fft(np.asarray(Fc, dtype=np.float64), axis=-1), axis=-1).real
-
-    def filter64(Fc, alpha, p):
-        L = Fc.shape[-1]
-        k = fc.mode_numbers(L)
-        if L % 2 == 0:
-            k[L // 2] = L / 2
-        return np.fft.ifft(fc.sigma(k, L, alpha, p) * np.fft.fft(np.asarray(Fc, dtype=np.float64), axis=-1),
-                           axis=-1).real
-
-    saved = fc.spectral_derivative, fc.spectral_filter
-    fc.spectral_derivative, fc.spectral_filter = deriv64, filter64
-    try:
-        return fn()
-    finally:
-        fc.spectral_derivative, fc.spectral_filter = saved
 
 
 def _box(n1, n2, policy):

@@ -78,3 +78,15 @@ def test_grid_patch_without_metrics_needs_2d_points_per_line():
     p = dataclasses.replace(W.as_grid(_box(16, 16)), n1=8, n2=16, metrics=None)
     p = dataclasses.replace(p, x=p.x[:, :8].copy(), y=p.y[:, :8].copy())
     assert _status(_wl([p])) == fcsdnn.FC_ERR_INVALID
+
+
+def test_free_stream_side_without_a_free_stream_is_invalid():
+    # a Dirichlet side of bc density 0 holds fc_params.freestream, which must then be set
+    p = dataclasses.replace(_box(16, 16), bc=((0.0, 0.0, 0.0, 0.0),) * 4)
+    w = W.Workload("edge", [p], W.Params(), (0.0, 0.0, 0.0, 0.0), "freestream", 1)
+    assert _status(w) == fcsdnn.FC_ERR_INVALID
+
+
+def test_bad_free_stream_is_invalid():
+    w = W.Workload("edge", [_box(16, 16)], W.Params(), (1.4, 1.0, 0.0, -1.0), "freestream", 1)
+    assert _status(w) == fcsdnn.FC_ERR_INVALID

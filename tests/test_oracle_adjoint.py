@@ -172,3 +172,74 @@ def test_step_adjoint_with_filter_dot_product_on_grid_patches(make):
     lam_n, _ = A.step_adjoint(sv, st, mu, dt, lam, filt=True)
     lhs, rhs = dot(jv, lam), dot(v, lam_n)
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
+
+
+def _mach_workload(mach, alpha):
+    import dataclasses
+    w = W.small_multipatch()
+    fs = (1.4, mach * np.cos(alpha), mach * np.sin(alpha), 1.0)
+    return W.Workload("small_mach", [dataclasses.replace(p, bc=(fs,) * 4) for p in w.patches], w.params, fs,
+                      "freestream", 2)
+
+
+def test_freestream_jacobian_against_differences():
+    fs = (1.4, 2.0 * np.cos(0.05), 2.0 * np.sin(0.05), 1.0)  # a = 1: Mach 2 at 0.05 rad
+    a = np.sqrt(1.4 * 1.0 / 1.4)
+    e = A.freestream_state(2.0, 0.05, 1.4, 1.0, 1.4)
+    assert np.allclose(e, [1.4, 1.4 * fs[1], 1.4 * fs[2], 1.0 / 0.4 + 0.7 * 4.0], rtol=1e-15)
+    dM, dA = A.freestream_jacobian(fs, 1.4)
+    h = 1e-6
+    fdM = (A.freestream_state(2.0 + h, 0.05, 1.4, 1.0, 1.4) - A.freestream_state(2.0 - h, 0.05, 1.4, 1.0, 1.4)) / (2 * h)
+    fdA = (A.freestream_state(2.0, 0.05 + h, 1.4, 1.0, 1.4) - A.freestream_state(2.0, 0.05 - h, 1.4, 1.0, 1.4)) / (2 * h)
+    assert np.allclose(dM, fdM, rtol=1e-8, atol=1e-9) and np.allclose(dA, fdA, rtol=1e-8, atol=1e-9)
+    assert dM[0] == 0.0 and dA[0] == 0.0 and abs(dA[3]) < 1e-15 and a == 1.0  # energy: |u| fixed
+
+
+def test_parameter_gradients_central_differences():
+    # J = wall drag after 2 steps (mu = 0, dt frozen) from the uniform free stream of
+    # (Mach, alpha), with the Dirichlet sides holding the same free stream: dJ/dMach and
+    # dJ/dalpha from the adjoint (Dirichlet part + initial-state part) against central
+    # differences, and dJ/drho_0 at a few points against density perturbations
+    M0, a0, nsteps, h = 2.0, 0.04, 2, 1e-6
+    w = _mach_workload(M0, a0)
+    sv = S.Solver(w)
+    st0 = W.initial_state(w)
+    mu = [np.zeros((p.n2, p.n1)) for p in w.patches]
+    dt = 0.5 * sv.dt(sv.project([a.copy() for a in st0]), mu)
+
+    def J_of(mach, alpha, drho=None):
+        ww = _mach_workload(mach, alpha)
+        s2 = S.Solver(ww)
+        st = W.initial_state(ww)
+        if drho is not None:
+            from oracle import euler
+            out = []
+            for e, d in zip(st, drho):
+                rho, u, v, p = euler.primitives(e, 1.4)
+                out.append(euler.cons_from_prim(rho + d, u, v, p, 1.4))
+            st = out
+        for _ in range(nsteps):
+            st = A.step_forward(s2, st, mu, dt)[5]
+        return A.wall_drag(s2, st)
+
+    traj = [st0]
+    for _ in range(nsteps):
+        traj.append(A.step_forward(sv, traj[-1], mu, dt)[5])
+    lam = A.wall_drag_grad(sv, traj[-1])
+    par = np.zeros(2)
+    for n in range(nsteps - 1, -1, -1):
+        lam, gbc = A.step_adjoint(sv, traj[n], mu, dt, lam)
+        par += A.dirichlet_param_sensitivity(sv, gbc, w.freestream)
+    drho, par0 = A.initial_sensitivity(sv, st0, lam, w.freestream)
+    par += par0
+    fdM = (J_of(M0 + h, a0) - J_of(M0 - h, a0)) / (2 * h)
+    fdA = (J_of(M0, a0 + h) - J_of(M0, a0 - h)) / (2 * h)
+    assert abs(fdM - par[0]) <= 1e-6 * max(abs(par[0]), 1e-3), (fdM, par[0])
+    assert abs(fdA - par[1]) <= 1e-6 * max(abs(par[1]), 1e-3), (fdA, par[1])
+    scale = max(np.abs(d).max() for d in drho)
+    k = 0  # points on the O-grid next to the wall, where the drag is most sensitive
+    for (j, i) in ((1, 3), (2, 40), (4, 77)):
+        d = [np.zeros((p.n2, p.n1)) for p in w.patches]
+        d[k][j, i] = h
+        fd = (J_of(M0, a0, d) - J_of(M0, a0, [-x for x in d])) / (2 * h)
+        assert abs(fd - drho[k][j, i]) <= 1e-6 * scale, (j, i, fd, drho[k][j, i])
