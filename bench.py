@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-patches", type=int, default=1)
     ap.add_argument("--no-per-patch", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=40,
+                    help="steps of the adjoint cost measurement (one checkpoint segment by default)")
+    ap.add_argument("--adjoint-checkpoint", type=int, default=40, help="checkpoint interval K of that measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the cost model's FFT stage orders and the default warps per CTA (skip fc_autotune)")
     return ap.parse_args()
@@ -91,24 +94,71 @@ def oracle_bench(workload, steps, warmup, npatch, budget_s=None, max_points=None
     return active * 5 * done / el, desc, el, done
 
 
-def cpu_threads():
-    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+def oracle_single_patch(steps):
+    """Single-thread oracle rate on the 128 x 128 shock tube (all of it, no sampling)."""
+    from oracle import solver as S
+    from paper_2506_16076_gb300 import workloads as W
+    w = W.sod128()
+    sv = S.Solver(w)
+    st = S.smear_initial(sv, W.initial_state(w), 0.5)
+    st = sv.step(st, 0)
+    t0 = time.perf_counter()
+    for n in range(steps):
+        st = sv.step(st, 1 + n)
+    el = time.perf_counter() - t0
+    return 5 * w.total_points * steps / el, el
 
 
-def run_oracle_subprocess(workload, steps, warmup, npatch, budget_s, max_points=None):
-    """Run the oracle in a fresh process (spawned before any GPU work of that process)."""
+def oracle_adjoint_ratio():
+    """Oracle adjoint / forward cost on the small cylinder under a Mach-2 stream at 2 degrees
+    (the adjoint configuration's geometry and state at a size the oracle runs in seconds):
+    one forward step with the viscosity and dt frozen, against one adjoint step (its
+    forward recompute included) of the same step."""
+    import dataclasses
+    import math
+    from oracle import adjoint as A, solver as S
+    from paper_2506_16076_gb300 import workloads as W
+    w0 = W.small_multipatch(W.ADIABATIC)
+    a = math.radians(2.0)
+    fs = (1.4, 2.0 * math.cos(a), 2.0 * math.sin(a), 1.0)
+    w = W.Workload("small_m2", [dataclasses.replace(p, bc=(fs,) * 4) for p in w0.patches], w0.params, fs,
+                   "freestream", 1)
+    sv = S.Solver(w)
+    st = sv.project(W.initial_state(w))
+    mu = [0.0 * g.x for g in sv.geos]
+    dt = 0.5 * sv.dt(st, mu)
+    t0 = time.perf_counter()
+    out = A.step_forward(sv, st, mu, dt, filt=True)[0][5]
+    t1 = time.perf_counter()
+    A.step_adjoint(sv, st, mu, dt, [0.0 * x + 1.0 for x in out], filt=True)
+    t2 = time.perf_counter()
+    return (t2 - t1) / (t1 - t0), t1 - t0, t2 - t1, w.total_points
+
+
+def oracle_suite(workload, steps, warmup, npatch, budget_s, max_points=None, extras=True):
+    r = {"sample": oracle_bench(workload, steps, warmup, npatch, budget_s, max_points)}
+    if extras:
+        r["sod128"] = oracle_single_patch(2)
+        r["adjoint"] = oracle_adjoint_ratio()
+    return r
+
+
+def run_oracle_subprocess(workload, steps, warmup, npatch, budget_s, max_points=None, extras=False):
+    """Run the oracle in a fresh process (spawned before any GPU work of that process), on one
+    thread: the long-double numpy oracle does not parallelise, so the thread count is 1 and
+    the math libraries are held to it."""
     env = dict(os.environ)
-    n = str(os.cpu_count() or 1)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = n
+        env[k] = "1"
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_bench(%r, %d, %d, %d, %r, %r); print(json.dumps(r))" % (ROOT, workload, steps, warmup,
-                                                                                    npatch, budget_s, max_points))
+            "r = bench.oracle_suite(%r, %d, %d, %d, %r, %r, %r); print(json.dumps(r))"
+            % (ROOT, workload, steps, warmup, npatch, budget_s, max_points, extras))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    v, desc, el, done = json.loads(out.stdout.strip().splitlines()[-1])
-    return v, desc, el, done, int(n)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    v, desc, el, done = r["sample"]
+    return v, desc, el, done, 1, r
 
 
 # ---------------------------------------------------------------- clocks sampler
@@ -228,10 +278,19 @@ def main_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, desc, el, done, cores = run_oracle_subprocess(args.workload, 2, 0, args.sample_patches, 30.0)
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc + f", {el:.1f} s"}
+            v, desc, el, done, cores, r = run_oracle_subprocess(args.workload, 2, 0, args.sample_patches, 30.0,
+                                                                extras=True)
+            sod_v, sod_s = r["sod128"]
+            ratio, f_s, a_s, npts = r["adjoint"]
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc + f", {el:.1f} s",
+                   "threads": "1 (numpy long-double oracle; host cores: %d)" % (os.cpu_count() or 1),
+                   "sod128_single_thread": {"value": sod_v, "unit": UNIT, "seconds": round(sod_s, 2),
+                                            "sample": "128 x 128 shock tube, 2 full steps"},
+                   "adjoint_forward_ratio": {"value": ratio, "forward_s": round(f_s, 2), "adjoint_s": round(a_s, 2),
+                                             "sample": f"small O-grid + 2 x 2 cylinder, Mach 2 at 2 deg, {npts} "
+                                                       "points, one filtered step, adiabatic wall"}}
         except Exception as ex:  # reported, not fatal
-            cpu = {"value": None, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": f"failed: {ex}"}
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -304,19 +363,22 @@ def main_ours(args):
         skip = ctx.line_stats(reset=True)
         n0 += 2
 
-        # adjoint / forward cost: nadj steps recorded (mu, dt frozen for the adjoint, checkpoints
-        # every 2 steps), then the checkpointed reverse sweep (segment replays + adjoint steps)
+        # adjoint / forward cost at the adjoint configuration's checkpoint interval: nadj filtered
+        # steps recorded (mu, dt frozen for the adjoint, a checkpoint every K steps), then the
+        # checkpointed reverse sweep (segment replays + adjoint steps); the drag functional's
+        # parameter gradients are accumulated on the device as in a gradient run
         from paper_2506_16076_gb300 import adjoint as ADJ
-        nadj = max(2, min(args.steps, 4))
+        nadj, kadj = args.adjoint_steps, args.adjoint_checkpoint
         e_adj = e.clone()
         ev0.record(stream)
-        eN, tr = ADJ.forward(ctx, e_adj, nadj, 2)
+        eN, tr = ADJ.forward(ctx, e_adj, nadj, kadj, filter=True, first_filtered=0)
         ev1.record(stream)
         stream.synchronize()
         ms_fwd = ev0.elapsed_time(ev1)
         lam = torch.ones_like(eN)
+        dparam = torch.zeros(2, dtype=torch.float64, device=dev)
         ev0.record(stream)
-        lam0, _ = ADJ.backward(ctx, tr, lam)
+        lam0, _ = ADJ.backward(ctx, tr, lam, dparam)
         ev1.record(stream)
         stream.synchronize()
         ms_adj = ev0.elapsed_time(ev1)
@@ -324,21 +386,23 @@ def main_ours(args):
 
         # end to end through the public API with host buffers: every step uploads its input
         # state from pinned host memory and reads its result back to pinned host memory.
-        # Serial: H2D, step, D2H on one stream. Pipelined: the steps' inputs are independent
-        # host states, so step n+1's upload and step n's read-back run on two copy streams
-        # while the neighbouring steps compute (device-side staging copies keep the step's
-        # own buffers, and with them its captured graph, fixed).
+        # Chained (the headline): a time march through host memory, step n+1 starts from the
+        # host copy of step n's result (H2D, step, D2H in order on one stream). Pipelined
+        # (reported beside it): the steps' inputs are independent host states, so step n+1's
+        # upload and step n's read-back run on two copy streams while the neighbouring steps
+        # compute (device-side staging copies keep the step's own buffers, and with them its
+        # captured graph, fixed).
         host = e.cpu().pin_memory()
         host_out = torch.empty_like(host).pin_memory()
-        k_e2e = max(1, min(args.steps, 5))
+        k_e2e = max(1, min(args.steps, 10))
         ev0.record(stream)
         for n in range(n0, n0 + k_e2e):
             e.copy_(host, non_blocking=True)
             ctx.rk_step(e, dt, mu, GRAPH | FILTER)
-            host_out.copy_(e, non_blocking=True)
+            host.copy_(e, non_blocking=True)
         ev1.record(stream)
         stream.synchronize()
-        ms_e2e_serial = ev0.elapsed_time(ev1) / k_e2e
+        ms_e2e_chain = ev0.elapsed_time(ev1) / k_e2e
         n0 += k_e2e
 
         h2d, d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
@@ -381,8 +445,13 @@ def main_ours(args):
         n0 += k_pipe
 
     pu_step = 5 * ctx.active
-    ms, ms_e2e, value, e2e = combine_ranks(world, pu_step, args.steps, ms, ms_e2e, dev)
-    _, ms_e2e_serial, _, e2e_serial = combine_ranks(world, pu_step, args.steps, ms, ms_e2e_serial, dev)
+    ms, ms_e2e_pipe, value, e2e_pipe = combine_ranks(world, pu_step, args.steps, ms, ms_e2e, dev)
+    _, ms_e2e_chain, _, e2e_chain = combine_ranks(world, pu_step, args.steps, ms, ms_e2e_chain, dev)
+    probe = None
+    try:
+        probe = fcsdnn.probe_fp64()
+    except Exception:  # reported as missing, not fatal
+        pass
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -408,7 +477,8 @@ def main_ours(args):
         passes = 2 * (5 if dom.startswith("cart") else 1)  # profiled 2 steps
         avg_pass_s = tot_ms / 1e3 / passes
         sm_max = pk.get("sm_max_mhz", 2070.0)
-        fp64_peak = 152 * sm_max * 1e6 * 4 / 1e12  # 2 FP64 FMA lanes / clk / SM on GB300, TFLOP/s
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp64_peak = n_sm * sm_max * 1e6 * 4 / 1e12  # 2 FP64 FMA lanes / clk / SM on GB300, TFLOP/s
         ach = flops / avg_pass_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fp64_peak, 4), "traffic": measured_traffic(f"k_{dom}", args.workload),
@@ -419,7 +489,11 @@ def main_ours(args):
                 "pass_ms": round(avg_pass_s * 1e3, 3), "launches_per_pass": groups // passes,
                 "hbm_GBps": round(nbytes / avg_pass_s / 1e9, 1),
                 "hbm_frac_of_measured": round(nbytes / avg_pass_s / 1e9 / pk.get("hbm_gbs", 6787.9), 4),
-                "peak_note": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flops x max SM clock (probe measured 1.199 TF/s)"}
+                "peak_note": f"FP64 unit count: {n_sm} SMs (device query) x 2 FMA lanes/clk x 2 flops x max SM "
+                             f"clock {sm_max:.0f} MHz",
+                "probe_TFLOPs": None if probe is None else {"dfma": round(probe[0] / 1e3, 4),
+                                                            "dmma": round(probe[1] / 1e3, 4),
+                                                            "source": "fc_probe_fp64, this run"}}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -432,18 +506,20 @@ def main_ours(args):
         "per_patch": None if ms_pp is None else {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
                                                  "batched_speedup": ms_pp / (ms / args.steps)},
         "kernels_ms_per_step": {k: round(v[0] / 2, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
-        "adjoint": {"steps": nadj, "checkpoint_every": 2, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
-                    "adjoint_forward_ratio": ms_adj / ms_fwd,
-                    "note": "forward = steps with mu/dt recorded and checkpoints (no filter); adjoint = segment "
-                            "replays + fc_adjoint_step per step"},
+        "adjoint": {"steps": nadj, "checkpoint_every": kadj, "filter": True, "forward_ms": ms_fwd,
+                    "adjoint_ms": ms_adj, "adjoint_forward_ratio": ms_adj / ms_fwd,
+                    "note": "forward = filtered steps with mu/dt recorded and checkpoints; adjoint = segment "
+                            "replays + fc_adjoint_step per step with the parameter gradients accumulated"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P, "d2h_bytes_per_step": 32 * ctx.P,
-                "ms_per_step": ms_e2e, "steps": k_pipe,
-                "schedule": "pipelined: step n+1's upload and step n's read-back on two copy streams overlap "
-                            "the neighbouring steps' compute",
-                "serial": {"value": e2e_serial, "ms_per_step": ms_e2e_serial, "steps": k_e2e,
-                           "schedule": "H2D, step, D2H in order on one stream"}},
+        "e2e": {"value": e2e_chain, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P,
+                "d2h_bytes_per_step": 32 * ctx.P, "ms_per_step": ms_e2e_chain, "steps": k_e2e,
+                "schedule": "chained time march through pinned host memory: H2D of the host state, step, D2H of "
+                            "its result into the same host buffer, in order on one stream",
+                "independent_inputs_pipelined": {
+                    "value": e2e_pipe, "ms_per_step": ms_e2e_pipe, "steps": k_pipe,
+                    "schedule": "independent host inputs: step n+1's upload and step n's read-back on two copy "
+                                "streams overlap the neighbouring steps' compute"}},
         "gpu_launches": launches,
         "clocks": ck,
         "state_status": int(status),
@@ -461,8 +537,8 @@ def main_reference(args):
     # two minutes at the slowest host rate seen for this oracle (3.5e4 point-updates/s, the
     # Arm cores, where long double is quad precision in software)
     max_points = max(4096, int(120.0 * 3.5e4 / 5.0 / max(1, args.steps + args.warmup)))
-    v, desc, el, done, cores = run_oracle_subprocess(args.workload, args.steps, args.warmup, args.sample_patches,
-                                                     None, max_points)
+    v, desc, el, done, cores, _ = run_oracle_subprocess(args.workload, args.steps, args.warmup,
+                                                        args.sample_patches, None, max_points)
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
            "ms_per_step": el / max(done, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",

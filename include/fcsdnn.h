@@ -270,6 +270,57 @@ fc_status fc_line_stats(fc_ctx *ctx, long long *lines_q1, long long *lines_q2, d
 fc_status fc_pass_stats(const fc_ctx *ctx, const char *pass, double *flops, double *bytes, long long *lines,
                         long long *points);
 
+/* ---- Sharded execution over several ranks (one GPU per rank) ----
+ * The patches are the unit of work: a rank advances only the patches it owns, and the
+ * operator couples patches only through the inter-patch exchange of every projection
+ * (Sec. 3.4.1, Sec. 4.2), the cross-patch sums of the smoothing-blending operator of the
+ * viscosity (Sec. 5.2) and the global minimum of the time step (eq. CFL): the
+ * communication step of Algorithm 1. */
+
+/* Host-only (no device needed): owner[p] in [0, nranks) for every patch. Patches are
+ * ordered along the Morton (Z-order) curve of their centres, so that neighbours share a
+ * rank, and the order is cut into nranks contiguous runs of about equal active (non-
+ * blanked) point counts; a boundary then moves by single patches while that lowers the
+ * larger of the two loads it separates. Deterministic. FC_ERR_INVALID for nranks < 1. */
+fc_status fc_partition(const fc_patch_desc *patches, int npatch, int nranks, int *owner);
+
+/* What a rank exchanges with the others, through a callback the caller supplies (NCCL,
+ * gloo, or an in-process transport). op FC_COMM_EXCHANGE: send_dev holds, for every
+ * rank q = 0..nranks-1 in order, send_counts[q] doubles owed to q (0 for this rank);
+ * the callback fills recv_dev with recv_counts[q] doubles from every q, in the same
+ * order, before any later work on `stream` (an all-to-all with these splits). op
+ * FC_COMM_MIN: recv_dev[0] = the minimum over ranks of send_dev[0] (send_counts[0] = 1).
+ * Buffers are device memory owned by the context. Return 0 on success; any other value
+ * makes the calling function fail with FC_ERR_CUDA. */
+enum { FC_COMM_EXCHANGE = 0, FC_COMM_MIN = 1 };
+typedef int (*fc_comm_fn)(void *user, int op, const double *send_dev, const long long *send_counts, double *recv_dev,
+                          const long long *recv_counts, void *stream);
+
+/* Turn ctx (built on the whole workload, identically on every rank) into rank `rank` of
+ * nranks with the patch owners `owner` (host array of npatch entries): from then on
+ * fc_rk_step, fc_rhs, fc_project, fc_viscosity, fc_filter, fc_timestep and
+ * fc_sync_status work on the owned patches only. State buffers keep the full layout;
+ * entries of other ranks' patches are neither read nor written, except the fringe values
+ * and window sums that arrive through `comm`. Per projection every rank packs the
+ * interpolated fringe values (3 x 3 donor stencils) it owes to others, calls comm
+ * (FC_COMM_EXCHANGE) and scatters what it receives; per viscosity evaluation the same
+ * for the window sums of the cross-patch blending; per time step one FC_COMM_MIN. The
+ * results equal the unsharded context's bit for bit (the same kernels on the same
+ * values). Not available while sharded: FC_STEP_GRAPH and FC_STEP_PER_PATCH steps, the
+ * adjoint, fc_drag and fc_autotune (FC_ERR_UNIMPLEMENTED). Once per context. */
+fc_status fc_shard(fc_ctx *ctx, int nranks, int rank, const int *owner, fc_comm_fn comm, void *user);
+
+/* Doubles this rank sends to / receives from `peer` in one FC_COMM_EXCHANGE of a
+ * projection (which = 0) or of a viscosity evaluation (which = 1). */
+fc_status fc_shard_counts(const fc_ctx *ctx, int which, int peer, long long *send, long long *recv);
+
+/* FP64 throughput probes of the current device (instrumentation, no paper counterpart):
+ * *dfma_gflops = FP64 FMA rate of independent chains on every SM, *dmma_gflops = rate of the
+ * FP64 matrix instruction (m8n8k4), both in GFLOP/s (2 flops per multiply-add), timed with
+ * CUDA events on `stream` (synchronised) after one warm-up round; about 0.1 s. Allocates
+ * 8 bytes (stream-ordered) for a result sink. */
+fc_status fc_probe_fp64(double *dfma_gflops, double *dmma_gflops, void *stream);
+
 /* RHS of one stand-alone affine patch without any device allocation. For callers that
  * cannot allocate device memory: code under a host memory manager that owns all device
  * memory, plug-ins whose host forbids allocation, paths that must not allocate once set

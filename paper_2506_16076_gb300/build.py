@@ -18,7 +18,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 # extra nvcc flags for tuning builds, e.g. FCSDNN_NVCC_FLAGS="-DFC_LINE_MAXNREG=96"
 EXTRA = os.environ.get("FCSDNN_NVCC_FLAGS", "").split()
 STAMP = os.path.join(OUT, "flags.txt")
-SOURCES = ["fc_kernels.cu", "fc_host.cpp", "fc_noalloc.cu"]
+SOURCES = ["fc_kernels.cu", "fc_host.cpp", "fc_noalloc.cu", "fc_probe.cu"]
 
 
 def nvcc():

@@ -116,6 +116,33 @@ struct fc_ctx {
   int nfcopy2 = 0;
   BcPt* d_bc = nullptr;
   int nbc = 0;
+  // host copies of the point lists (restricted to the owned patches by fc_shard)
+  std::vector<Recv> h_recv;
+  std::vector<BcPt> h_bc;
+  std::vector<WallPt> h_walls;
+  std::vector<int> h_fix, h_fcopy1, h_fcopy2, h_cdst, h_cptr, h_csrc;
+  std::vector<GFix> h_gfix;
+  // sharded execution (fc_shard): this rank of nranks, patch owners, the caller's transport
+  int nranks = 1, rank = 0;
+  std::vector<int> owner;
+  fc_comm_fn comm = nullptr;
+  void* comm_user = nullptr;
+  uint8_t* d_owned = nullptr;
+  struct XPlan {  // one kind of exchange: records per peer, in peer order
+    std::vector<long long> scount, rcount;  // doubles per peer
+    int nsend = 0, nrecv = 0;
+    double* d_sbuf = nullptr;
+    double* d_rbuf = nullptr;
+  };
+  XPlan xp_fringe, xp_visc;
+  Recv* d_xsend = nullptr;   // fringe records this rank interpolates for others
+  int* d_xrecv = nullptr;    // receivers of this rank filled from others
+  int* d_vsend = nullptr;    // window-sum entries this rank sends
+  int* d_vrecv = nullptr;    // window-sum entries this rank receives
+  bool sharded() const { return nranks > 1; }
+  bool comm_failed = false;
+  double* d_dtmin = nullptr;
+
   // free stream (fc_params.freestream) and the parameter adjoint of its Dirichlet points
   bool has_fs = false;
   FsJac fsj{};
@@ -256,6 +283,15 @@ fc_status cuda_check(fc_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, FC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
   return FC_OK;
+}
+
+// cuda_check, plus the status of the communication callbacks of a sharded call
+fc_status comm_check(fc_ctx* c, const char* where) {
+  if (c->comm_failed) {
+    c->comm_failed = false;
+    return fail(c, FC_ERR_CUDA, std::string(where) + ": the communication callback failed");
+  }
+  return cuda_check(c, where);
 }
 
 // ---------------------------------------------------------------- geometry (Sec. 3)
@@ -1477,6 +1513,16 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_wall, wall) && c->upload(&c->d_wallw, wallw) && c->upload(&c->d_wallc, wallc);
   c->plans_h = B.plans;
   c->plan_cands = B.cands;
+  c->h_recv = recv;
+  c->h_bc = bcs;
+  c->h_walls = walls;
+  c->h_fix = fix;
+  c->h_gfix = gfix;
+  c->h_fcopy1 = fc1;
+  c->h_fcopy2 = fc2;
+  c->h_cdst = cdst;
+  c->h_cptr = cptr;
+  c->h_csrc = csrc;
   c->ndon = (int)dsrc.size();
   c->nwall = (int)wall.size();
   c->nfix = (int)fix.size();
@@ -1707,6 +1753,14 @@ void project(fc_ctx* c, double* e, cudaStream_t st) {
     launch_exchange(c->d_recv, c->nrecv, e, c->P, st);
     c->launches++;
   }
+  if (c->sharded()) {  // fringe values interpolated on the donors' ranks
+    fc_ctx::XPlan& x = c->xp_fringe;
+    launch_xpack(c->d_xsend, x.nsend, e, c->P, x.d_sbuf, st);
+    if (c->comm(c->comm_user, FC_COMM_EXCHANGE, x.d_sbuf, x.scount.data(), x.d_rbuf, x.rcount.data(), st) != 0)
+      c->comm_failed = true;
+    launch_xunpack(c->d_xrecv, x.nrecv, x.d_rbuf, e, c->P, st);
+    c->launches += (x.nsend > 0) + (x.nrecv > 0);
+  }
 }
 
 void viscosity(fc_ctx* c, const double* e, double* mu, int32_t* tau, cudaStream_t st) {
@@ -1716,6 +1770,14 @@ void viscosity(fc_ctx* c, const double* e, double* mu, int32_t* tau, cudaStream_
   launch_visc_muhat(T, c->d_phi, c->d_S, c->d_sdnn, c->d_R, c->d_muhat, tau, st);
   launch_window_rows(T, c->d_muhat, c->d_tmp, c->d_wtab, c->prm.win_r, st);
   launch_window_cols(T, c->d_tmp, c->d_num, c->d_wtab, c->prm.win_r, st);
+  if (c->sharded()) {  // window sums of other ranks' patches that the cross-patch sums read
+    fc_ctx::XPlan& x = c->xp_visc;
+    launch_gather(c->d_vsend, x.nsend, c->d_num, x.d_sbuf, st);
+    if (c->comm(c->comm_user, FC_COMM_EXCHANGE, x.d_sbuf, x.scount.data(), x.d_rbuf, x.rcount.data(), st) != 0)
+      c->comm_failed = true;
+    launch_scatter(c->d_vrecv, x.nrecv, x.d_rbuf, c->d_num, st);
+    c->launches += (x.nsend > 0) + (x.nrecv > 0);
+  }
   launch_mu_final(T, c->d_num, c->d_den, c->d_cross_dst, c->d_cross_ptr, c->d_cross_src, c->ncross, mu, st);
   c->launches += 5 + (c->ncross > 0);
 }
@@ -1761,6 +1823,11 @@ void timestep(fc_ctx* c, const double* e, const double* mu, double* dt, cudaStre
   Prof pr(c, st, "timestep");
   launch_dt(c->T, e, mu, c->d_pmax, c->prm.cfl, dt, st);
   c->launches += 2;
+  if (c->sharded()) {
+    const long long one[1] = {1};
+    if (c->comm(c->comm_user, FC_COMM_MIN, dt, one, c->d_dtmin, one, st) != 0) c->comm_failed = true;
+    cudaMemcpyAsync(dt, c->d_dtmin, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
 }
 
 void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream_t st) {
@@ -1859,13 +1926,13 @@ fc_status fc_rhs(fc_ctx* c, const double* e, double* rhs, const double* mu, void
   s.rhs_only = 1;
   s.dt = c->d_dt;
   stage(c, s, mu, false, st);
-  return cuda_check(c, "fc_rhs");
+  return comm_check(c, "fc_rhs");
 }
 
 fc_status fc_viscosity(fc_ctx* c, const double* e, double* mu, int32_t* tau, void* stream) {
   if (!c || !e || !mu) return FC_ERR_INVALID;
   viscosity(c, e, mu, tau, (cudaStream_t)stream);
-  return cuda_check(c, "fc_viscosity");
+  return comm_check(c, "fc_viscosity");
 }
 
 fc_status fc_filter(fc_ctx* c, double* e, void* stream) {
@@ -1877,13 +1944,13 @@ fc_status fc_filter(fc_ctx* c, double* e, void* stream) {
 fc_status fc_project(fc_ctx* c, double* e, void* stream) {
   if (!c || !e) return FC_ERR_INVALID;
   project(c, e, (cudaStream_t)stream);
-  return cuda_check(c, "fc_project");
+  return comm_check(c, "fc_project");
 }
 
 fc_status fc_timestep(fc_ctx* c, const double* e, const double* mu, double* dt, void* stream) {
   if (!c || !e || !mu || !dt) return FC_ERR_INVALID;
   timestep(c, e, mu, dt, (cudaStream_t)stream);
-  return cuda_check(c, "fc_timestep");
+  return comm_check(c, "fc_timestep");
 }
 
 fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, void* stream) {
@@ -1893,9 +1960,11 @@ fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, vo
   cudaStream_t st = (cudaStream_t)stream;
   if (!mu) mu = c->d_mu;
   if (!dt) dt = c->d_dt;
+  if (c->sharded() && (flags & (FC_STEP_GRAPH | FC_STEP_PER_PATCH)))
+    return fail(c, FC_ERR_UNIMPLEMENTED, "graph and per-patch steps are not available while sharded");
   if (!(flags & FC_STEP_GRAPH)) {
     rk_body(c, e, dt, mu, flags, st);
-    return cuda_check(c, "fc_rk_step");
+    return comm_check(c, "fc_rk_step");
   }
   // graph mode: capture the step once per (buffers, flags, stream) and replay it
   const int gf = flags & ~FC_STEP_GRAPH;
@@ -1934,6 +2003,7 @@ fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, vo
 
 fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
   if (!c) return FC_ERR_INVALID;
+  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "fc_autotune is not available while sharded");
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "fc_autotune");
   double rep[6] = {0, 0, 0, 0, 0, 0};
@@ -2077,6 +2147,7 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
 
 fc_status fc_drag(fc_ctx* c, const double* e, double* J, double* dJde, void* stream) {
   if (!c || !e || !J) return FC_ERR_INVALID;
+  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "fc_drag is not available while sharded");
   if (c->nwall == 0) return fail(c, FC_ERR_INVALID, "no curvilinear patch with a slip wall");
   cudaStream_t st = (cudaStream_t)stream;
   if (dJde) cudaMemsetAsync(dJde, 0, sizeof(double) * 4 * (size_t)c->P, st);
@@ -2234,6 +2305,7 @@ fc_status fc_line_stats(fc_ctx* c, long long* lines_q1, long long* lines_q2, dou
 fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const double* dt, const double* lam_np1,
                           double* lam_n, double* gbc, double* dparam, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
+  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "the adjoint is not available while sharded");
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
   cudaStream_t st = (cudaStream_t)stream;
   if (dparam && !c->d_bcacc && c->nbc > 0) {
@@ -2352,9 +2424,246 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
   return finish();
 }
 
+// ---------------------------------------------------------------- sharded execution
+
+fc_status fc_partition(const fc_patch_desc* patches, int npatch, int nranks, int* owner) {
+  if (!patches || npatch <= 0 || nranks < 1 || !owner) return FC_ERR_INVALID;
+  // active points and centre of every patch
+  std::vector<double> w(npatch), cx(npatch), cy(npatch);
+  for (int p = 0; p < npatch; ++p) {
+    const fc_patch_desc& d = patches[p];
+    if (d.n1 < 1 || d.n2 < 1) return FC_ERR_INVALID;
+    const long long N = (long long)d.n1 * d.n2;
+    double sx = 0.0, sy = 0.0;
+    long long act = 0;
+    const bool hole = d.kind != FC_PATCH_OGRID && d.hole[2] > 0.0;
+    for (int j = 0; j < d.n2; ++j)
+      for (int i = 0; i < d.n1; ++i) {
+        double x, y;
+        if (d.kind == FC_PATCH_AFFINE) {
+          x = d.geom[0] + (d.geom[1] - d.geom[0]) * (d.n1 > 1 ? (double)i / (d.n1 - 1) : 0.0);
+          y = d.geom[2] + (d.geom[3] - d.geom[2]) * (d.n2 > 1 ? (double)j / (d.n2 - 1) : 0.0);
+        } else if (d.kind == FC_PATCH_OGRID) {
+          const double r = d.geom[2] + (d.geom[3] - d.geom[2]) * (d.n2 > 1 ? (double)j / (d.n2 - 1) : 0.0);
+          const double th = 2.0 * PI * i / d.n1;
+          x = d.geom[0] + r * std::cos(th);
+          y = d.geom[1] + r * std::sin(th);
+        } else {
+          if (!d.x || !d.y) return FC_ERR_INVALID;
+          x = d.x[(size_t)j * d.n1 + i];
+          y = d.y[(size_t)j * d.n1 + i];
+        }
+        sx += x;
+        sy += y;
+        if (!hole || std::hypot(x - d.hole[0], y - d.hole[1]) >= d.hole[2]) ++act;
+      }
+    w[p] = (double)act;
+    cx[p] = sx / (double)N;
+    cy[p] = sy / (double)N;
+  }
+  // Morton order of the centres on a 2^16 x 2^16 grid over their bounding box
+  double x0 = *std::min_element(cx.begin(), cx.end()), x1 = *std::max_element(cx.begin(), cx.end());
+  double y0 = *std::min_element(cy.begin(), cy.end()), y1 = *std::max_element(cy.begin(), cy.end());
+  const double span = std::max(std::max(x1 - x0, y1 - y0), 1e-300);
+  auto spread = [](uint64_t v) {  // bits of v at even positions
+    v &= 0xFFFF;
+    v = (v | (v << 8)) & 0x00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0Full;
+    v = (v | (v << 2)) & 0x33333333ull;
+    v = (v | (v << 1)) & 0x55555555ull;
+    return v;
+  };
+  std::vector<std::pair<uint64_t, int>> key(npatch);
+  for (int p = 0; p < npatch; ++p) {
+    const uint64_t qx = (uint64_t)std::min(65535.0, std::floor((cx[p] - x0) / span * 65535.0));
+    const uint64_t qy = (uint64_t)std::min(65535.0, std::floor((cy[p] - y0) / span * 65535.0));
+    key[p] = {spread(qx) | (spread(qy) << 1), p};
+  }
+  std::sort(key.begin(), key.end());
+  // contiguous runs of about total / nranks along the curve
+  double total = 0.0;
+  for (double v : w) total += v;
+  std::vector<int> first(nranks + 1, npatch);  // run r = order positions [first[r], first[r+1])
+  first[0] = 0;
+  {
+    double cum = 0.0;
+    int r = 1;
+    for (int k = 0; k < npatch && r < nranks; ++k) {
+      const double wk = w[key[k].second];
+      while (r < nranks && cum + 0.5 * wk > total * r / nranks) first[r++] = k;
+      cum += wk;
+    }
+    while (r < nranks) first[r++] = npatch;
+  }
+  // move boundaries by single patches while that lowers the larger neighbouring load
+  std::vector<double> pre(npatch + 1, 0.0);  // weights along the curve, prefix sums
+  for (int k = 0; k < npatch; ++k) pre[k + 1] = pre[k] + w[key[k].second];
+  auto load = [&](int r) { return pre[first[r + 1]] - pre[first[r]]; };
+  for (int pass = 0; pass < 4 * npatch; ++pass) {
+    bool moved = false;
+    for (int r = 1; r < nranks; ++r) {
+      const double a = load(r - 1), b = load(r);
+      const double cur = std::max(a, b);
+      if (first[r] > first[r - 1] + 1) {  // left run gives its last patch
+        const double v = w[key[first[r] - 1].second];
+        if (std::max(a - v, b + v) < cur) {
+          --first[r];
+          moved = true;
+          continue;
+        }
+      }
+      if (first[r] + 1 < first[r + 1]) {  // right run gives its first patch
+        const double v = w[key[first[r]].second];
+        if (std::max(a + v, b - v) < cur) {
+          ++first[r];
+          moved = true;
+        }
+      }
+    }
+    if (!moved) break;
+  }
+  for (int r = 0; r < nranks; ++r)
+    for (int k = first[r]; k < first[r + 1]; ++k) owner[key[k].second] = r;
+  return FC_OK;
+}
+
+fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn comm, void* user) {
+  if (!c || nranks < 1 || rank < 0 || rank >= nranks || !owner) return FC_ERR_INVALID;
+  if (c->nranks != 1 || !c->owner.empty()) return fail(c, FC_ERR_INVALID, "fc_shard: the context is sharded already");
+  if (nranks > 1 && !comm) return fail(c, FC_ERR_INVALID, "fc_shard: a communication callback is needed");
+  const int npatch = (int)c->hp.size();
+  for (int p = 0; p < npatch; ++p)
+    if (owner[p] < 0 || owner[p] >= nranks) return fail(c, FC_ERR_INVALID, "fc_shard: owner out of range");
+  std::vector<int> own(owner, owner + npatch);
+  std::vector<long long> offs(npatch + 1, 0);
+  for (int p = 0; p < npatch; ++p) offs[p + 1] = c->hp[p].off + (long long)c->hp[p].n1 * c->hp[p].n2;
+  auto patch_of = [&](long long idx) {
+    return (int)(std::upper_bound(offs.begin() + 1, offs.end(), idx) - offs.begin() - 1);
+  };
+  auto mine = [&](long long idx) { return own[patch_of(idx)] == rank; };
+  bool ok = true;
+  // line queues of the owned patches
+  for (fc_ctx::Queue* q : {&c->q_cart1, &c->q_cart2, &c->q_gen1, &c->q_gen2, &c->q_filt1, &c->q_filt2}) {
+    std::vector<Job> jobs;
+    for (const Job& J : q->h)
+      if (own[J.patch] == rank) jobs.push_back(J);
+    make_queue(c, *q, jobs, c->plans_h, npatch, ok);
+  }
+  // point lists of the owned patches
+  std::vector<BcPt> bc;
+  for (const BcPt& b : c->h_bc)
+    if (mine(b.idx)) bc.push_back(b);
+  std::vector<WallPt> walls;
+  for (const WallPt& wp : c->h_walls)
+    if (mine(wp.idx)) walls.push_back(wp);
+  std::vector<int> fix, fc1, fc2;
+  for (int k : c->h_fix)
+    if (mine(k)) fix.push_back(k);
+  for (int k : c->h_fcopy1)
+    if (mine(k)) fc1.push_back(k);
+  for (int k : c->h_fcopy2)
+    if (mine(k)) fc2.push_back(k);
+  std::vector<GFix> gfix;
+  for (const GFix& g : c->h_gfix)
+    if (mine(g.p)) gfix.push_back(g);
+  // fringe receivers: local ones, and per peer the ones this rank interpolates for it and
+  // the ones it receives, both in the order of the unsharded receiver list
+  std::vector<Recv> loc, xsend;
+  std::vector<int> xrecv;
+  c->xp_fringe.scount.assign(nranks, 0);
+  c->xp_fringe.rcount.assign(nranks, 0);
+  for (int q = 0; q < nranks; ++q)
+    for (const Recv& r : c->h_recv) {
+      const int pd = own[patch_of(r.dst)], ps = own[patch_of(r.src[0])];
+      if (q == rank && pd == rank && ps == rank) loc.push_back(r);
+      if (q != rank && ps == rank && pd == q) {
+        xsend.push_back(r);
+        c->xp_fringe.scount[q] += 4;
+      }
+      if (q != rank && pd == rank && ps == q) {
+        xrecv.push_back(r.dst);
+        c->xp_fringe.rcount[q] += 4;
+      }
+    }
+  // cross-patch blending: the owned points' entries, and the window sums of other ranks'
+  // points they read (per peer, sorted, unique); the same rule on the peers' entries gives
+  // what this rank sends
+  std::vector<int> cdst, cptr{0}, csrc;
+  std::vector<std::vector<int>> need(nranks), give(nranks);
+  for (size_t i = 0; i < c->h_cdst.size(); ++i) {
+    const int pd = own[patch_of(c->h_cdst[i])];
+    if (pd == rank) cdst.push_back(c->h_cdst[i]);
+    for (int k = c->h_cptr[i]; k < c->h_cptr[i + 1]; ++k) {
+      const int src = c->h_csrc[k], ps = own[patch_of(src)];
+      if (pd == rank) csrc.push_back(src);
+      if (pd == rank && ps != rank) need[ps].push_back(src);
+      if (pd != rank && ps == rank) give[pd].push_back(src);
+    }
+    if (pd == rank) cptr.push_back((int)csrc.size());
+  }
+  std::vector<int> vsend, vrecv;
+  c->xp_visc.scount.assign(nranks, 0);
+  c->xp_visc.rcount.assign(nranks, 0);
+  for (int q = 0; q < nranks; ++q) {
+    for (std::vector<int>* v : {&need[q], &give[q]}) {
+      std::sort(v->begin(), v->end());
+      v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    vrecv.insert(vrecv.end(), need[q].begin(), need[q].end());
+    vsend.insert(vsend.end(), give[q].begin(), give[q].end());
+    c->xp_visc.rcount[q] = (long long)need[q].size();
+    c->xp_visc.scount[q] = (long long)give[q].size();
+  }
+  std::vector<uint8_t> mask(npatch);
+  for (int p = 0; p < npatch; ++p) mask[p] = own[p] == rank ? 1 : 0;
+  ok = ok && c->upload(&c->d_bc, bc) && c->upload(&c->d_walls, walls) && c->upload(&c->d_fix, fix) &&
+       c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) && c->upload(&c->d_gfix, gfix) &&
+       c->upload(&c->d_recv, loc) && c->upload(&c->d_xsend, xsend) && c->upload(&c->d_xrecv, xrecv) &&
+       c->upload(&c->d_cross_dst, cdst) && c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) &&
+       c->upload(&c->d_vsend, vsend) && c->upload(&c->d_vrecv, vrecv) && c->upload(&c->d_owned, mask) &&
+       c->alloc(&c->xp_fringe.d_sbuf, 4 * xsend.size()) && c->alloc(&c->xp_fringe.d_rbuf, 4 * xrecv.size()) &&
+       c->alloc(&c->xp_visc.d_sbuf, vsend.size()) && c->alloc(&c->xp_visc.d_rbuf, vrecv.size()) &&
+       c->alloc(&c->d_dtmin, 1);
+  if (!ok) return fail(c, FC_ERR_OOM, c->err);
+  c->nbc = (int)bc.size();
+  c->nwalls = (int)walls.size();
+  c->nfix = (int)fix.size();
+  c->nfcopy1 = (int)fc1.size();
+  c->nfcopy2 = (int)fc2.size();
+  c->ngfix = (int)gfix.size();
+  c->nrecv = (int)loc.size();
+  c->ncross = (int)cdst.size();
+  c->xp_fringe.nsend = (int)xsend.size();
+  c->xp_fringe.nrecv = (int)xrecv.size();
+  c->xp_visc.nsend = (int)vsend.size();
+  c->xp_visc.nrecv = (int)vrecv.size();
+  c->owner = own;
+  c->nranks = nranks;
+  c->rank = rank;
+  c->comm = comm;
+  c->comm_user = user;
+  c->T.owned = c->d_owned;
+  if (c->gexec) {  // a captured step of the whole workload is stale now
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->gflags = -1;
+  return cuda_check(c, "fc_shard");
+}
+
+fc_status fc_shard_counts(const fc_ctx* c, int which, int peer, long long* send, long long* recv) {
+  if (!c || !send || !recv || which < 0 || which > 1 || peer < 0 || peer >= c->nranks || c->owner.empty())
+    return FC_ERR_INVALID;
+  const fc_ctx::XPlan& x = which == 0 ? c->xp_fringe : c->xp_visc;
+  *send = x.scount[peer];
+  *recv = x.rcount[peer];
+  return FC_OK;
+}
+
 fc_status fc_initial_sensitivity(fc_ctx* c, const double* e0, const double* lam0, double* drho, double* dparam,
                                  void* stream) {
   if (!c || !e0 || !lam0) return FC_ERR_INVALID;
+  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "the adjoint is not available while sharded");
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
   if (!drho && !dparam) return FC_OK;
   cudaStream_t st = (cudaStream_t)stream;

@@ -127,6 +127,8 @@ struct DevTables {
   // warps per CTA of the line kernels per length class ceil(log2 Lmax) (0: the default);
   // set by the autotuner
   int lw[NCLASS];
+  // sharded execution: 1 for the patches this rank owns (null: all patches are owned)
+  const uint8_t* owned;
 };
 
 // ---- launch wrappers (fc_kernels.cu) ----
@@ -158,6 +160,13 @@ void launch_filterT_copy2(const DevTables& T, const int* idx, int n, const doubl
 void launch_filterT_copy1(const DevTables& T, const int* idx, int n, const double* MF, const double* e, double* out,
                           cudaStream_t st);
 void launch_exchange(const Recv* r, int n, double* e, long long P, cudaStream_t st);
+// sharded exchange: buf[4 i + c] = the interpolated value of record i (as launch_exchange
+// would write it), and its scatter e[dst[i] + c P] = buf[4 i + c]
+void launch_xpack(const Recv* r, int n, const double* e, long long P, double* buf, cudaStream_t st);
+void launch_xunpack(const int* dst, int n, const double* buf, double* e, long long P, cudaStream_t st);
+// buf[i] = src[idx[i]] and dst[idx[i]] = buf[i]
+void launch_gather(const int* idx, int n, const double* src, double* buf, cudaStream_t st);
+void launch_scatter(const int* idx, int n, const double* buf, double* dst, cudaStream_t st);
 void launch_filter_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* F, cudaStream_t st);
 void launch_filter_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* F, double* e, cudaStream_t st);
 void launch_filter_copy_q1(const DevTables& T, const int* idx, int n, const double* e, double* F, cudaStream_t st);

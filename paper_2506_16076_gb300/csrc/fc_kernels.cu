@@ -208,56 +208,165 @@ __global__ void LINE_KERNEL_BOUNDS k_cart_q1(DevTables T, const Job* __restrict_
 
 // ---------------------------------------------------------------- affine patches, q2 lines
 // d/dy of e -> H_y -> R2 = d/dy H_y; L = -(R1 + R2) (0 on PT_NODIFF points); stage combination.
+__device__ __forceinline__ void q2_line(const DevTables& T, const Job& J, const Plan& P, double2* A, int Lmax,
+                                        const double* __restrict__ mu, const double* __restrict__ R1,
+                                        const StageCoef& sc, int lane) {
+  const long long cs = T.P;
+  const double* e = sc.Ucur;
+  const int L = P.L;
+  const bool visc = line_viscous(J, mu, lane);
+  if (visc) {
+    load4(A, L, J, e, cs, lane);
+    deriv2(A, Lmax, J, P, T, lane);
+  } else {
+    count_skip(T, 1, J, L, lane);
+  }
+  for (int t = lane; t < J.n; t += 32) {
+    const long long p = J.base + (long long)t * J.stride;
+    double f[4];
+    flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+    if (visc) {
+      const double m = mu[p];
+      const double2 g0 = A[t], g1 = A[L + t];
+      A[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
+      A[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
+    } else {
+      A[t] = cpx(f[0], f[1]);
+      A[L + t] = cpx(f[2], f[3]);
+    }
+  }
+  deriv2(A, Lmax, J, P, T, lane);
+  for (int t = lane; t < J.n; t += 32) {
+    const long long p = J.base + (long long)t * J.stride;
+    const double2 a = A[t], b = A[L + t];
+    double L4[4];
+    if (T.info[p] & PT_NODIFF) {
+      L4[0] = L4[1] = L4[2] = L4[3] = 0.0;
+    } else {
+      L4[0] = -(R1[p] + a.x);
+      L4[1] = -(R1[p + cs] + a.y);
+      L4[2] = -(R1[p + 2 * cs] + b.x);
+      L4[3] = -(R1[p + 3 * cs] + b.y);
+    }
+    stage_write(sc, p, cs, L4);
+  }
+}
+
+// one warp per line
 __global__ void LINE_KERNEL_BOUNDS k_cart_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                         const double* __restrict__ mu, const double* __restrict__ R1,
                                                         StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double2* A = sm + warp * (2 * Lmax + CONT_TMP);
-  const long long cs = T.P;
-  const double* e = sc.Ucur;
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
-    const Plan P = T.plans[J.plan];
-    const int L = P.L;
-    const bool visc = line_viscous(J, mu, lane);
-    if (visc) {
-      load4(A, L, J, e, cs, lane);
-      deriv2(A, Lmax, J, P, T, lane);
-    } else {
-      count_skip(T, 1, J, L, lane);
-    }
-    for (int t = lane; t < J.n; t += 32) {
-      const long long p = J.base + (long long)t * J.stride;
-      double f[4];
-      flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
-      if (visc) {
-        const double m = mu[p];
-        const double2 g0 = A[t], g1 = A[L + t];
-        A[t] = cpx(fma(-m, g0.x, f[0]), fma(-m, g0.y, f[1]));
-        A[L + t] = cpx(fma(-m, g1.x, f[2]), fma(-m, g1.y, f[3]));
-      } else {
-        A[t] = cpx(f[0], f[1]);
-        A[L + t] = cpx(f[2], f[3]);
-      }
-    }
-    deriv2(A, Lmax, J, P, T, lane);
-    double2* Z = A;
-    for (int t = lane; t < J.n; t += 32) {
-      const long long p = J.base + (long long)t * J.stride;
-      const double2 a = Z[t], b = Z[L + t];
-      double L4[4];
-      if (T.info[p] & PT_NODIFF) {
-        L4[0] = L4[1] = L4[2] = L4[3] = 0.0;
-      } else {
-        L4[0] = -(R1[p] + a.x);
-        L4[1] = -(R1[p + cs] + a.y);
-        L4[2] = -(R1[p + 2 * cs] + b.x);
-        L4[3] = -(R1[p + 3 * cs] + b.y);
-      }
-      stage_write(sc, p, cs, L4);
-    }
+    q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, sc, lane);
     FC_SYNC();
+  }
+}
+
+// ---------------------------------------------------------------- affine patches, q2 lines, tiled
+// A CTA of TW warps takes TW consecutive jobs of the queue. When they are TW adjacent
+// columns of one patch with the same segment (the common case), the CTA reads their
+// points row by row (TW consecutive doubles per row: whole 32-byte sectors) into the
+// warps' line buffers, and writes the stage result the same way; in between each warp
+// transforms its own column. Other job sets run one line per warp as in k_cart_q2.
+constexpr int TW = 4;
+__host__ __device__ inline int tiled_stride(int Lmax) {
+  const int b = 2 * Lmax + CONT_TMP;
+  return b + ((2 - b % 8) + 8) % 8;  // = 2 (mod 8): conflict-free row-by-column smem access
+}
+__global__ void __launch_bounds__(TW * 32) k_cart_q2_tiled(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                            int Lmax, const double* __restrict__ mu,
+                                                            const double* __restrict__ R1, StageCoef sc) {
+  extern __shared__ double2 sm[];
+  __shared__ int vflag[TW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sA = tiled_stride(Lmax);
+  double2* A = sm + warp * sA;
+  const long long cs = T.P;
+  const double* e = sc.Ucur;
+  for (int g0 = blockIdx.x * TW; g0 < njobs; g0 += gridDim.x * TW) {
+    const int nc = min(TW, njobs - g0);
+    const Job J0 = jobs[g0];
+    bool tiled = true;
+    for (int c = 1; c < nc; ++c) {
+      const Job Jc = jobs[g0 + c];
+      tiled = tiled && Jc.base == J0.base + c && Jc.stride == J0.stride && Jc.n == J0.n && Jc.plan == J0.plan &&
+              Jc.fcm == J0.fcm && Jc.C == J0.C && Jc.scale == J0.scale;
+    }
+    if (!tiled) {
+      if (warp < nc) {
+        const Job J = jobs[g0 + warp];
+        q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, sc, lane);
+      }
+      __syncthreads();
+      continue;
+    }
+    const Plan P = T.plans[J0.plan];
+    const int L = P.L, n = J0.n, st = J0.stride;
+    if (threadIdx.x < TW) vflag[threadIdx.x] = 0;
+    __syncthreads();
+    // rows of the TW columns: e into the line buffers, viscosity vote per column
+    for (int k = threadIdx.x; k < n * TW; k += TW * 32) {
+      const int r = k / TW, c = k % TW;
+      if (c < nc) {
+        const long long p = J0.base + c + (long long)r * st;
+        if (mu[p] != 0.0) vflag[c] = 1;
+        double2* Ac = sm + c * sA;
+        Ac[r] = cpx(e[p], e[p + cs]);
+        Ac[L + r] = cpx(e[p + 2 * cs], e[p + 3 * cs]);
+      }
+    }
+    __syncthreads();
+    if (warp < nc) {
+      const Job J = jobs[g0 + warp];
+      const bool visc = vflag[warp] != 0;
+      if (visc) {  // gradient of e first; the flux then reads e again from memory
+        deriv2(A, Lmax, J, P, T, lane);
+        for (int t = lane; t < n; t += 32) {
+          const long long p = J.base + (long long)t * st;
+          double f[4];
+          flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+          const double m = mu[p];
+          const double2 g0v = A[t], g1v = A[L + t];
+          A[t] = cpx(fma(-m, g0v.x, f[0]), fma(-m, g0v.y, f[1]));
+          A[L + t] = cpx(fma(-m, g1v.x, f[2]), fma(-m, g1v.y, f[3]));
+        }
+      } else {
+        count_skip(T, 1, J, L, lane);
+        for (int t = lane; t < n; t += 32) {
+          const double2 a = A[t], b = A[L + t];
+          double f[4];
+          flux_y(a.x, a.y, b.x, b.y, T.gamma, f);
+          A[t] = cpx(f[0], f[1]);
+          A[L + t] = cpx(f[2], f[3]);
+        }
+      }
+      deriv2(A, Lmax, J, P, T, lane);
+    }
+    __syncthreads();
+    // rows again: stage combination of the TW columns
+    for (int k = threadIdx.x; k < n * TW; k += TW * 32) {
+      const int r = k / TW, c = k % TW;
+      if (c < nc) {
+        const long long p = J0.base + c + (long long)r * st;
+        const double2* Ac = sm + c * sA;
+        const double2 a = Ac[r], b = Ac[L + r];
+        double L4[4];
+        if (T.info[p] & PT_NODIFF) {
+          L4[0] = L4[1] = L4[2] = L4[3] = 0.0;
+        } else {
+          L4[0] = -(R1[p] + a.x);
+          L4[1] = -(R1[p + cs] + a.y);
+          L4[2] = -(R1[p + 2 * cs] + b.x);
+          L4[3] = -(R1[p + 3 * cs] + b.y);
+        }
+        stage_write(sc, p, cs, L4);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -532,23 +641,48 @@ __global__ void k_bc_wall(const WallPt* __restrict__ wp, int n, double* __restri
 
 // ---------------------------------------------------------------- inter-patch exchange (Sec. 3.4.1)
 // iterated 1-D quadratic interpolation: along q1 in each of the 3 stencil rows, then along q2
+// iterated quadratic interpolation of one component from the 3 x 3 donor stencil
+__device__ __forceinline__ double interp33(const Recv& R, const double* __restrict__ ec) {
+  double acc = 0.0;
+#pragma unroll
+  for (int m2 = 0; m2 < 3; ++m2) {
+    double row = 0.0;
+#pragma unroll
+    for (int m1 = 0; m1 < 3; ++m1) row = fma(R.w1[m1], ec[R.src[3 * m2 + m1]], row);
+    acc = fma(R.w2[m2], row, acc);
+  }
+  return acc;
+}
 __global__ void k_exchange(const Recv* __restrict__ r, int n, double* __restrict__ e, long long P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Recv R = r[i];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const double* ec = e + c * P;
-    double acc = 0.0;
+  for (int c = 0; c < 4; ++c) e[R.dst + c * P] = interp33(R, e + c * P);
+}
+// sharded exchange: the values a rank owes to others, and their scatter on arrival
+__global__ void k_xpack(const Recv* __restrict__ r, int n, const double* __restrict__ e, long long P,
+                        double* __restrict__ buf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Recv R = r[i];
 #pragma unroll
-    for (int m2 = 0; m2 < 3; ++m2) {
-      double row = 0.0;
+  for (int c = 0; c < 4; ++c) buf[4 * (long long)i + c] = interp33(R, e + c * P);
+}
+__global__ void k_xunpack(const int* __restrict__ dst, int n, const double* __restrict__ buf, double* __restrict__ e,
+                          long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
 #pragma unroll
-      for (int m1 = 0; m1 < 3; ++m1) row = fma(R.w1[m1], ec[R.src[3 * m2 + m1]], row);
-      acc = fma(R.w2[m2], row, acc);
-    }
-    e[R.dst + c * P] = acc;
-  }
+  for (int c = 0; c < 4; ++c) e[dst[i] + c * P] = buf[4 * (long long)i + c];
+}
+__global__ void k_gather(const int* __restrict__ idx, int n, const double* __restrict__ src, double* __restrict__ buf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) buf[i] = src[idx[i]];
+}
+__global__ void k_scatter(const int* __restrict__ idx, int n, const double* __restrict__ buf, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] = buf[i];
 }
 
 // ---------------------------------------------------------------- per-step filter (Sec. 4.3.1)
@@ -847,7 +981,7 @@ __global__ void k_dt_reduce(DevTables T, const double* __restrict__ e, const dou
   unsigned long long bs = 0, bm = 0;
   if (p < T.P) {
     const uint32_t f = T.info[p];
-    if (!(f & PT_BLANK)) {
+    if (!(f & PT_BLANK) && (!T.owned || T.owned[pt_patch(f)])) {
       patch = pt_patch(f);
       const long long cs = T.P;
       const double gam = T.gamma;
@@ -885,6 +1019,7 @@ __global__ void k_dt_final(DevTables T, const unsigned long long* __restrict__ p
   __shared__ double red[256];
   double best = INFINITY;
   for (int q = threadIdx.x; q < T.npatch; q += blockDim.x) {
+    if (T.owned && !T.owned[q]) continue;
     const double Sm = __longlong_as_double((long long)pmax[2 * q]);
     const double Mm = __longlong_as_double((long long)pmax[2 * q + 1]);
     const double h = T.patches[q].htil;
@@ -908,6 +1043,7 @@ __global__ void k_check_state(DevTables T, const double* __restrict__ e, int* fl
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= T.P) return;
   if (T.info[p] & PT_BLANK) return;
+  if (T.owned && !T.owned[pt_patch(T.info[p])]) return;
   const long long cs = T.P;
   const double r = e[p], mx = e[p + cs], my = e[p + 2 * cs], E = e[p + 3 * cs];
   const Prim q = primitives(r, mx, my, E, T.gamma);
@@ -1561,7 +1697,11 @@ void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, co
 void launch_cart_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* mu, const double* R1,
                     const StageCoef& sc, cudaStream_t st) {
   if (njobs <= 0) return;
-  k_cart_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, mu, R1, sc);
+  const size_t smem = (size_t)TW * tiled_stride(Lmax) * sizeof(double2);
+  if (smem <= SMEM_CAP)
+    k_cart_q2_tiled<<<(njobs + TW - 1) / TW, TW * 32, smem, st>>>(T, jobs, njobs, Lmax, mu, R1, sc);
+  else
+    k_cart_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, mu, R1, sc);
 }
 void launch_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* G,
                   cudaStream_t st) {
@@ -1713,6 +1853,18 @@ void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, double* acc, F
   if (n <= 0) return;
   k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, acc, fj, P);
 }
+void launch_xpack(const Recv* r, int n, const double* e, long long P, double* buf, cudaStream_t st) {
+  if (n > 0) k_xpack<<<grid_pts(n, 128), 128, 0, st>>>(r, n, e, P, buf);
+}
+void launch_xunpack(const int* dst, int n, const double* buf, double* e, long long P, cudaStream_t st) {
+  if (n > 0) k_xunpack<<<grid_pts(n, 256), 256, 0, st>>>(dst, n, buf, e, P);
+}
+void launch_gather(const int* idx, int n, const double* src, double* buf, cudaStream_t st) {
+  if (n > 0) k_gather<<<grid_pts(n, 256), 256, 0, st>>>(idx, n, src, buf);
+}
+void launch_scatter(const int* idx, int n, const double* buf, double* dst, cudaStream_t st) {
+  if (n > 0) k_scatter<<<grid_pts(n, 256), 256, 0, st>>>(idx, n, buf, dst);
+}
 void launch_pair_reduce(double* acc, int n, double* out, cudaStream_t st) {
   if (n <= 0) return;
   k_pair_reduce<<<1, 512, 0, st>>>(acc, n, out);
@@ -1754,6 +1906,7 @@ void set_kernel_attributes() {
   const int cap = (int)SMEM_CAP;
   cudaFuncSetAttribute(k_cart_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_cart_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_cart_q2_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_gen_A, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_gen_B, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);

@@ -27,9 +27,9 @@ TUNE_PLANS, TUNE_WARPS = 1, 2
 # every symbol include/fcsdnn.h declares
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
            "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_autotune", "fc_adjoint_step",
-           "fc_initial_sensitivity", "fc_drag", "fc_sync_status",
+           "fc_initial_sensitivity", "fc_drag", "fc_sync_status", "fc_partition", "fc_shard", "fc_shard_counts",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
-           "fc_pass_stats", "fc_line_stats", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
+           "fc_pass_stats", "fc_line_stats", "fc_probe_fp64", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
 
 
 class FcError(RuntimeError):
@@ -50,6 +50,12 @@ class ParamsC(C.Structure):
                 ("n_v", C.c_int), ("win_r", C.c_int), ("loc", C.c_int), ("R", C.c_double * 4),
                 ("depth_cap", C.c_int), ("fc_tables", C.POINTER(C.c_double)), ("fc_tables_len", C.c_int),
                 ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int), ("freestream", C.c_double * 4)]
+
+
+# fc_comm_fn: (user, op, send_dev, send_counts, recv_dev, recv_counts, stream) -> int
+COMM_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_longlong), C.c_void_p,
+                      C.POINTER(C.c_longlong), C.c_void_p)
+COMM_EXCHANGE, COMM_MIN = 0, 1
 
 
 def library_path():
@@ -91,6 +97,10 @@ def load():
                                     C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fc_line_stats": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), ip]),
+        "fc_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
+        "fc_partition": (C.c_int, [C.POINTER(PatchDescC), ip, ip, C.POINTER(C.c_int)]),
+        "fc_shard": (C.c_int, [vp, ip, ip, C.POINTER(C.c_int), COMM_FN, vp]),
+        "fc_shard_counts": (C.c_int, [vp, ip, ip, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "fc_rhs_patch_noalloc": (C.c_int, [vp, vp, vp, ip, ip, C.POINTER(C.c_double), ip, ip,
                                            C.POINTER(C.c_double), ip, C.c_double, vp]),
         "fc_last_error": (C.c_char_p, [vp]),
@@ -152,6 +162,63 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def pack_descs(workload):
+    """fc_patch_desc array of a workload, and the host arrays it points to (keep them alive)."""
+    n = len(workload.patches)
+    descs = (PatchDescC * n)()
+    keep = []
+    for k, p in enumerate(workload.patches):
+        dsc = descs[k]
+        dsc.kind, dsc.n1, dsc.n2 = p.kind, p.n1, p.n2
+        for m in range(4):
+            dsc.geom[m] = p.geom[m]
+            dsc.side[m] = p.side[m]
+            for q in range(4):
+                dsc.bc[m][q] = p.bc[m][q]
+        for m in range(3):
+            dsc.hole[m] = p.hole[m]
+        if p.kind == W.GRID:  # host arrays, kept alive until fc_init_patches returns
+            ptrs = []
+            for a, m in ((p.x, 1), (p.y, 1), (p.metrics, 4)):
+                if a is None:  # null: metrics are then computed by the library; x, y are required
+                    ptrs.append(None)
+                    continue
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                if a.size != m * p.n1 * p.n2:
+                    raise ValueError(f"GRID patch {k}: array of {a.size} values, expected {m * p.n1 * p.n2}")
+                keep.append(a)
+                ptrs.append(a.ctypes.data_as(C.POINTER(C.c_double)))
+            dsc.x, dsc.y, dsc.metrics = ptrs
+    return descs, keep
+
+
+def partition(workload, nranks):
+    """fc_partition: owner rank of every patch (Morton order, balanced active points)."""
+    lib = load()
+    descs, keep = pack_descs(workload)
+    n = len(workload.patches)
+    owner = (C.c_int * n)()
+    st = lib.fc_partition(descs, n, int(nranks), owner)
+    if st != FC_OK:
+        raise FcError(st, "fc_partition failed")
+    return list(owner)
+
+
+class _DevArray:
+    """A device buffer owned by the library, seen by torch without a copy."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr or 0), False),
+                                         "version": 3}
+
+
+def _dev_tensor(ptr, n):
+    import torch
+    if n == 0:
+        return torch.empty(0, dtype=torch.float64, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n), device="cuda")
+
+
 class Context:
     """One fc_ctx: geometry and device workspaces of a workload.
 
@@ -165,30 +232,7 @@ class Context:
         self.w = workload
         prm = workload.params
         n = len(workload.patches)
-        descs = (PatchDescC * n)()
-        keep = []
-        for k, p in enumerate(workload.patches):
-            dsc = descs[k]
-            dsc.kind, dsc.n1, dsc.n2 = p.kind, p.n1, p.n2
-            for m in range(4):
-                dsc.geom[m] = p.geom[m]
-                dsc.side[m] = p.side[m]
-                for q in range(4):
-                    dsc.bc[m][q] = p.bc[m][q]
-            for m in range(3):
-                dsc.hole[m] = p.hole[m]
-            if p.kind == W.GRID:  # host arrays, kept alive until fc_init_patches returns
-                ptrs = []
-                for a, m in ((p.x, 1), (p.y, 1), (p.metrics, 4)):
-                    if a is None:  # null: metrics are then computed by the library; x, y are required
-                        ptrs.append(None)
-                        continue
-                    a = np.ascontiguousarray(a, dtype=np.float64)
-                    if a.size != m * p.n1 * p.n2:
-                        raise ValueError(f"GRID patch {k}: array of {a.size} values, expected {m * p.n1 * p.n2}")
-                    keep.append(a)
-                    ptrs.append(a.ctypes.data_as(C.POINTER(C.c_double)))
-                dsc.x, dsc.y, dsc.metrics = ptrs
+        descs, keep = pack_descs(workload)
         self._tab = fc_table_blob(prm.d)
         self._sd = sdnn_blob()
         P = ParamsC()
@@ -264,6 +308,41 @@ class Context:
         self._check(self.lib.fc_initial_sensitivity(self.ctx, _ptr(e0), _ptr(lam0), _ptr(drho), _ptr(dparam),
                                                     _stream()))
 
+    def shard(self, nranks, rank, owner, comm):
+        """fc_shard: this context becomes rank `rank` of nranks with the patch owners `owner`;
+        comm has exchange(send, send_counts, recv, recv_counts) (an all-to-all of device
+        tensors with those splits) and allmin(send, recv), both ordered on the current stream."""
+        import torch
+        nr = int(nranks)
+
+        def cb(user, op, send, scounts, recv, rcounts, stream):
+            try:
+                s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(s):
+                    if op == COMM_MIN:
+                        comm.allmin(_dev_tensor(send, 1), _dev_tensor(recv, 1))
+                    else:
+                        sc = [int(scounts[q]) for q in range(nr)]
+                        rc = [int(rcounts[q]) for q in range(nr)]
+                        comm.exchange(_dev_tensor(send, sum(sc)), sc, _dev_tensor(recv, sum(rc)), rc)
+                return 0
+            except Exception:  # reported to the library as a failed exchange
+                import traceback
+                traceback.print_exc()
+                return 1
+
+        self._comm_cb = COMM_FN(cb)  # kept alive with the context
+        self._comm = comm
+        own = (C.c_int * len(self.w.patches))(*owner)
+        self._check(self.lib.fc_shard(self.ctx, nr, int(rank), own, self._comm_cb, None))
+        self.nranks, self.rank, self.owner = nr, int(rank), list(owner)
+
+    def shard_counts(self, which, peer):
+        """(doubles sent to, received from) peer per exchange: which 0 fringe, 1 viscosity."""
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.fc_shard_counts(self.ctx, int(which), int(peer), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def drag(self, e, J, dJde=None):
         self._check(self.lib.fc_drag(self.ctx, _ptr(e), _ptr(J), _ptr(dJde), _stream()))
 
@@ -303,6 +382,16 @@ class Context:
 
     def profile_reset(self):
         self._check(self.lib.fc_profile_reset(self.ctx))
+
+
+def probe_fp64():
+    """(DFMA, DMMA) FP64 rates of the current device in GFLOP/s (fc_probe_fp64)."""
+    lib = load()
+    a, b = C.c_double(), C.c_double()
+    st = lib.fc_probe_fp64(C.byref(a), C.byref(b), _stream())
+    if st != FC_OK:
+        raise FcError(st, "fc_probe_fp64 failed")
+    return a.value, b.value
 
 
 def _check_field(t, name, numel):

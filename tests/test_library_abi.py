@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "fcsdnn.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declarations_match_binding():
