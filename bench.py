@@ -13,8 +13,10 @@ keeps the fastest (--no-autotune: the cost model's choices).
 
   python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
 
-N > 1 (torchrun): independent replicas, one per GPU (the operator's only
-cross-patch coupling is the per-stage exchange, which is not sharded).
+N > 1 (torchrun): independent replicas, one per GPU (weak scaling); with --shard the
+ranks share one workload instead (fc_partition + fc_shard: each rank advances its own
+patches, the fringe values, window sums and the time step's minimum go through NCCL;
+strong scaling, no graph, no per-patch or adjoint measurement).
 --impl reference: the CPU oracle on the host cores, on a bounded sample of the
 same workload, same metric and unit.
 """
@@ -45,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-patches", type=int, default=1)
     ap.add_argument("--no-per-patch", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split the workload's patches over the ranks (fc_shard) instead of replicas")
     ap.add_argument("--adjoint-steps", type=int, default=40,
                     help="steps of the adjoint cost measurement (one checkpoint segment by default)")
     ap.add_argument("--adjoint-checkpoint", type=int, default=40, help="checkpoint interval K of that measurement")
@@ -210,16 +214,18 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- ranks
-def combine_ranks(world, pu_step, steps, ms, ms_e2e, device):
-    """Whole-job rates of independent replicas: times are the maximum over ranks, work is the
-    sum over ranks (weak scaling). Returns (ms, ms_e2e, value, e2e)."""
+def combine_ranks(world, pu_step, steps, ms, ms_e2e, device, shared=False):
+    """Whole-job rates: times are the maximum over ranks; work is the sum over ranks for
+    independent replicas (weak scaling), or the one shared workload's when the ranks split
+    it (shared, strong scaling). Returns (ms, ms_e2e, value, e2e)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms, ms_e2e = t[0].item(), t[1].item()
-    return ms, ms_e2e, world * pu_step * steps / (ms / 1e3), world * pu_step / (ms_e2e / 1e3)
+    copies = 1 if shared else world
+    return ms, ms_e2e, copies * pu_step * steps / (ms / 1e3), copies * pu_step / (ms_e2e / 1e3)
 
 
 # ---------------------------------------------------------------- our arm
@@ -300,8 +306,12 @@ def main_ours(args):
     t0 = time.perf_counter()
     ctx = fcsdnn.Context(w)
     init_s = time.perf_counter() - t0
+    sharded = world > 1 and args.shard
+    if sharded:
+        from paper_2506_16076_gb300 import shard as SH
+        ctx.shard(world, rank, SH.partition(w, world), SH.DistComm())
     tune = None
-    if not args.no_autotune:
+    if not args.no_autotune and not sharded:
         t0 = time.perf_counter()
         tune = ctx.autotune()
         tune["s"] = round(time.perf_counter() - t0, 2)
@@ -311,6 +321,8 @@ def main_ours(args):
     mu = torch.zeros(ctx.P, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     GRAPH, FILTER, PERPATCH = fcsdnn.STEP_GRAPH, fcsdnn.STEP_FILTER, fcsdnn.STEP_PER_PATCH
+    if sharded:  # host-side exchanges between the stages: no captured graph
+        GRAPH = 0
 
     def steps(k, flags, start):
         for n in range(start, start + k):
@@ -344,7 +356,7 @@ def main_ours(args):
 
         # per-patch schedule on the same GPU (baseline of the batched launch)
         ms_pp = None
-        if not args.no_per_patch:
+        if not args.no_per_patch and not sharded:
             k_pp = max(1, min(args.steps, 3))
             ev0.record(stream)
             steps(k_pp, PERPATCH, n0)
@@ -369,20 +381,22 @@ def main_ours(args):
         # parameter gradients are accumulated on the device as in a gradient run
         from paper_2506_16076_gb300 import adjoint as ADJ
         nadj, kadj = args.adjoint_steps, args.adjoint_checkpoint
-        e_adj = e.clone()
-        ev0.record(stream)
-        eN, tr = ADJ.forward(ctx, e_adj, nadj, kadj, filter=True, first_filtered=0)
-        ev1.record(stream)
-        stream.synchronize()
-        ms_fwd = ev0.elapsed_time(ev1)
-        lam = torch.ones_like(eN)
-        dparam = torch.zeros(2, dtype=torch.float64, device=dev)
-        ev0.record(stream)
-        lam0, _ = ADJ.backward(ctx, tr, lam, dparam)
-        ev1.record(stream)
-        stream.synchronize()
-        ms_adj = ev0.elapsed_time(ev1)
-        del tr, lam, lam0, eN, e_adj
+        ms_fwd = ms_adj = None
+        if not sharded:
+            e_adj = e.clone()
+            ev0.record(stream)
+            eN, tr = ADJ.forward(ctx, e_adj, nadj, kadj, filter=True, first_filtered=0)
+            ev1.record(stream)
+            stream.synchronize()
+            ms_fwd = ev0.elapsed_time(ev1)
+            lam = torch.ones_like(eN)
+            dparam = torch.zeros(2, dtype=torch.float64, device=dev)
+            ev0.record(stream)
+            lam0, _ = ADJ.backward(ctx, tr, lam, dparam)
+            ev1.record(stream)
+            stream.synchronize()
+            ms_adj = ev0.elapsed_time(ev1)
+            del tr, lam, lam0, eN, e_adj
 
         # end to end through the public API with host buffers: every step uploads its input
         # state from pinned host memory and reads its result back to pinned host memory.
@@ -445,8 +459,8 @@ def main_ours(args):
         n0 += k_pipe
 
     pu_step = 5 * ctx.active
-    ms, ms_e2e_pipe, value, e2e_pipe = combine_ranks(world, pu_step, args.steps, ms, ms_e2e, dev)
-    _, ms_e2e_chain, _, e2e_chain = combine_ranks(world, pu_step, args.steps, ms, ms_e2e_chain, dev)
+    ms, ms_e2e_pipe, value, e2e_pipe = combine_ranks(world, pu_step, args.steps, ms, ms_e2e, dev, sharded)
+    _, ms_e2e_chain, _, e2e_chain = combine_ranks(world, pu_step, args.steps, ms, ms_e2e_chain, dev, sharded)
     probe = None
     try:
         probe = fcsdnn.probe_fp64()
@@ -480,9 +494,10 @@ def main_ours(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp64_peak = n_sm * sm_max * 1e6 * 4 / 1e12  # 2 FP64 FMA lanes / clk / SM on GB300, TFLOP/s
         ach = flops / avg_pass_s / 1e12
+        kname = {"cart_q2": "k_cart_q2_tiled"}.get(dom, f"k_{dom}")  # the kernel the pass launches
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": round(ach / fp64_peak, 4), "traffic": measured_traffic(f"k_{dom}", args.workload),
-                "traffic_unit": "DRAM bytes per pass (all length-class launches), ncu", "kernel": f"k_{dom}",
+                "frac": round(ach / fp64_peak, 4), "traffic": measured_traffic(kname, args.workload),
+                "traffic_unit": "DRAM bytes per pass (all length-class launches), ncu", "kernel": kname,
                 "algorithmic_bytes_per_pass": nbytes,
                 "lines_per_pass": nl, "inviscid_lines_per_pass": skipped_lines,
                 "flops_per_pass_executed": flops, "flops_per_pass_all_rounds": flops_full,
@@ -496,20 +511,23 @@ def main_ours(args):
                                                             "source": "fc_probe_fp64, this run"}}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "points": ctx.P, "active_points": ctx.active,
                    "patches": len(w.patches), "schedule": "batched, one launch per pass and length class, CUDA graph",
                    "l2": "inputs larger than L2 (state %.2f GB)" % (32 * ctx.P / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU", "init_s": round(init_s, 2),
+                   "parallelism": ("sharded patches, NCCL exchange" if sharded else "replicas") if world > 1
+                   else "1 GPU", "init_s": round(init_s, 2),
                    "autotune": tune},
         "per_patch": None if ms_pp is None else {"value": world * pu_step / (ms_pp / 1e3), "ms_per_step": ms_pp,
                                                  "batched_speedup": ms_pp / (ms / args.steps)},
         "kernels_ms_per_step": {k: round(v[0] / 2, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
-        "adjoint": {"steps": nadj, "checkpoint_every": kadj, "filter": True, "forward_ms": ms_fwd,
-                    "adjoint_ms": ms_adj, "adjoint_forward_ratio": ms_adj / ms_fwd,
-                    "note": "forward = filtered steps with mu/dt recorded and checkpoints; adjoint = segment "
-                            "replays + fc_adjoint_step per step with the parameter gradients accumulated"},
+        "adjoint": None if ms_fwd is None else {
+            "steps": nadj, "checkpoint_every": kadj, "filter": True, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
+            "adjoint_forward_ratio": ms_adj / ms_fwd,
+            "note": "forward = filtered steps with mu/dt recorded and checkpoints; adjoint = segment replays + "
+                    "fc_adjoint_step per step with the parameter gradients accumulated"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_chain, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P,

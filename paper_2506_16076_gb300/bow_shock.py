@@ -9,6 +9,12 @@ behind a normal shock and the experimental fit d0 / (2 R) = 0.193 exp(4.67 / M^2
 paper validates against (Sec. 7, eq. cylinder_bow).
 
   python -m paper_2506_16076_gb300.bow_shock --mach 3 --steps 40000 --report-every 5000
+  python -m paper_2506_16076_gb300.bow_shock --mach 25 --steps 60000 --report-every 5000
+
+A uniform hypersonic stream switched on against the no-slip wall loses positivity in the
+first filtered steps, so from Mach 10 on (or with --potential-start) the run starts as
+the Mach-25 workloads do: free-stream density and pressure with the potential-flow
+velocity around the cylinder, damped to zero in a 0.05-thick layer at the wall.
 
 The shock is located on the O-grid's radial line through the front stagnation point
 (angle pi): the outermost radius where the density exceeds the midpoint between the
@@ -47,12 +53,16 @@ def shock_radius(r, rho, rho_inf):
     return float(r[k.max()]) if len(k) else float("nan")
 
 
-def workload(mach):
+def workload(mach, potential_start=False):
     from paper_2506_16076_gb300 import workloads as W
     w = W.cyl_m3()
     fs = (1.4, float(mach), 0.0, 1.0)
     pts = [dataclasses.replace(p, bc=(fs,) * 4) for p in w.patches]
-    return dataclasses.replace(w, name=f"cyl_m{mach:g}", patches=pts, freestream=fs)
+    w = dataclasses.replace(w, name=f"cyl_m{mach:g}", patches=pts, freestream=fs)
+    if potential_start:
+        w = dataclasses.replace(w, init="potential",
+                                extra={"cyl_radius": 0.5, "cutoff": 3.0, "wall_layer": 0.05})
+    return w
 
 
 def main():
@@ -60,11 +70,13 @@ def main():
     ap.add_argument("--mach", type=float, default=3.0)
     ap.add_argument("--steps", type=int, default=40000)
     ap.add_argument("--report-every", type=int, default=5000)
+    ap.add_argument("--potential-start", action="store_true",
+                    help="start from the potential flow with a no-slip wall layer (default from Mach 10 on)")
     args = ap.parse_args()
     import torch
     from paper_2506_16076_gb300 import fcsdnn, workloads as W
 
-    w = workload(args.mach)
+    w = workload(args.mach, args.potential_start or args.mach >= 10.0)
     og = w.patches[0]
     assert og.kind == W.OGRID
     xc, yc, r0, r1 = og.geom

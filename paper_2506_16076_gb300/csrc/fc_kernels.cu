@@ -113,9 +113,8 @@ __device__ __forceinline__ void deriv2(double2* A, int Lmax, const Job& J, const
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
-  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
-  mul_deriv_rev(A, P.L, 2, J.scale * TWO_PI / ((double)P.L * (double)P.L), T.ip + P.rev, lane, 32);
-  FC_SYNC();
+  fft_forward_mul<MUL_DERIV>(A, P, 2, T.tw, J.scale * TWO_PI / ((double)P.L * (double)P.L), T.ip + P.rev, nullptr,
+                             lane, 32);
   fft_inplace<true>(A, P, 2, T.tw, lane, 32);
 }
 
@@ -701,9 +700,7 @@ __device__ __forceinline__ void filter2(double2* A, int Lmax, const Job& J, cons
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
-  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
-  mul_filter_rev(A, P.L, 2, T.rp + P.sig, T.ip + P.rev, lane, 32);
-  FC_SYNC();
+  fft_forward_mul<MUL_FILTER>(A, P, 2, T.tw, 0.0, T.ip + P.rev, T.rp + P.sig, lane, 32);
   fft_inplace<true>(A, P, 2, T.tw, lane, 32);
 }
 

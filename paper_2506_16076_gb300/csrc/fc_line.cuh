@@ -164,8 +164,21 @@ struct Dft<7, INV> : DftOdd<7, INV> {};
 // k = sum_s d_s R_0..R_{s-1} (digit-reversed order, table Plan::rev); the inverse
 // transform takes that order back to natural order, so no permutation pass is needed
 // and spectral multipliers look up each slot's mode number.
-template <int R, bool INV, bool DIF>
-FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2* __restrict__ tw, int lane, int nl) {
+// spectral multipliers folded into the last stage of a forward transform (span 1, where
+// the R outputs of butterfly bb land in slots bb R + r): MUL_DERIV: i m_k (eq. fc_der),
+// MUL_FILTER: sigma(2k/L)/L (eq. filtering), with k = rev[slot]
+enum { MUL_NONE = 0, MUL_DERIV = 1, MUL_FILTER = 2 };
+FC_HD double2 deriv_mult(double2 z, int k, int L, double fac) {
+  int kk = (2 * k <= L) ? k : k - L;
+  if (2 * k == L) kk = 0;
+  const double m = (fac * (double)kk);
+  return cpx(-m * z.y, m * z.x);
+}
+
+template <int R, bool INV, bool DIF, int MUL = MUL_NONE>
+FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2* __restrict__ tw, int lane, int nl,
+                           double fac = 0.0, const int* __restrict__ rev = nullptr,
+                           const double* __restrict__ sig = nullptr) {
   const int nbf = L / R;
   const int tws = L / (R * span);
   for (int idx = lane; idx < nseq * nbf; idx += nl) {
@@ -193,6 +206,13 @@ FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2*
         if (INV) w.y = -w.y;
         v[q] = cmul(v[q], w);
       }
+    }
+    if (MUL == MUL_DERIV) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = deriv_mult(v[r], rev[bb * R + r], L, fac);
+    } else if (MUL == MUL_FILTER) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = cscl(v[r], sig[rev[bb * R + r]]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r * span] = v[r];
@@ -290,12 +310,7 @@ FC_HD void mul_deriv_rev(double2* a, int L, int nseq, double fac, const int* __r
   for (int idx = lane; idx < nseq * L; idx += nl) {
     const int s = idx / L;
     const int t = idx - s * L;
-    const int k = rev[t];
-    int kk = (2 * k <= L) ? k : k - L;
-    if (2 * k == L) kk = 0;
-    const double m = (fac * (double)kk);
-    const double2 z = a[idx];
-    a[idx] = cpx(-m * z.y, m * z.x);
+    a[idx] = deriv_mult(a[idx], rev[t], L, fac);
   }
 }
 
@@ -306,6 +321,50 @@ FC_HD void mul_filter_rev(double2* a, int L, int nseq, const double* __restrict_
     const int s = idx / L;
     const int t = idx - s * L;
     a[idx] = cscl(a[idx], sig[rev[t]]);
+  }
+}
+
+// forward transform (as fft_inplace<false>) followed by the derivative (MUL_DERIV) or
+// filter (MUL_FILTER) multiplier, the multiplier applied inside the last stage when its
+// radix has a fixed butterfly (one shared-memory pass and one barrier fewer)
+template <int MUL>
+FC_HD void fft_forward_mul(double2* a, const Plan& P, int nseq, const double2* twpool, double fac,
+                           const int* __restrict__ rev, const double* __restrict__ sig, int lane, int nl) {
+  const double2* tw = twpool + P.tw;
+  const int L = P.L;
+  int span = L;
+  for (int st = 0; st < P.nst; ++st) {
+    const int R = P.rad[st];
+    span /= R;
+    if (st == P.nst - 1) {
+      switch (R) {
+        case 2: inplace_stage_r<2, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 3: inplace_stage_r<3, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 4: inplace_stage_r<4, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 5: inplace_stage_r<5, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 7: inplace_stage_r<7, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 8: inplace_stage_r<8, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        default:
+          inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl);
+          FC_SYNC();
+          if (MUL == MUL_DERIV)
+            mul_deriv_rev(a, L, nseq, fac, rev, lane, nl);
+          else
+            mul_filter_rev(a, L, nseq, sig, rev, lane, nl);
+          break;
+      }
+    } else {
+      switch (R) {
+        case 2: inplace_stage_r<2, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 3: inplace_stage_r<3, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 4: inplace_stage_r<4, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 5: inplace_stage_r<5, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 7: inplace_stage_r<7, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        case 8: inplace_stage_r<8, false, true>(a, L, span, nseq, tw, lane, nl); break;
+        default: inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl); break;
+      }
+    }
+    FC_SYNC();
   }
 }
 
