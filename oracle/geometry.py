@@ -349,6 +349,9 @@ def neville(nodes, vals, t):
     return P[0]
 
 
+SNAP = 1e-9  # index units: fractional stencil offsets this close to an integer are that integer
+
+
 class Connectivity:
     """Receivers of every patch with their donors and stencils (Sec. 3.4.1)."""
 
@@ -388,6 +391,12 @@ class Connectivity:
                 T2 = np.where(better, s2 - a2, T2)
             if n and (donor < 0).any():
                 self.errors.append((p, int((donor < 0).sum())))
+            # a receiver that coincides with a donor grid point (sub-patches of one patch
+            # share their overlap points, Sec. 3.4.2) takes that point's value: its offsets
+            # within the stencil are snapped to the integer they equal up to rounding, where
+            # the quadratic interpolation reduces to the node value
+            T1 = np.where(np.abs(T1 - np.round(T1)) < SNAP, np.round(T1), T1)
+            T2 = np.where(np.abs(T2 - np.round(T2)) < SNAP, np.round(T2), T2)
             self.items.append(dict(j=rj, i=ri, donor=donor, a1=A1, a2=A2, t1=T1, t2=T2))
 
     def exchange(self, states):

@@ -61,6 +61,26 @@ struct DBuf {
 };
 
 inline long long rnd_half_up(double t) { return (long long)std::floor(t + 0.5); }
+constexpr double SNAP_IDX = 1e-9;  // index units: stencil offsets this close to an integer are that integer
+
+// receivers whose weights are unit vectors (a coincident donor point) go to the copy list
+void split_exchange(const std::vector<Recv>& all, std::vector<Recv>& interp, std::vector<PtCopy>& copies) {
+  interp.clear();
+  copies.clear();
+  for (const Recv& r : all) {
+    int m1 = -1, m2 = -1;
+    for (int m = 0; m < 3; ++m) {
+      const bool u1 = r.w1[m] == 1.0 && r.w1[(m + 1) % 3] == 0.0 && r.w1[(m + 2) % 3] == 0.0;
+      const bool u2 = r.w2[m] == 1.0 && r.w2[(m + 1) % 3] == 0.0 && r.w2[(m + 2) % 3] == 0.0;
+      if (u1) m1 = m;
+      if (u2) m2 = m;
+    }
+    if (m1 >= 0 && m2 >= 0)
+      copies.push_back(PtCopy{r.dst, r.src[3 * m2 + m1]});
+    else
+      interp.push_back(r);
+  }
+}
 inline double pymod(double a, double n) { return a - n * std::floor(a / n); }
 
 }  // namespace
@@ -151,8 +171,12 @@ struct fc_ctx {
   double* cur_acc = nullptr;  // d_bcacc while an adjoint step accumulates dparam, else null
   WallPt* d_walls = nullptr;  // no-slip adiabatic wall points
   int nwalls = 0;
-  Recv* d_recv = nullptr;
+  Recv* d_recv = nullptr;  // receivers interpolated from 3 x 3 donor stencils
   int nrecv = 0;
+  PtCopy* d_rcopy = nullptr;  // receivers that copy a coincident donor point
+  int nrcopy = 0;
+  Recv* d_recv_all = nullptr;  // every receiver (the exchange transpose zeroes them)
+  int nrecv_all = 0;
   int* d_cross_dst = nullptr;
   int* d_cross_ptr = nullptr;
   int* d_cross_src = nullptr;
@@ -1130,6 +1154,11 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
             w[1] = t * (2.0 - t);
             w[2] = 0.5 * t * (t - 1.0);
           };
+          // a receiver that coincides with a donor grid point (shared overlap points of the
+          // sub-patches of one patch, Sec. 3.4.2) takes that point's value: offsets within
+          // rounding of an integer are that integer (unit weights, an exact copy)
+          if (std::fabs(bt1 - std::nearbyint(bt1)) < SNAP_IDX) bt1 = std::nearbyint(bt1);
+          if (std::fabs(bt2 - std::nearbyint(bt2)) < SNAP_IDX) bt2 = std::nearbyint(bt2);
           lag(bt1, r.w1);
           lag(bt2, r.w2);
           recv.push_back(r);
@@ -1502,12 +1531,16 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   for (const Plan& pl : B.plans)
     for (int st = 0; st < pl.nst; ++st)
       if (pl.rad[st] > MAX_GENERIC_RADIX) return bad("a continued line length has a prime factor above 128");
+  std::vector<Recv> rinterp;
+  std::vector<PtCopy> rcopy;
+  split_exchange(recv, rinterp, rcopy);
   ok = ok && c->upload(&c->d_plans, B.plans) && c->upload(&c->d_tw, B.tw) && c->upload(&c->d_rp, B.rp) &&
        c->upload(&c->d_ip, B.ip) &&
        c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
        c->upload(&c->d_fix, fix) && c->upload(&c->d_gfix, gfix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
-       c->upload(&c->d_bc, bcs) && c->upload(&c->d_walls, walls) && c->upload(&c->d_recv, recv) && c->upload(&c->d_cross_dst, cdst) &&
+       c->upload(&c->d_bc, bcs) && c->upload(&c->d_walls, walls) && c->upload(&c->d_recv, rinterp) &&
+       c->upload(&c->d_rcopy, rcopy) && c->upload(&c->d_recv_all, recv) && c->upload(&c->d_cross_dst, cdst) &&
        c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
        c->upload(&c->d_dsrc, dsrc) && c->upload(&c->d_drecv, drecv) && c->upload(&c->d_dw, dw) &&
        c->upload(&c->d_wall, wall) && c->upload(&c->d_wallw, wallw) && c->upload(&c->d_wallc, wallc);
@@ -1531,7 +1564,9 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->nfcopy2 = (int)fc2.size();
   c->nbc = (int)bcs.size();
   c->nwalls = (int)walls.size();
-  c->nrecv = (int)recv.size();
+  c->nrecv = (int)rinterp.size();
+  c->nrcopy = (int)rcopy.size();
+  c->nrecv_all = (int)recv.size();
   c->ncross = (int)cdst.size();
   const size_t P = (size_t)c->P, Pg = (size_t)std::max<long long>(c->Pg, 1);
   ok = ok && c->alloc(&c->d_B1, 4 * P) && c->alloc(&c->d_B2, 4 * P) && c->alloc(&c->d_B3, 4 * P) &&
@@ -1753,6 +1788,10 @@ void project(fc_ctx* c, double* e, cudaStream_t st) {
     launch_exchange(c->d_recv, c->nrecv, e, c->P, st);
     c->launches++;
   }
+  if (c->nrcopy) {
+    launch_copy_points(c->d_rcopy, c->nrcopy, e, c->P, st);
+    c->launches++;
+  }
   if (c->sharded()) {  // fringe values interpolated on the donors' ranks
     fc_ctx::XPlan& x = c->xp_fringe;
     launch_xpack(c->d_xsend, x.nsend, e, c->P, x.d_sbuf, st);
@@ -1869,10 +1908,10 @@ void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream
 // transpose of project(); u: the state project() was applied to (used by the adiabatic walls)
 void projectT(fc_ctx* c, double* lam, double* gbc, const double* u, cudaStream_t st) {
   Prof pr(c, st, "bc_exchange_T");
-  launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv, c->nrecv, lam, c->P, st);
+  launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv_all, c->nrecv_all, lam, c->P, st);
   launch_bc_wall_T(c->d_walls, c->nwalls, u, lam, c->P, c->prm.gamma, st);
   launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->cur_acc, c->fsj, c->P, st);
-  c->launches += (c->ndon > 0) + (c->nrecv > 0) + (c->nwalls > 0) + (c->nbc > 0);
+  c->launches += (c->ndon > 0) + (c->nrecv_all > 0) + (c->nwalls > 0) + (c->nbc > 0);
 }
 
 // acc += dt L'(u)^T psi
@@ -2616,9 +2655,13 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   }
   std::vector<uint8_t> mask(npatch);
   for (int p = 0; p < npatch; ++p) mask[p] = own[p] == rank ? 1 : 0;
+  std::vector<Recv> loc_interp;
+  std::vector<PtCopy> loc_copy;
+  split_exchange(loc, loc_interp, loc_copy);
   ok = ok && c->upload(&c->d_bc, bc) && c->upload(&c->d_walls, walls) && c->upload(&c->d_fix, fix) &&
        c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) && c->upload(&c->d_gfix, gfix) &&
-       c->upload(&c->d_recv, loc) && c->upload(&c->d_xsend, xsend) && c->upload(&c->d_xrecv, xrecv) &&
+       c->upload(&c->d_recv, loc_interp) && c->upload(&c->d_rcopy, loc_copy) && c->upload(&c->d_xsend, xsend) &&
+       c->upload(&c->d_xrecv, xrecv) &&
        c->upload(&c->d_cross_dst, cdst) && c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) &&
        c->upload(&c->d_vsend, vsend) && c->upload(&c->d_vrecv, vrecv) && c->upload(&c->d_owned, mask) &&
        c->alloc(&c->xp_fringe.d_sbuf, 4 * xsend.size()) && c->alloc(&c->xp_fringe.d_rbuf, 4 * xrecv.size()) &&
@@ -2631,7 +2674,8 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
   c->ngfix = (int)gfix.size();
-  c->nrecv = (int)loc.size();
+  c->nrecv = (int)loc_interp.size();
+  c->nrcopy = (int)loc_copy.size();
   c->ncross = (int)cdst.size();
   c->xp_fringe.nsend = (int)xsend.size();
   c->xp_fringe.nrecv = (int)xrecv.size();

@@ -66,6 +66,12 @@ struct Recv {
   double w1[3], w2[3];
 };
 
+// Receiver that coincides with a donor grid point (sub-patches of one patch share their
+// overlap points, Sec. 3.4.2): the exchange copies the value.
+struct PtCopy {
+  int dst, src;
+};
+
 // Boundary overwrite of one point.
 struct BcPt {
   int idx;
@@ -160,6 +166,7 @@ void launch_filterT_copy2(const DevTables& T, const int* idx, int n, const doubl
 void launch_filterT_copy1(const DevTables& T, const int* idx, int n, const double* MF, const double* e, double* out,
                           cudaStream_t st);
 void launch_exchange(const Recv* r, int n, double* e, long long P, cudaStream_t st);
+void launch_copy_points(const PtCopy* c, int n, double* e, long long P, cudaStream_t st);
 // sharded exchange: buf[4 i + c] = the interpolated value of record i (as launch_exchange
 // would write it), and its scatter e[dst[i] + c P] = buf[4 i + c]
 void launch_xpack(const Recv* r, int n, const double* e, long long P, double* buf, cudaStream_t st);

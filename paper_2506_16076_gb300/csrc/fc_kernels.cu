@@ -659,6 +659,14 @@ __global__ void k_exchange(const Recv* __restrict__ r, int n, double* __restrict
 #pragma unroll
   for (int c = 0; c < 4; ++c) e[R.dst + c * P] = interp33(R, e + c * P);
 }
+// intra-patch exchange: receivers that coincide with a donor point take its value
+__global__ void k_copy_points(const PtCopy* __restrict__ cp, int n, double* __restrict__ e, long long P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const PtCopy c = cp[i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[c.dst + k * P] = e[c.src + k * P];
+}
 // sharded exchange: the values a rank owes to others, and their scatter on arrival
 __global__ void k_xpack(const Recv* __restrict__ r, int n, const double* __restrict__ e, long long P,
                         double* __restrict__ buf) {
@@ -1849,6 +1857,9 @@ void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, double* acc, F
                  cudaStream_t st) {
   if (n <= 0) return;
   k_bc_T<<<grid_pts(n, 256), 256, 0, st>>>(bc, n, lam, gbc, acc, fj, P);
+}
+void launch_copy_points(const PtCopy* c, int n, double* e, long long P, cudaStream_t st) {
+  if (n > 0) k_copy_points<<<grid_pts(n, 256), 256, 0, st>>>(c, n, e, P);
 }
 void launch_xpack(const Recv* r, int n, const double* e, long long P, double* buf, cudaStream_t st) {
   if (n > 0) k_xpack<<<grid_pts(n, 128), 128, 0, st>>>(r, n, e, P, buf);

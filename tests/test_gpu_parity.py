@@ -260,3 +260,4 @@ def test_nonfinite_detector(case):
     e[0, 5] = float("nan")
     assert ctx.sync_status(e) == 5
     assert ctx.sync_status(e, check_state=False) == 0  # the flag was cleared by the read
+

@@ -116,3 +116,29 @@ def test_every_point_of_a_periodic_line_has_its_centred_window():
     s2 = V.window_starts(g, 2)
     j = np.arange(g.n2)
     assert np.array_equal(s2[:, 0], np.clip(j - 3, 0, g.n2 - 7))
+
+
+def test_intra_patch_exchange_copies_shared_points():
+    # sub-patches of one patch share their overlap grid points (Sec. 3.2.1); the exchange
+    # between them copies values (Sec. 3.4.2): every such receiver's stencil offsets are
+    # integers and its value equals the coincident donor point's bit for bit
+    from oracle import geometry as G
+    w = W.subpatched(W.sod128(185))  # 2 x 2 sub-patches of 101 x 101 sharing 17 lines
+    geos, conn = G.build(w)
+    rng = np.random.default_rng(4)
+    states = [rng.normal(size=(4, g.n2, g.n1)) for g in geos]
+    before = [s.copy() for s in states]
+    conn.exchange(states)
+    ncopy = 0
+    for p, it in enumerate(conn.items):
+        for k in range(len(it["j"])):
+            q = it["donor"][k]
+            if q < 0:
+                continue
+            assert float(it["t1"][k]).is_integer() and float(it["t2"][k]).is_integer()
+            i1 = int(it["a1"][k] + it["t1"][k])
+            i2 = int(it["a2"][k] + it["t2"][k])
+            got = states[p][:, it["j"][k], it["i"][k]]
+            assert np.array_equal(got, before[q][:, i2, i1])
+            ncopy += 1
+    assert ncopy > 1000
