@@ -9,7 +9,7 @@ behind a normal shock and the experimental fit d0 / (2 R) = 0.193 exp(4.67 / M^2
 paper validates against (Sec. 7, eq. cylinder_bow).
 
   python -m paper_2506_16076_gb300.bow_shock --mach 3 --steps 40000 --report-every 5000
-  python -m paper_2506_16076_gb300.bow_shock --mach 25 --steps 60000 --report-every 5000
+  python -m paper_2506_16076_gb300.bow_shock --workload cyl_m25_32 --steps 8000 --report-every 1000
 
 A uniform hypersonic stream switched on against the no-slip wall loses positivity in the
 first filtered steps, so from Mach 10 on (or with --potential-start) the run starts as
@@ -72,11 +72,23 @@ def main():
     ap.add_argument("--report-every", type=int, default=5000)
     ap.add_argument("--potential-start", action="store_true",
                     help="start from the potential flow with a no-slip wall layer (default from Mach 10 on)")
+    ap.add_argument("--d", type=int, default=None,
+                    help="FC order d of the continuation (the paper uses d = 2 throughout; default: the workload's)")
+    ap.add_argument("--workload", default=None,
+                    help="a named workload with an O-grid around the cylinder (e.g. cyl_m25_32) instead of the "
+                         "Mach-M cylinder on the 4 x 4 array")
     args = ap.parse_args()
     import torch
     from paper_2506_16076_gb300 import fcsdnn, workloads as W
 
-    w = workload(args.mach, args.potential_start or args.mach >= 10.0)
+    if args.workload:
+        w = W.WORKLOADS[args.workload]()
+        args.mach = float(np.hypot(w.freestream[1], w.freestream[2]) / math.sqrt(GAMMA * w.freestream[3] /
+                                                                                w.freestream[0]))
+    else:
+        w = workload(args.mach, args.potential_start or args.mach >= 10.0)
+    if args.d is not None:
+        w = dataclasses.replace(w, params=dataclasses.replace(w.params, d=args.d))
     og = w.patches[0]
     assert og.kind == W.OGRID
     xc, yc, r0, r1 = og.geom
@@ -101,11 +113,14 @@ def main():
             rho = a[0][:, i_front]
             p = (GAMMA - 1.0) * (a[3][:, i_front] - 0.5 * (a[1][:, i_front] ** 2 + a[2][:, i_front] ** 2) / rho)
             rs = shock_radius(r, rho, w.freestream[0])
-            print(json.dumps({"step": n + 1, "t": round(t, 5), "status": ctx.sync_status(e),
+            status = ctx.sync_status(e)
+            print(json.dumps({"step": n + 1, "t": round(t, 5), "status": status,
                               "p_stagnation_wall": round(float(p[0]), 4),
                               "p_pitot": round(pitot_pressure(args.mach, w.freestream[3]), 4),
                               "standoff_over_2R": round((rs - R) / (2 * R), 4),
                               "billig_fit": round(billig_standoff(args.mach), 4)}), flush=True)
+            if status != 0:  # a non-finite or non-physical state: nothing further to measure
+                break
 
 
 if __name__ == "__main__":
