@@ -409,35 +409,11 @@ def main_ours(args):
         host = e.cpu().pin_memory()
         host_out = torch.empty_like(host).pin_memory()
         k_e2e = max(1, min(args.steps, 10))
-        # the round trip of each step's result runs in NCH chunks on two copy streams, so
-        # that chunk k travels back to the device while chunk k + 1 is still on its way to
-        # the host (the two directions of the link overlap); the next step starts when the
-        # whole state is back
-        NCH = 8
-        flat_d, flat_h = e.view(-1), host.view(-1)
-        bounds = [flat_d.numel() * k // NCH for k in range(NCH + 1)]
-        d2h_s, h2d_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
         ev0.record(stream)
-        e.copy_(host, non_blocking=True)  # the first step's input
         for n in range(n0, n0 + k_e2e):
+            e.copy_(host, non_blocking=True)
             ctx.rk_step(e, dt, mu, GRAPH | FILTER)
-            done = torch.cuda.Event()
-            done.record(stream)
-            d2h_s.wait_event(done)
-            last = n == n0 + k_e2e - 1
-            for k in range(NCH):
-                a, b = bounds[k], bounds[k + 1]
-                with torch.cuda.stream(d2h_s):
-                    flat_h[a:b].copy_(flat_d[a:b], non_blocking=True)
-                    back = torch.cuda.Event()
-                    back.record(d2h_s)
-                if not last:  # the next step's input: this chunk, from the host buffer
-                    h2d_s.wait_event(back)
-                    with torch.cuda.stream(h2d_s):
-                        flat_d[a:b].copy_(flat_h[a:b], non_blocking=True)
-            arrived = torch.cuda.Event()
-            arrived.record(d2h_s if last else h2d_s)
-            stream.wait_event(arrived)
+            host.copy_(e, non_blocking=True)
         ev1.record(stream)
         stream.synchronize()
         ms_e2e_chain = ev0.elapsed_time(ev1) / k_e2e
@@ -556,9 +532,8 @@ def main_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_chain, "unit": UNIT, "h2d_bytes_per_step": 32 * ctx.P,
                 "d2h_bytes_per_step": 32 * ctx.P, "ms_per_step": ms_e2e_chain, "steps": k_e2e,
-                "schedule": "chained time march through pinned host memory: step, D2H of its result into the host "
-                            "buffer, H2D of that buffer as the next step's input; the round trip in 8 chunks on "
-                            "two copy streams (the two link directions overlap), the next step after all chunks",
+                "schedule": "chained time march through pinned host memory: H2D of the host state, step, D2H of "
+                            "its result into the same host buffer, in order on one stream",
                 "independent_inputs_pipelined": {
                     "value": e2e_pipe, "ms_per_step": ms_e2e_pipe, "steps": k_pipe,
                     "schedule": "independent host inputs: step n+1's upload and step n's read-back on two copy "
