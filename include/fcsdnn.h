@@ -306,8 +306,13 @@ typedef int (*fc_comm_fn)(void *user, int op, const double *send_dev, const long
  * (FC_COMM_EXCHANGE) and scatters what it receives; per viscosity evaluation the same
  * for the window sums of the cross-patch blending; per time step one FC_COMM_MIN. The
  * results equal the unsharded context's bit for bit (the same kernels on the same
- * values). Not available while sharded: FC_STEP_GRAPH and FC_STEP_PER_PATCH steps, the
- * adjoint, fc_drag and fc_autotune (FC_ERR_UNIMPLEMENTED). Once per context. */
+ * values). fc_adjoint_step runs sharded too: its projections' transposes send each
+ * receiver's adjoint back to the donors' rank (the exchange reversed), so lam_n on the
+ * owned patches equals the unsharded one bit for bit; fc_drag evaluates J and dJ/de on
+ * the rank that owns the wall ring's patch (J = 0 elsewhere), and the dparam sums of
+ * fc_adjoint_step and fc_initial_sensitivity cover the owned patches: the caller adds J
+ * and dparam over the ranks. Not available while sharded: FC_STEP_GRAPH and
+ * FC_STEP_PER_PATCH steps and fc_autotune (FC_ERR_UNIMPLEMENTED). Once per context. */
 fc_status fc_shard(fc_ctx *ctx, int nranks, int rank, const int *owner, fc_comm_fn comm, void *user);
 
 /* Doubles this rank sends to / receives from `peer` in one FC_COMM_EXCHANGE of a

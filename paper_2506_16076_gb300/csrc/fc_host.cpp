@@ -156,6 +156,7 @@ struct fc_ctx {
   };
   XPlan xp_fringe, xp_visc;
   Recv* d_xsend = nullptr;   // fringe records this rank interpolates for others
+  int* d_xsend_dst = nullptr;  // their receivers (other ranks' points): the adjoint's arrivals
   int* d_xrecv = nullptr;    // receivers of this rank filled from others
   int* d_vsend = nullptr;    // window-sum entries this rank sends
   int* d_vrecv = nullptr;    // window-sum entries this rank receives
@@ -169,8 +170,9 @@ struct fc_ctx {
   double* d_bcacc = nullptr;  // [nbc][2] per-record sums of one adjoint step
   double* d_part = nullptr;   // [SENS_BLOCKS][2] partial sums of fc_initial_sensitivity
   double* cur_acc = nullptr;  // d_bcacc while an adjoint step accumulates dparam, else null
-  WallPt* d_walls = nullptr;  // no-slip adiabatic wall points
+  WallPt* d_walls = nullptr;  // no-slip adiabatic wall points (of the owned patches, when sharded)
   int nwalls = 0;
+  bool any_walls = false;  // the workload has adiabatic walls (the same on every rank)
   Recv* d_recv = nullptr;  // receivers interpolated from 3 x 3 donor stencils
   int nrecv = 0;
   PtCopy* d_rcopy = nullptr;  // receivers that copy a coincident donor point
@@ -204,6 +206,7 @@ struct fc_ctx {
   bool adj_ready = false;
   // wall ring for the drag functional
   int* d_wall = nullptr;
+  int wall_patch = -1;  // the patch that carries the wall ring
   double* d_wallw = nullptr;
   double* d_wallc = nullptr;
   int nwall = 0;
@@ -1503,8 +1506,10 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   // ---- wall ring of the first curvilinear patch with a wall at q2 = 0 (drag functional)
   std::vector<int> wall;
   std::vector<double> wallw, wallc;
-  for (const HPatch& h : c->hp) {
+  for (int p = 0; p < npatch; ++p) {
+    const HPatch& h = c->hp[p];
     if (h.d.kind != FC_PATCH_OGRID || (h.d.side[2] != FC_SIDE_SLIPWALL && h.d.side[2] != FC_SIDE_ADIABATIC)) continue;
+    c->wall_patch = p;
     for (int i = 0; i < h.n1; ++i) {
       const double dx = h.x[i] - h.d.geom[0], dy = h.y[i] - h.d.geom[1];
       wall.push_back((int)(h.off + i));
@@ -1564,6 +1569,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->nfcopy2 = (int)fc2.size();
   c->nbc = (int)bcs.size();
   c->nwalls = (int)walls.size();
+  c->any_walls = !walls.empty();
   c->nrecv = (int)rinterp.size();
   c->nrcopy = (int)rcopy.size();
   c->nrecv_all = (int)recv.size();
@@ -1908,6 +1914,14 @@ void rk_body(fc_ctx* c, double* e, double* dt, double* mu, int flags, cudaStream
 // transpose of project(); u: the state project() was applied to (used by the adiabatic walls)
 void projectT(fc_ctx* c, double* lam, double* gbc, const double* u, cudaStream_t st) {
   Prof pr(c, st, "bc_exchange_T");
+  if (c->sharded()) {  // the exchange reversed: receivers' adjoint back to the donors' ranks
+    fc_ctx::XPlan& x = c->xp_fringe;
+    launch_xgather(c->d_xrecv, x.nrecv, lam, c->P, x.d_rbuf, st);
+    if (c->comm(c->comm_user, FC_COMM_EXCHANGE, x.d_rbuf, x.rcount.data(), x.d_sbuf, x.scount.data(), st) != 0)
+      c->comm_failed = true;
+    launch_xunpack(c->d_xsend_dst, x.nsend, x.d_sbuf, lam, c->P, st);
+    c->launches += (x.nsend > 0) + (x.nrecv > 0);
+  }
   launch_exchange_T(c->d_dptr, c->d_dsrc, c->d_drecv, c->d_dw, c->ndon, c->d_recv_all, c->nrecv_all, lam, c->P, st);
   launch_bc_wall_T(c->d_walls, c->nwalls, u, lam, c->P, c->prm.gamma, st);
   launch_bc_T(c->d_bc, c->nbc, lam, gbc, c->cur_acc, c->fsj, c->P, st);
@@ -2186,11 +2200,12 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
 
 fc_status fc_drag(fc_ctx* c, const double* e, double* J, double* dJde, void* stream) {
   if (!c || !e || !J) return FC_ERR_INVALID;
-  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "fc_drag is not available while sharded");
   if (c->nwall == 0) return fail(c, FC_ERR_INVALID, "no curvilinear patch with a slip wall");
   cudaStream_t st = (cudaStream_t)stream;
   if (dJde) cudaMemsetAsync(dJde, 0, sizeof(double) * 4 * (size_t)c->P, st);
-  launch_drag(c->d_wall, c->d_wallw, c->d_wallc, c->nwall, e, c->P, c->prm.gamma, J, dJde, st);
+  // sharded: the rank that owns the wall ring's patch evaluates J; the others report 0
+  const bool mine = !c->sharded() || c->owner[c->wall_patch] == c->rank;
+  launch_drag(c->d_wall, c->d_wallw, c->d_wallc, mine ? c->nwall : 0, e, c->P, c->prm.gamma, J, dJde, st);
   c->launches++;
   return cuda_check(c, "fc_drag");
 }
@@ -2344,7 +2359,6 @@ fc_status fc_line_stats(fc_ctx* c, long long* lines_q1, long long* lines_q2, dou
 fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const double* dt, const double* lam_np1,
                           double* lam_n, double* gbc, double* dparam, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
-  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "the adjoint is not available while sharded");
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
   cudaStream_t st = (cudaStream_t)stream;
   if (dparam && !c->d_bcacc && c->nbc > 0) {
@@ -2362,7 +2376,7 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
       launch_pair_reduce(c->d_bcacc, c->nbc, dparam, st);
       c->launches += c->nbc > 0;
     }
-    return cuda_check(c, "fc_adjoint_step");
+    return comm_check(c, "fc_adjoint_step");
   };
   if (!c->adj_ready) {
     const size_t n4 = 4 * (size_t)c->P;
@@ -2400,7 +2414,7 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
     s.c0 = c0[i];
     s.c1 = c1[i];
     s.cb = cb[i];
-    if (i == 3 && c->nwalls) {  // acc = a52 u2 + a53 u3 + b53 dt L(u3) for u5 below
+    if (i == 3 && c->any_walls) {  // acc = a52 u2 + a53 u3 + b53 dt L(u3) for u5 below
       s.Uaux = U[2];
       s.out2 = PSb;
       s.d1 = A53;
@@ -2412,7 +2426,7 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
   }
   // the adiabatic walls' transpose at the last projection needs u5 = e_{n+1} (in A3 until
   // the reverse sweep first writes A3)
-  if (c->nwalls) {
+  if (c->any_walls) {
     StageCoef s5{};
     s5.dt = dt;
     s5.Ucur = U[4];
@@ -2658,9 +2672,12 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   std::vector<Recv> loc_interp;
   std::vector<PtCopy> loc_copy;
   split_exchange(loc, loc_interp, loc_copy);
+  std::vector<int> xsend_dst;
+  for (const Recv& r : xsend) xsend_dst.push_back(r.dst);
   ok = ok && c->upload(&c->d_bc, bc) && c->upload(&c->d_walls, walls) && c->upload(&c->d_fix, fix) &&
        c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) && c->upload(&c->d_gfix, gfix) &&
        c->upload(&c->d_recv, loc_interp) && c->upload(&c->d_rcopy, loc_copy) && c->upload(&c->d_xsend, xsend) &&
+       c->upload(&c->d_xsend_dst, xsend_dst) &&
        c->upload(&c->d_xrecv, xrecv) &&
        c->upload(&c->d_cross_dst, cdst) && c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) &&
        c->upload(&c->d_vsend, vsend) && c->upload(&c->d_vrecv, vrecv) && c->upload(&c->d_owned, mask) &&
@@ -2707,14 +2724,13 @@ fc_status fc_shard_counts(const fc_ctx* c, int which, int peer, long long* send,
 fc_status fc_initial_sensitivity(fc_ctx* c, const double* e0, const double* lam0, double* drho, double* dparam,
                                  void* stream) {
   if (!c || !e0 || !lam0) return FC_ERR_INVALID;
-  if (c->sharded()) return fail(c, FC_ERR_UNIMPLEMENTED, "the adjoint is not available while sharded");
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
   if (!drho && !dparam) return FC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (dparam && !c->d_part) {
     if (!c->alloc(&c->d_part, 2 * (size_t)SENS_BLOCKS)) return FC_ERR_OOM;
   }
-  launch_init_sens(c->d_info, c->P, e0, lam0, drho, dparam ? c->d_part : nullptr, c->fsj, st);
+  launch_init_sens(c->d_info, c->d_owned, c->P, e0, lam0, drho, dparam ? c->d_part : nullptr, c->fsj, st);
   c->launches++;
   if (dparam) {
     launch_pair_reduce(c->d_part, SENS_BLOCKS, dparam, st);

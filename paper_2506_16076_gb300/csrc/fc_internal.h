@@ -173,6 +173,8 @@ void launch_xpack(const Recv* r, int n, const double* e, long long P, double* bu
 void launch_xunpack(const int* dst, int n, const double* buf, double* e, long long P, cudaStream_t st);
 // buf[i] = src[idx[i]] and dst[idx[i]] = buf[i]
 void launch_gather(const int* idx, int n, const double* src, double* buf, cudaStream_t st);
+// buf[4 i + c] = e[dst[i] + c P] (the adjoint's reversed fringe exchange)
+void launch_xgather(const int* dst, int n, const double* e, long long P, double* buf, cudaStream_t st);
 void launch_scatter(const int* idx, int n, const double* buf, double* dst, cudaStream_t st);
 void launch_filter_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* F, cudaStream_t st);
 void launch_filter_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* F, double* e, cudaStream_t st);
@@ -211,9 +213,9 @@ void launch_bc_T(const BcPt* bc, int n, double* lam, double* gbc, double* acc, F
 void launch_pair_reduce(double* acc, int n, double* out, cudaStream_t st);
 constexpr int SENS_BLOCKS = 1024;
 // drho (nullable) = lam0 . d e / d rho at fixed u, v, p; part (nullable, [SENS_BLOCKS][2]): per-block
-// sums of lam0 . (dM, dA) over non-blanked points
-void launch_init_sens(const uint32_t* info, long long P, const double* e0, const double* lam0, double* drho,
-                      double* part, FsJac fj, cudaStream_t st);
+// sums of lam0 . (dM, dA) over non-blanked points (of the owned patches, owned non-null)
+void launch_init_sens(const uint32_t* info, const uint8_t* owned, long long P, const double* e0, const double* lam0,
+                      double* drho, double* part, FsJac fj, cudaStream_t st);
 void launch_drag(const int* wall, const double* w, const double* nx, int n, const double* e, long long P, double gam,
                  double* J, double* dJde, cudaStream_t st);
 void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);

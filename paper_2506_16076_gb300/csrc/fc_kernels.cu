@@ -683,6 +683,13 @@ __global__ void k_xunpack(const int* __restrict__ dst, int n, const double* __re
 #pragma unroll
   for (int c = 0; c < 4; ++c) e[dst[i] + c * P] = buf[4 * (long long)i + c];
 }
+__global__ void k_xgather(const int* __restrict__ dst, int n, const double* __restrict__ e, long long P,
+                          double* __restrict__ buf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) buf[4 * (long long)i + c] = e[dst[i] + c * P];
+}
 __global__ void k_gather(const int* __restrict__ idx, int n, const double* __restrict__ src, double* __restrict__ buf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) buf[i] = src[idx[i]];
@@ -1476,14 +1483,15 @@ __global__ void __launch_bounds__(512) k_pair_reduce(double* __restrict__ acc, i
 // sensitivities to the initial data: drho = lam . d e / d rho at fixed u, v, p
 // (lam_rho + lam_mx u + lam_my v + lam_E |u|^2 / 2), and per-block sums of lam . (dM, dA)
 // over non-blanked points (grid-stride in a fixed order, fixed tree per block)
-__global__ void __launch_bounds__(256) k_init_sens(const uint32_t* __restrict__ info, long long P,
+__global__ void __launch_bounds__(256) k_init_sens(const uint32_t* __restrict__ info,
+                                                   const uint8_t* __restrict__ owned, long long P,
                                                    const double* __restrict__ e, const double* __restrict__ lam,
                                                    double* __restrict__ drho, double* __restrict__ part, FsJac fj) {
   __shared__ double s0[256], s1[256];
   const int t = threadIdx.x;
   double a = 0.0, b = 0.0;
   for (long long p = (long long)blockIdx.x * 256 + t; p < P; p += (long long)gridDim.x * 256) {
-    const bool blank = (info[p] & PT_BLANK) != 0;
+    const bool blank = (info[p] & PT_BLANK) != 0 || (owned && !owned[pt_patch(info[p])]);
     const double l0 = lam[p], l1 = lam[p + P], l2 = lam[p + 2 * P], l3 = lam[p + 3 * P];
     if (drho) {
       double r = 0.0;
@@ -1867,6 +1875,9 @@ void launch_xpack(const Recv* r, int n, const double* e, long long P, double* bu
 void launch_xunpack(const int* dst, int n, const double* buf, double* e, long long P, cudaStream_t st) {
   if (n > 0) k_xunpack<<<grid_pts(n, 256), 256, 0, st>>>(dst, n, buf, e, P);
 }
+void launch_xgather(const int* dst, int n, const double* e, long long P, double* buf, cudaStream_t st) {
+  if (n > 0) k_xgather<<<grid_pts(n, 256), 256, 0, st>>>(dst, n, e, P, buf);
+}
 void launch_gather(const int* idx, int n, const double* src, double* buf, cudaStream_t st) {
   if (n > 0) k_gather<<<grid_pts(n, 256), 256, 0, st>>>(idx, n, src, buf);
 }
@@ -1877,9 +1888,9 @@ void launch_pair_reduce(double* acc, int n, double* out, cudaStream_t st) {
   if (n <= 0) return;
   k_pair_reduce<<<1, 512, 0, st>>>(acc, n, out);
 }
-void launch_init_sens(const uint32_t* info, long long P, const double* e0, const double* lam0, double* drho,
-                      double* part, FsJac fj, cudaStream_t st) {
-  k_init_sens<<<SENS_BLOCKS, 256, 0, st>>>(info, P, e0, lam0, drho, part, fj);
+void launch_init_sens(const uint32_t* info, const uint8_t* owned, long long P, const double* e0, const double* lam0,
+                      double* drho, double* part, FsJac fj, cudaStream_t st) {
+  k_init_sens<<<SENS_BLOCKS, 256, 0, st>>>(info, owned, P, e0, lam0, drho, part, fj);
 }
 // p[i] = a + b sin(w i): synthetic inputs of the autotuner
 void launch_deriv_lines(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* src, double* dst,
