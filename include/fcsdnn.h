@@ -178,6 +178,15 @@ fc_status fc_timestep(fc_ctx *ctx, const double *e_dev, const double *mu_dev, do
  * `stream`. */
 fc_status fc_rk_step(fc_ctx *ctx, double *e_dev, double *dt_dev, double *mu_dev, int flags, void *stream);
 
+/* fc_rk_step on a state held in host memory: e_host (4 P doubles, the layout above) is
+ * copied to a device buffer the context owns (allocated on the first call), advanced by
+ * one fc_rk_step (flags as there; FC_STEP_GRAPH captures the step on that buffer once),
+ * and copied back; the call synchronises `stream` before it returns, so e_host holds the
+ * new state then. dt_dev and mu_dev are device buffers as in fc_rk_step. Page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister, torch pin_memory) copies at the link's rate;
+ * pageable memory works but copies slower. */
+fc_status fc_rk_step_host(fc_ctx *ctx, double *e_host, double *dt_dev, double *mu_dev, int flags, void *stream);
+
 /* fc_autotune flags */
 enum { FC_TUNE_PLANS = 1, FC_TUNE_WARPS = 2 };
 /* Measured schedule choice for this context's lines (no paper counterpart: the paper's

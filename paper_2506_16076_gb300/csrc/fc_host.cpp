@@ -163,6 +163,7 @@ struct fc_ctx {
   bool sharded() const { return nranks > 1; }
   bool comm_failed = false;
   double* d_dtmin = nullptr;
+  double* d_ehost = nullptr;  // device copy of the state of fc_rk_step_host
 
   // free stream (fc_params.freestream) and the parameter adjoint of its Dirichlet points
   bool has_fs = false;
@@ -2052,6 +2053,21 @@ fc_status fc_rk_step(fc_ctx* c, double* e, double* dt, double* mu, int flags, vo
   if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_check(c, "graph launch");
   c->launches += c->glaunches;
   return cuda_check(c, "fc_rk_step");
+}
+
+fc_status fc_rk_step_host(fc_ctx* c, double* e_host, double* dt, double* mu, int flags, void* stream) {
+  if (!c || !e_host) return FC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * 4 * (size_t)c->P;
+  if (!c->d_ehost && !c->alloc(&c->d_ehost, 4 * (size_t)c->P)) return fail(c, FC_ERR_OOM, c->err);
+  if (cudaMemcpyAsync(c->d_ehost, e_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return cuda_check(c, "fc_rk_step_host (upload)");
+  const fc_status s = fc_rk_step(c, c->d_ehost, dt, mu, flags, stream);
+  if (s != FC_OK) return s;
+  if (cudaMemcpyAsync(e_host, c->d_ehost, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cuda_check(c, "fc_rk_step_host (read-back)");
+  return FC_OK;
 }
 
 fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {

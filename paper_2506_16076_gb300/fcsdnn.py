@@ -26,7 +26,7 @@ TUNE_PLANS, TUNE_WARPS = 1, 2
 
 # every symbol include/fcsdnn.h declares
 EXPORTS = ["fc_init_patches", "fc_state_size", "fc_patch_offset", "fc_active_points", "fc_rhs", "fc_viscosity",
-           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_autotune", "fc_adjoint_step",
+           "fc_filter", "fc_project", "fc_timestep", "fc_rk_step", "fc_rk_step_host", "fc_autotune", "fc_adjoint_step",
            "fc_initial_sensitivity", "fc_drag", "fc_sync_status", "fc_partition", "fc_shard", "fc_shard_counts",
            "fc_launch_count", "fc_profile_enable", "fc_profile_read", "fc_profile_get", "fc_profile_reset",
            "fc_pass_stats", "fc_line_stats", "fc_probe_fp64", "fc_rhs_patch_noalloc", "fc_last_error", "fc_destroy"]
@@ -83,6 +83,7 @@ def load():
         "fc_project": (C.c_int, [vp, vp, vp]),
         "fc_timestep": (C.c_int, [vp, vp, vp, vp, vp]),
         "fc_rk_step": (C.c_int, [vp, vp, vp, vp, ip, vp]),
+        "fc_rk_step_host": (C.c_int, [vp, vp, vp, vp, ip, vp]),
         "fc_autotune": (C.c_int, [vp, ip, C.POINTER(C.c_double), vp]),
         "fc_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "fc_initial_sensitivity": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -288,6 +289,16 @@ class Context:
 
     def rk_step(self, e, dt, mu, flags=0):
         self._check(self.lib.fc_rk_step(self.ctx, _ptr(e), _ptr(dt), _ptr(mu), int(flags), _stream()))
+
+    def rk_step_host(self, e_host, dt, mu, flags=0):
+        """fc_rk_step_host: one step of a state in host memory (a contiguous CPU float64 tensor
+        of 4 P values, best page-locked); returns when e_host holds the new state."""
+        import torch
+        if not (isinstance(e_host, torch.Tensor) and not e_host.is_cuda and e_host.dtype == torch.float64
+                and e_host.is_contiguous() and e_host.numel() == 4 * self.P):
+            raise FcError(FC_ERR_INVALID, f"e_host must be a contiguous CPU float64 tensor of {4 * self.P} values")
+        self._check(self.lib.fc_rk_step_host(self.ctx, C.c_void_p(e_host.data_ptr()), _ptr(dt), _ptr(mu),
+                                             int(flags), _stream()))
 
     def autotune(self, flags=TUNE_PLANS | TUNE_WARPS):
         """Measured choice of FFT stage orders and warps per CTA (fc_autotune); returns its report."""

@@ -252,6 +252,22 @@ def test_multipatch_steps_parity(gpu_lib, make):
     assert max(errs) < 1e-9, errs
 
 
+def test_host_step_equals_device_step(case, gpu_lib):
+    # fc_rk_step_host (state in page-locked host memory) is fc_rk_step on a device copy
+    w, ctx, sv = case
+    st = W.random_smooth_state(w, seed=37, amp=0.05)
+    e = to_dev(st)
+    host = e.cpu().pin_memory()
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mu = torch.zeros(e.shape[1], dtype=torch.float64, device="cuda")
+    dt2, mu2 = dt.clone(), mu.clone()
+    for n in range(2):
+        ctx.rk_step(e, dt, mu, 1 if n else 0)
+        ctx.rk_step_host(host, dt2, mu2, 1 if n else 0)
+    torch.cuda.synchronize()
+    assert torch.equal(host, e.cpu()) and torch.equal(dt, dt2)
+
+
 def test_nonfinite_detector(case):
     w, ctx, sv = case
     st = W.initial_state(w)
