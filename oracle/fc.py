@@ -152,6 +152,69 @@ def extend_ld(F, d, C):
     return np.concatenate([np.asarray(F).astype(LD), continuation_ld(F, d, C)], axis=-1)
 
 
+def neumann_coefficients(d, C):
+    """Sec. 2.2, the Neumann variant of the FC-Gram continuation (end data with the
+    derivative in place of the end value): the d x d matrix that maps the left-end data
+    (h F'_0, F_1, ..., F_{d-1}) to the coefficients of the degree d-1 polynomial they fix
+    in the Gram basis of the table (the columns of Q, orthonormal on the d matching
+    points 0..d-1). Built as the inverse of the matrix whose row 0 holds the Gram
+    polynomials' derivatives at point 0 (exact Lagrange derivative weights on the nodes
+    0..d-1) and whose rows 1..d-1 hold their values, in long double."""
+    from fractions import Fraction
+    Q, _, _ = load_tables(d, C)
+    nodes = range(d)
+    w0 = []  # l_j'(0) for the Lagrange basis on the nodes 0..d-1
+    for j in nodes:
+        others = [m for m in nodes if m != j]
+        den = Fraction(1)
+        for m in others:
+            den *= Fraction(j - m)
+        num = Fraction(0)
+        for skip in others:  # derivative of prod_m (x - m) at x = 0
+            term = Fraction(1)
+            for m in others:
+                if m != skip:
+                    term *= Fraction(0 - m)
+            num += term
+        w0.append(num / den)
+    QL = Q.astype(LD)
+    V = np.empty((d, d), dtype=LD)
+    V[0] = sum(LD(w0[j].numerator) / LD(w0[j].denominator) * QL[j] for j in nodes)
+    V[1:] = QL[1:]
+    return _inv_ld(V)
+
+
+def _inv_ld(V):
+    """Gauss-Jordan inverse with partial pivoting in long double."""
+    n = V.shape[0]
+    A = np.concatenate([V.astype(LD), np.eye(n, dtype=LD)], axis=1)
+    for col in range(n):
+        piv = col + int(np.argmax(np.abs(A[col:, col])))
+        A[[col, piv]] = A[[piv, col]]
+        A[col] = A[col] / A[col, col]
+        for r in range(n):
+            if r != col:
+                A[r] = A[r] - A[r, col] * A[col]
+    return A[:, n:]
+
+
+def neumann_extend_ld(F, dF0, d, C):
+    """The Neumann-variant continued vector of a line whose left end carries a derivative
+    condition (Sec. 2.2; Remark adiabatic): F[1:] are the values at points 1..N-1, dF0 the
+    derivative at point 0 times the spacing. Returns (wall value, continued vector of
+    length N + C) in long double: the wall value is that of the polynomial the left-end
+    data fix, the continuation A_l c~ + A_r Q^T F_r with c~ its Gram coefficients."""
+    Q, AL, AR = load_tables(d, C)
+    Ft = np.asarray(F).astype(LD)
+    data = np.concatenate([np.atleast_1d(LD(dF0)), Ft[1:d]])
+    c = neumann_coefficients(d, C) @ data
+    wall = c @ Q[0].astype(LD)
+    ext = AL.astype(LD) @ c + AR.astype(LD) @ (Q.T.astype(LD) @ Ft[-d:])
+    full = Ft.copy()
+    full[0] = wall
+    return wall, np.concatenate([full, ext])
+
+
 def dft(x):
     """X_k = sum_j x_j exp(-2 pi i j k / L) along the last axis (definition), in long double."""
     return np.fft.fft(np.asarray(x).astype(CLD), axis=-1)

@@ -153,3 +153,39 @@ def test_choose_C_policies():
         C = fc.choose_C(n, 27, 2)
         assert lo <= C <= hi and fc.transform_cost(n + C) == min(
             fc.transform_cost(n + c) for c in range(27, hi + 1) if fc.transform_cost(n + c) is not None)
+
+
+@pytest.mark.parametrize("d", [2, 5])
+def test_neumann_continuation_reproduces_zero_slope_polynomials(d):
+    # Sec. 2.2, Neumann variant: data (h F'_0 = 0, F_1, ..., F_{N-1}) of a polynomial of
+    # degree < d with zero slope at the wall give back its wall value, and the continued
+    # vector differentiates it (the continuation of a polynomial of degree < d is exact)
+    N, C = 60, 31
+    h = 1.0 / (N - 1)
+    x = np.arange(N) * h
+    p = 1.0 + 0.7 * x ** 2 if d > 2 else np.full(N, 1.3)
+    dp = 1.4 * x if d > 2 else np.zeros(N)
+    wall, ext = fc.neumann_extend_ld(p, 0.0, d, C)
+    assert abs(float(wall) - p[0]) < 1e-13
+    D = fc.spectral_derivative(ext, (N + C) * h)[:N].astype(np.float64)
+    assert np.abs(D - dp).max() < 2e-10 * N
+
+
+@pytest.mark.parametrize("d", [2, 5])  # the orders with tables
+def test_neumann_wall_value_is_the_adiabatic_wall_temperature(d):
+    # the wall value of the Neumann FC end data with zero derivative (Gram-basis
+    # construction) equals the adiabatic wall temperature the solver imposes (polynomial
+    # elimination, solver.adiabatic_weights), and the Neumann continued vector equals the
+    # ordinary continuation of the line whose wall entry holds that temperature
+    from oracle import solver as S
+    rng = np.random.default_rng(d)
+    N, C = 48, 27
+    th = 1.0 + 0.1 * rng.normal(size=N)
+    wall, ext = fc.neumann_extend_ld(th, 0.0, d, C)
+    wts = S.adiabatic_weights(d)
+    ref = sum(w * th[1 + j] for j, w in enumerate(wts))
+    assert abs(float(wall) - ref) < 1e-14 * abs(ref)
+    th2 = th.copy()
+    th2[0] = float(wall)
+    ext2 = fc.extend_ld(th2, d, C)
+    assert np.abs((ext - ext2).astype(np.float64)).max() < 1e-11
