@@ -23,6 +23,10 @@ derivative reaches 1.6e-10 of the result, where an FP64 FFT stays near 5e-12.
 Mode numbers k run over the symmetric range -M..M; for even L the Nyquist
 coefficient k = L/2 gets derivative factor 0 (keeps real data real) and filter
 factor sigma(1).
+
+Sec. 2.2 also admits end data with a derivative in place of the end value (the Neumann
+variant, used for the adiabatic condition of Remark adiabatic): neumann_extend_ld builds
+the Gram coefficients of (h F'_0, F_1, ..., F_{d-1}) and continues from them.
 """
 import functools
 import os
