@@ -70,7 +70,10 @@ def d2T(sv, g, G):
 
 
 def rhs_adjoint_patch(sv, g, u, mu, lam):
-    """L'(u)^T lam on one patch."""
+    """L'(u)^T lam on one patch (the flux form; the product-rule form of wall patches has
+    no adjoint here)."""
+    if sv.product_form(g):
+        raise NotImplementedError("adjoint of the product-rule form at adiabatic walls")
     J1x, J1y, J2x, J2y = g.J
     lm = np.where(g.nodiff[None], 0.0, lam)
     eta_x = -(d1T(sv, g, J1x * lm) + d2T(sv, g, J2x * lm))

@@ -13,6 +13,11 @@ exchange at every stage (Sec. 4.2, Alg. 1 line sol_comm), per-step spectral
 filter of rho, rho u, rho v, theta with E rebuilt (Sec. 4.3.1), and the
 Algorithm 1 order per step: viscosity, filter, dt, 5 stages.
 
+On patches with a no-slip adiabatic side, Params.wall_form = 1 selects the form of
+Remark adiabatic: theta in place of E among the FC-differentiated quantities, the
+derivatives of E and p by the sum and product rules, the convective divergence from them
+(Solver.rhs_patch_product).
+
 Readings (see the design notes): derivatives are 0 on blanked points and on
 segments too short for FC (fewer than 2d points), where L is set to 0; the
 filter acts on steps n >= 1 ("every time step following the initial time")
@@ -100,6 +105,8 @@ class Solver:
 
     # ---- eq. (semi-discrete) ------------------------------------------------------------
     def rhs_patch(self, g, e, mu):
+        if self.product_form(g):
+            return self.rhs_patch_product(g, e, mu)
         gam = self.prm.gamma
         J1x, J1y, J2x, J2y = g.J
         D1, D2 = self.d1(g, e), self.d2(g, e)
@@ -109,6 +116,30 @@ class Solver:
         Hy = euler.flux_y(e, gam) - mu * dy
         L = -(J1x * self.d1(g, Hx) + J1y * self.d1(g, Hy) + J2x * self.d2(g, Hx) + J2y * self.d2(g, Hy))
         return np.where(g.nodiff[None], 0.0, L)
+
+    def product_form(self, g):
+        return getattr(self.prm, "wall_form", 0) == 1 and W.ADIABATIC in tuple(g.desc.side)
+
+    def rhs_patch_product(self, g, e, mu):
+        """L on a patch with a no-slip adiabatic wall in the form of Remark adiabatic: the
+        temperature theta = p/rho replaces E among the FC-differentiated quantities (its
+        continuation along the wall-normal lines is the Neumann expansion, since the wall
+        overwrite puts the Neumann end data's value at the wall); the x and y derivatives
+        of E and p follow from those of rho, rho u, rho v and theta by the sum and product
+        rules, the convective flux divergence from the same rules, and the viscous fluxes
+        mu grad e, with grad E from the product rule, are FC-differentiated as elsewhere:
+            L = -( div f(e) - sum_k sum_i J_ki d/dq^k (mu sum_m J_mi d/dq^m e) )."""
+        gam = self.prm.gamma
+        J1x, J1y, J2x, J2y = g.J
+        th = euler.temperature(e, gam)
+        Q = np.stack([e[0], e[1], e[2], th])
+        D1, D2 = self.d1(g, Q), self.d2(g, Q)
+        ex, px = euler.product_rule_derivatives(Q, J1x * D1 + J2x * D2, gam)
+        ey, py = euler.product_rule_derivatives(Q, J1y * D1 + J2y * D2, gam)
+        conv = euler.flux_divergence_product(e, th, ex, px, ey, py)
+        Vx, Vy = mu * ex, mu * ey
+        visc = J1x * self.d1(g, Vx) + J1y * self.d1(g, Vy) + J2x * self.d2(g, Vx) + J2y * self.d2(g, Vy)
+        return np.where(g.nodiff[None], 0.0, -(conv - visc))
 
     def rhs(self, states, mus):
         return [self.rhs_patch(g, e, m) for g, e, m in zip(self.geos, states, mus)]

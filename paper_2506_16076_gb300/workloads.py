@@ -68,6 +68,9 @@ class Params:
     loc: int = 7
     R: tuple = (1.5, 1.0, 0.5, 0.0)
     depth_cap: int = 64
+    wall_form: int = 0  # 0: flux form on every patch; 1: on patches with an ADIABATIC side the
+    #                     product-rule form of Remark adiabatic (derivatives of E and p from FC
+    #                     derivatives of rho, rho u, rho v and theta)
 
 
 @dataclass
