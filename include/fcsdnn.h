@@ -126,6 +126,19 @@ typedef struct {
    * M = |(u, v)| / a the Mach number and alpha = atan2(v, u) the angle of attack, at fixed
    * density and pressure (sound speed a = sqrt(gamma p / rho)). */
   double freestream[4];
+  /* Operator on patches with an ADIABATIC side (Remark adiabatic). 0: the flux form used on
+   * every other patch (FC derivatives of the flux components). 1: the product-rule form:
+   * rho, rho u, rho v and the temperature theta = p / rho are FC-differentiated (theta in
+   * place of E; along the wall-normal lines its continuation is the Neumann expansion,
+   * the wall overwrite having put the Neumann end data's value at the wall), the x and y
+   * derivatives of p = rho theta (eq. p_T) and E (eq. perfect_gas_T) follow from them by
+   * the sum and product rules, the convective divergence div f(e) is formed from these
+   * derivatives by the same rules, and the viscous fluxes mu grad e, with grad E from the
+   * product rule, are FC-differentiated as elsewhere. Patches without an adiabatic side
+   * keep the flux form. With 1, an AFFINE patch with an ADIABATIC side is FC_ERR_INVALID
+   * at init, and fc_adjoint_step returns FC_ERR_UNIMPLEMENTED when some patch uses the
+   * product-rule form. Other values: FC_ERR_INVALID. */
+  int wall_form;
 } fc_params;
 
 /* fc_rk_step flags */

@@ -174,6 +174,7 @@ struct fc_ctx {
   WallPt* d_walls = nullptr;  // no-slip adiabatic wall points (of the owned patches, when sharded)
   int nwalls = 0;
   bool any_walls = false;  // the workload has adiabatic walls (the same on every rank)
+  bool any_pform = false;  // some patch uses the product-rule form (fc_params.wall_form)
   Recv* d_recv = nullptr;  // receivers interpolated from 3 x 3 donor stencils
   int nrecv = 0;
   PtCopy* d_rcopy = nullptr;  // receivers that copy a coincident donor point
@@ -1017,6 +1018,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   if (!prm->sdnn_w || prm->sdnn_len != SDNN_H * 7 + SDNN_H + SDNN_H * SDNN_H + SDNN_H + 4 * SDNN_H + 4)
     return bad("SDNN weights missing or of the wrong size");
   if (prm->win_r < 1 || prm->win_r > 32 || prm->n_f < 1 || prm->n_v < 1 || prm->depth_cap < 2) return bad("bad params");
+  if (prm->wall_form != 0 && prm->wall_form != 1) return bad("wall_form must be 0 or 1");
   c->sdnn.assign(prm->sdnn_w, prm->sdnn_w + prm->sdnn_len);
   if (prm->freestream[0] > 0.0) {  // d e_fs / d(M, alpha) at fixed rho and p (eq. mach_flow_ic)
     const double rho = prm->freestream[0], u = prm->freestream[1], v = prm->freestream[2];
@@ -1531,7 +1533,13 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   std::vector<PatchDev> pdev(npatch);
   for (int p = 0; p < npatch; ++p) {
     const HPatch& h = c->hp[p];
-    pdev[p] = PatchDev{h.off, h.gbase, h.n1, h.n2, h.d.kind, h.periodic1 ? 1 : 0, h.hhat, h.htil};
+    bool wall = false;
+    for (int sd = 0; sd < 4; ++sd) wall = wall || h.d.side[sd] == FC_SIDE_ADIABATIC;
+    const int pform = prm->wall_form == 1 && wall ? 1 : 0;
+    if (pform && h.d.kind == FC_PATCH_AFFINE)
+      return bad("the product-rule wall form needs adiabatic walls on OGRID or GRID patches");
+    c->any_pform = c->any_pform || pform;
+    pdev[p] = PatchDev{h.off, h.gbase, h.n1, h.n2, h.d.kind, h.periodic1 ? 1 : 0, h.hhat, h.htil, pform, 0};
   }
   const std::vector<double> Rv(prm->R, prm->R + 4);
   for (const Plan& pl : B.plans)
@@ -2376,6 +2384,7 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
                           double* lam_n, double* gbc, double* dparam, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
+  if (c->any_pform) return fail(c, FC_ERR_UNIMPLEMENTED, "adjoint of the product-rule wall form");
   cudaStream_t st = (cudaStream_t)stream;
   if (dparam && !c->d_bcacc && c->nbc > 0) {
     if (!c->alloc(&c->d_bcacc, 2 * (size_t)c->nbc)) return FC_ERR_OOM;

@@ -57,6 +57,8 @@ struct PatchDev {
   long long gbase;  // first index in the curvilinear scratch (-1 for affine)
   int n1, n2, kind, periodic1;
   double hhat, htil;
+  int pform;        // 1: the product-rule form of the operator (adiabatic wall patch, fc_params.wall_form)
+  int pad;
 };
 
 // Receiver of the inter-patch exchange: 3x3 donor stencil, iterated quadratic weights.

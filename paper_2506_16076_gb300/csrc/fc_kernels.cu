@@ -94,6 +94,39 @@ __device__ __forceinline__ void flux_y(double r, double mx, double my, double E,
   f[3] = v * (E + p);
 }
 
+// ---- product-rule form on adiabatic wall patches (Remark adiabatic)
+// Derivatives along one direction of e = (rho, rho u, rho v, E) and of p from those of
+// Q = (rho, rho u, rho v, theta): dp = theta drho + rho dtheta (eq. p_T),
+// dE = dp / (gamma - 1) + u d(rho u) + v d(rho v) - (u^2 + v^2) / 2 drho (eq. perfect_gas_T).
+__device__ __forceinline__ void product_rule(const double* Q, const double* DQ, double gm1, double* De, double& Dp) {
+  const double ir = 1.0 / Q[0];
+  const double u = Q[1] * ir, v = Q[2] * ir;
+  Dp = fma(Q[3], DQ[0], Q[0] * DQ[3]);
+  De[0] = DQ[0];
+  De[1] = DQ[1];
+  De[2] = DQ[2];
+  De[3] = fma(-0.5 * fma(u, u, v * v), DQ[0], fma(u, DQ[1], fma(v, DQ[2], Dp / gm1)));
+}
+
+// div f(e) (eq. euler 2d equation) by the sum and product rules from the x and y derivatives
+// of e (ex, ey) and p (px, py); theta = p / rho; du = (d(rho u) - u drho) / rho
+__device__ __forceinline__ void conv_div_product(const double* e, double th, const double* ex, double px,
+                                                 const double* ey, double py, double* out) {
+  const double ir = 1.0 / e[0];
+  const double u = e[1] * ir, v = e[2] * ir, p = e[0] * th;
+  const double ux = (ex[1] - u * ex[0]) * ir, vy = (ey[2] - v * ey[0]) * ir;
+  out[0] = ex[1] + ey[2];
+  out[1] = fma(u, ex[1], fma(e[1], ux, px)) + fma(v, ey[1], e[1] * vy);
+  out[2] = fma(u, ex[2], e[2] * ux) + fma(v, ey[2], fma(e[2], vy, py));
+  out[3] = fma(e[3] + p, ux + vy, fma(u, ex[3] + px, v * (ey[3] + py)));
+}
+
+// theta = p / rho (eq. p_T)
+__device__ __forceinline__ double theta_of(double r, double mx, double my, double E, double gam) {
+  const Prim q = primitives(r, mx, my, E, gam);
+  return q.p / r;
+}
+
 // Load 4 state components of a line into two packed complex sequences.
 __device__ __forceinline__ void load4(double2* A, int L, const Job& J, const double* __restrict__ src, long long cs,
                                       int lane) {
@@ -101,6 +134,17 @@ __device__ __forceinline__ void load4(double2* A, int L, const Job& J, const dou
     const long long p = J.base + (long long)t * J.stride;
     A[t] = cpx(src[p], src[p + cs]);
     A[L + t] = cpx(src[p + 2 * cs], src[p + 3 * cs]);
+  }
+}
+
+// The same with theta in place of E (the product-rule form's differentiated quantities).
+__device__ __forceinline__ void load4_theta(double2* A, int L, const Job& J, const double* __restrict__ e,
+                                            long long cs, double gam, int lane) {
+  for (int t = lane; t < J.n; t += 32) {
+    const long long p = J.base + (long long)t * J.stride;
+    const double r = e[p], mx = e[p + cs], my = e[p + 2 * cs];
+    A[t] = cpx(r, mx);
+    A[L + t] = cpx(my, theta_of(r, mx, my, e[p + 3 * cs], gam));
   }
 }
 
@@ -376,7 +420,7 @@ __device__ __forceinline__ const double* gslot(const double* G, long long Pg, in
   return G + (4 * slot + c) * Pg;
 }
 
-// pass A: D1e = d/dq1 e
+// pass A: D1e = d/dq1 e (product-rule form: d/dq1 of (rho, rho u, rho v, theta))
 __global__ void LINE_KERNEL_BOUNDS k_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                       const double* __restrict__ e, double* __restrict__ G) {
   extern __shared__ double2 sm[];
@@ -385,7 +429,10 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_A(DevTables T, const Job* __restrict__ 
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
-    load4(A, P.L, J, e, T.P, lane);
+    if (T.patches[J.patch].pform)
+      load4_theta(A, P.L, J, e, T.P, T.gamma, lane);
+    else
+      load4(A, P.L, J, e, T.P, lane);
     deriv2(A, Lmax, J, P, T, lane);
     double2* X = A;
     for (int t = lane; t < J.n; t += 32) {
@@ -400,7 +447,10 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_A(DevTables T, const Job* __restrict__ 
 }
 
 // pass B: D2e; grad_x e = J1x D1 + J2x D2, grad_y e = J1y D1 + J2y D2; H_x, H_y;
-// R2 = J2x d/dq2 H_x + J2y d/dq2 H_y
+// R2 = J2x d/dq2 H_x + J2y d/dq2 H_y.
+// Product-rule form (adiabatic wall patches, Remark adiabatic): D1, D2 of (rho, rho u,
+// rho v, theta); grad e and grad p by the product rules; H = -mu grad e (viscous flux
+// only); R2 = div f(e) (from the product rules) + J2x d/dq2 H_x + J2y d/dq2 H_y.
 __global__ void LINE_KERNEL_BOUNDS k_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                       const double* __restrict__ e, const double* __restrict__ mu,
                                                       const double* __restrict__ Jm, double* __restrict__ G) {
@@ -412,7 +462,11 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_B(DevTables T, const Job* __restrict__ 
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
-    load4(A, L, J, e, cs, lane);
+    const bool pf = T.patches[J.patch].pform != 0;
+    if (pf)
+      load4_theta(A, L, J, e, cs, T.gamma, lane);
+    else
+      load4(A, L, J, e, cs, lane);
     deriv2(A, Lmax, J, P, T, lane);
     double2* X = A;
     double2* Y = A;
@@ -421,19 +475,43 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_B(DevTables T, const Job* __restrict__ 
       const long long g = J.gbase + (long long)t * J.stride;
       const double j1x = Jm[g], j1y = Jm[g + Pg], j2x = Jm[g + 2 * Pg], j2y = Jm[g + 3 * Pg];
       const double d2[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
-      double fx[4], fy[4];
-      flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, fx, fy);
       const double m = mu[p];
       double hx[4], hy[4];
+      if (pf) {
+        const double e4[4] = {e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs]};
+        const double th = theta_of(e4[0], e4[1], e4[2], e4[3], T.gamma);
+        const double Q[4] = {e4[0], e4[1], e4[2], th};
+        double qx[4], qy[4], ex[4], ey[4], px, py, div[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const double d1 = gslot(G, Pg, 0, c)[g];
-        const double gx = fma(j1x, d1, j2x * d2[c]);
-        const double gy = fma(j1y, d1, j2y * d2[c]);
-        hx[c] = fma(-m, gx, fx[c]);
-        hy[c] = fma(-m, gy, fy[c]);
-        gslot(G, Pg, 1, c)[g] = hx[c];
-        gslot(G, Pg, 2, c)[g] = hy[c];
+        for (int c = 0; c < 4; ++c) {
+          const double d1 = gslot(G, Pg, 0, c)[g];
+          qx[c] = fma(j1x, d1, j2x * d2[c]);
+          qy[c] = fma(j1y, d1, j2y * d2[c]);
+        }
+        product_rule(Q, qx, T.gamma - 1.0, ex, px);
+        product_rule(Q, qy, T.gamma - 1.0, ey, py);
+        conv_div_product(e4, th, ex, px, ey, py, div);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          hx[c] = -m * ex[c];
+          hy[c] = -m * ey[c];
+          gslot(G, Pg, 1, c)[g] = hx[c];
+          gslot(G, Pg, 2, c)[g] = hy[c];
+          gslot(G, Pg, 3, c)[g] = div[c];
+        }
+      } else {
+        double fx[4], fy[4];
+        flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, fx, fy);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double d1 = gslot(G, Pg, 0, c)[g];
+          const double gx = fma(j1x, d1, j2x * d2[c]);
+          const double gy = fma(j1y, d1, j2y * d2[c]);
+          hx[c] = fma(-m, gx, fx[c]);
+          hy[c] = fma(-m, gy, fy[c]);
+          gslot(G, Pg, 1, c)[g] = hx[c];
+          gslot(G, Pg, 2, c)[g] = hy[c];
+        }
       }
       Y[t] = cpx(hx[0], hx[1]);
       Y[L + t] = cpx(hx[2], hx[3]);
@@ -444,10 +522,21 @@ __global__ void LINE_KERNEL_BOUNDS k_gen_B(DevTables T, const Job* __restrict__ 
     for (int t = lane; t < J.n; t += 32) {
       const long long g = J.gbase + (long long)t * J.stride;
       const double j2x = Jm[g + 2 * Pg];
-      gslot(G, Pg, 3, 0)[g] = j2x * Z[t].x;
-      gslot(G, Pg, 3, 1)[g] = j2x * Z[t].y;
-      gslot(G, Pg, 3, 2)[g] = j2x * Z[L + t].x;
-      gslot(G, Pg, 3, 3)[g] = j2x * Z[L + t].y;
+      if (pf) {
+        double* r = gslot(G, Pg, 3, 0);
+        r[g] = fma(j2x, Z[t].x, r[g]);
+        r = gslot(G, Pg, 3, 1);
+        r[g] = fma(j2x, Z[t].y, r[g]);
+        r = gslot(G, Pg, 3, 2);
+        r[g] = fma(j2x, Z[L + t].x, r[g]);
+        r = gslot(G, Pg, 3, 3);
+        r[g] = fma(j2x, Z[L + t].y, r[g]);
+      } else {
+        gslot(G, Pg, 3, 0)[g] = j2x * Z[t].x;
+        gslot(G, Pg, 3, 1)[g] = j2x * Z[t].y;
+        gslot(G, Pg, 3, 2)[g] = j2x * Z[L + t].x;
+        gslot(G, Pg, 3, 3)[g] = j2x * Z[L + t].y;
+      }
       W[t] = cpx(gslot(G, Pg, 2, 0)[g], gslot(G, Pg, 2, 1)[g]);
       W[L + t] = cpx(gslot(G, Pg, 2, 2)[g], gslot(G, Pg, 2, 3)[g]);
     }
@@ -534,9 +623,30 @@ __global__ void k_gen_fix(DevTables T, const GFix* __restrict__ f, int n, const 
     for (int c = 0; c < 4; ++c) gslot(G, Pg, 0, c)[g] = 0.0;
     return;
   }
+  const double m = mu[p], j1x = Jm[g], j1y = Jm[g + Pg];
+  if (T.patches[pt_patch(T.info[p])].pform) {
+    // product-rule form: the viscous flux alone, grad E from the product rule (the point's
+    // own L is 0, so its convective divergence is not needed)
+    const double th = theta_of(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma);
+    const double Q[4] = {e[p], e[p + cs], e[p + 2 * cs], th};
+    double qx[4], qy[4], ex[4], ey[4], px, py;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double d1 = gslot(G, Pg, 0, c)[g];
+      qx[c] = fma(j1x, d1, 0.0);
+      qy[c] = fma(j1y, d1, 0.0);
+    }
+    product_rule(Q, qx, T.gamma - 1.0, ex, px);
+    product_rule(Q, qy, T.gamma - 1.0, ey, py);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      gslot(G, Pg, 1, c)[g] = -m * ex[c];
+      gslot(G, Pg, 2, c)[g] = -m * ey[c];
+    }
+    return;
+  }
   double fx[4], fy[4];
   flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, fx, fy);
-  const double m = mu[p], j1x = Jm[g], j1y = Jm[g + Pg];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const double d1 = gslot(G, Pg, 0, c)[g];
@@ -700,10 +810,6 @@ __global__ void k_scatter(const int* __restrict__ idx, int n, const double* __re
 }
 
 // ---------------------------------------------------------------- per-step filter (Sec. 4.3.1)
-__device__ __forceinline__ double theta_of(double r, double mx, double my, double E, double gam) {
-  const Prim q = primitives(r, mx, my, E, gam);
-  return q.p / r;
-}
 __device__ __forceinline__ double energy_of(double r, double mx, double my, double th, double gam) {
   return r * th / (gam - 1.0) + 0.5 * (mx * mx + my * my) / r;
 }

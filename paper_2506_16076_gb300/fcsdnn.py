@@ -49,7 +49,8 @@ class ParamsC(C.Structure):
                 ("alpha_f", C.c_double), ("p_f", C.c_int), ("cfl", C.c_double), ("n_f", C.c_int),
                 ("n_v", C.c_int), ("win_r", C.c_int), ("loc", C.c_int), ("R", C.c_double * 4),
                 ("depth_cap", C.c_int), ("fc_tables", C.POINTER(C.c_double)), ("fc_tables_len", C.c_int),
-                ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int), ("freestream", C.c_double * 4)]
+                ("sdnn_w", C.POINTER(C.c_float)), ("sdnn_len", C.c_int), ("freestream", C.c_double * 4),
+                ("wall_form", C.c_int)]
 
 
 # fc_comm_fn: (user, op, send_dev, send_counts, recv_dev, recv_counts, stream) -> int
@@ -247,6 +248,7 @@ class Context:
         P.sdnn_len = len(self._sd)
         for m in range(4):
             P.freestream[m] = workload.freestream[m]
+        P.wall_form = getattr(prm, "wall_form", 0)
         ctx = C.c_void_p()
         st = lib.fc_init_patches(C.byref(ctx), descs, n, C.byref(P), None)
         if st != FC_OK:
