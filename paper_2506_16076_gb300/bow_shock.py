@@ -10,6 +10,7 @@ paper validates against (Sec. 7, eq. cylinder_bow).
 
   python -m paper_2506_16076_gb300.bow_shock --mach 3 --steps 40000 --report-every 5000
   python -m paper_2506_16076_gb300.bow_shock --workload cyl_m25_32 --steps 8000 --report-every 1000
+  python -m paper_2506_16076_gb300.bow_shock --mach 25 --wall-form product --steps 60000
 
 A uniform hypersonic stream switched on against the no-slip wall loses positivity in the
 first filtered steps, so from Mach 10 on (or with --potential-start) the run starts as
@@ -74,6 +75,9 @@ def main():
                     help="start from the potential flow with a no-slip wall layer (default from Mach 10 on)")
     ap.add_argument("--d", type=int, default=None,
                     help="FC order d of the continuation (the paper uses d = 2 throughout; default: the workload's)")
+    ap.add_argument("--wall-form", choices=["flux", "product"], default="flux",
+                    help="operator on the wall patch: the flux form, or the product-rule form of Remark adiabatic "
+                         "(fc_params.wall_form = 1)")
     ap.add_argument("--workload", default=None,
                     help="a named workload with an O-grid around the cylinder (e.g. cyl_m25_32) instead of the "
                          "Mach-M cylinder on the 4 x 4 array")
@@ -89,6 +93,8 @@ def main():
         w = workload(args.mach, args.potential_start or args.mach >= 10.0)
     if args.d is not None:
         w = dataclasses.replace(w, params=dataclasses.replace(w.params, d=args.d))
+    if args.wall_form == "product":
+        w = dataclasses.replace(w, params=dataclasses.replace(w.params, wall_form=1))
     og = w.patches[0]
     assert og.kind == W.OGRID
     xc, yc, r0, r1 = og.geom
