@@ -70,10 +70,9 @@ def d2T(sv, g, G):
 
 
 def rhs_adjoint_patch(sv, g, u, mu, lam):
-    """L'(u)^T lam on one patch (the flux form; the product-rule form of wall patches has
-    no adjoint here)."""
+    """L'(u)^T lam on one patch."""
     if sv.product_form(g):
-        raise NotImplementedError("adjoint of the product-rule form at adiabatic walls")
+        return rhs_adjoint_patch_product(sv, g, u, mu, lam)
     J1x, J1y, J2x, J2y = g.J
     lm = np.where(g.nodiff[None], 0.0, lam)
     eta_x = -(d1T(sv, g, J1x * lm) + d2T(sv, g, J2x * lm))
@@ -83,6 +82,41 @@ def rhs_adjoint_patch(sv, g, u, mu, lam):
     out -= d1T(sv, g, mu * (J1x * eta_x + J1y * eta_y))
     out -= d2T(sv, g, mu * (J2x * eta_x + J2y * eta_y))
     return out
+
+
+def rhs_adjoint_patch_product(sv, g, u, mu, lam, h=1e-30):
+    """L'(u)^T lam on a patch in the product-rule form (Remark adiabatic):
+        L(u) = -N ( c(u, Qx, Qy) + sum_k sum_i J_ki D_k H_i(u, Qx, Qy) ),
+        Qx = sum_k J_kx D_k Q(u),  Qy = sum_k J_ky D_k Q(u),
+    with Q = (rho, rho u, rho v, theta) and (c, H_x, H_y) the pointwise map of
+    solver.wall_pointwise. Transposed in reverse order: eta_i = -sum_k D_k^T (J_ki N lam)
+    are the adjoints of H_i and -N lam that of c; the transpose of the pointwise map's
+    Jacobian (its 12 columns by the complex step, exact to rounding for this analytic
+    map) gives the adjoints of u, Qx and Qy; Qbar = sum_k D_k^T (sum_i J_ki Qbar_i); and
+    the Jacobian of Q(u) carries Qbar back to u."""
+    from .solver import wall_pointwise, wall_quantities
+    gam = sv.prm.gamma
+    J1x, J1y, J2x, J2y = g.J
+    lm = np.where(g.nodiff[None], 0.0, lam)
+    eta_x = -(d1T(sv, g, J1x * lm) + d2T(sv, g, J2x * lm))
+    eta_y = -(d1T(sv, g, J1y * lm) + d2T(sv, g, J2y * lm))
+    Q = wall_quantities(u, gam)
+    D1, D2 = sv.d1(g, Q), sv.d2(g, Q)
+    inp = np.concatenate([u, J1x * D1 + J2x * D2, J1y * D1 + J2y * D2]).astype(complex)
+    wbar = np.concatenate([-lm, eta_x, eta_y])  # adjoints of the outputs (c, H_x, H_y)
+    bar = np.zeros(inp.shape)
+    for j in range(12):
+        z = inp.copy()
+        z[j] += 1j * h
+        out = np.concatenate(wall_pointwise(z[:4], z[4:8], z[8:], mu, gam))
+        bar[j] = np.sum(wbar * (out.imag / h), axis=0)
+    ubar, qxbar, qybar = bar[:4], bar[4:8], bar[8:]
+    Qbar = d1T(sv, g, J1x * qxbar + J1y * qybar) + d2T(sv, g, J2x * qxbar + J2y * qybar)
+    for j in range(4):  # dQ/du: identity on rho, rho u, rho v; d theta / d u_j
+        z = u.astype(complex)
+        z[j] += 1j * h
+        ubar[j] += (Qbar[j] if j < 3 else 0.0) + (wall_quantities(z, gam)[3].imag / h) * Qbar[3]
+    return ubar
 
 
 def rhs_adjoint(sv, states, mus, lams):

@@ -131,15 +131,11 @@ class Solver:
             L = -( div f(e) - sum_k sum_i J_ki d/dq^k (mu sum_m J_mi d/dq^m e) )."""
         gam = self.prm.gamma
         J1x, J1y, J2x, J2y = g.J
-        th = euler.temperature(e, gam)
-        Q = np.stack([e[0], e[1], e[2], th])
+        Q = wall_quantities(e, gam)
         D1, D2 = self.d1(g, Q), self.d2(g, Q)
-        ex, px = euler.product_rule_derivatives(Q, J1x * D1 + J2x * D2, gam)
-        ey, py = euler.product_rule_derivatives(Q, J1y * D1 + J2y * D2, gam)
-        conv = euler.flux_divergence_product(e, th, ex, px, ey, py)
-        Vx, Vy = mu * ex, mu * ey
-        visc = J1x * self.d1(g, Vx) + J1y * self.d1(g, Vy) + J2x * self.d2(g, Vx) + J2y * self.d2(g, Vy)
-        return np.where(g.nodiff[None], 0.0, -(conv - visc))
+        conv, Hx, Hy = wall_pointwise(e, J1x * D1 + J2x * D2, J1y * D1 + J2y * D2, mu, gam)
+        L = -(conv + J1x * self.d1(g, Hx) + J1y * self.d1(g, Hy) + J2x * self.d2(g, Hx) + J2y * self.d2(g, Hy))
+        return np.where(g.nodiff[None], 0.0, L)
 
     def rhs(self, states, mus):
         return [self.rhs_patch(g, e, m) for g, e, m in zip(self.geos, states, mus)]
@@ -256,6 +252,23 @@ class Solver:
             states = self.step(states, n, **kw)
             dts.append(self.last_dt)
         return states, dts
+
+
+def wall_quantities(e, gam):
+    """Q = (rho, rho u, rho v, theta): the FC-differentiated quantities of the product-rule
+    form (Remark adiabatic), theta = p / rho (eq. p_T)."""
+    return np.stack([e[0], e[1], e[2], euler.temperature(e, gam)])
+
+
+def wall_pointwise(e, Qx, Qy, mu, gam):
+    """The pointwise part of the product-rule form (Remark adiabatic) from the state e and
+    the x and y derivatives Qx, Qy of Q = (rho, rho u, rho v, theta): the convective
+    divergence div f(e) and the viscous fluxes H_x = -mu d/dx e, H_y = -mu d/dy e, the
+    derivatives of E and p by the sum and product rules."""
+    Q = wall_quantities(e, gam)
+    ex, px = euler.product_rule_derivatives(Q, Qx, gam)
+    ey, py = euler.product_rule_derivatives(Q, Qy, gam)
+    return euler.flux_divergence_product(e, Q[3], ex, px, ey, py), -mu * ex, -mu * ey
 
 
 def _side_slice(s):

@@ -14,12 +14,17 @@ What fixes each result independently of the oracle's code:
   E); a dropped term, a flipped sign or exchanged directions leaves an error of 1.6e-2
   (the kinetic term of dE) to O(1), and three such mistakes planted in the oracle are
   caught;
-- a uniform state gives L = 0, and patches without an adiabatic side are unchanged.
+- a uniform state gives L = 0, and patches without an adiabatic side are unchanged;
+- its transpose (the discrete adjoint) satisfies the dot-product identity against
+  complex-step directional derivatives of the forward operator and of a whole filtered
+  step, on the O-grid, the curved GRID annulus and the S-type arcs.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
-from oracle import euler, solver as S
+from oracle import adjoint as A, euler, solver as S
 from paper_2506_16076_gb300 import workloads as W
 
 sp = pytest.importorskip("sympy")
@@ -168,3 +173,41 @@ def test_uniform_state_and_patches_without_walls():
     mu2 = _ev(m["mu"], a.geos[0].x, a.geos[0].y)
     assert np.array_equal(a.rhs_patch(a.geos[0], e2, mu2), b.rhs_patch(b.geos[0], e2, mu2))
     assert sv1.product_form(g) and not a.product_form(a.geos[0])
+
+
+def _dot(a, b):
+    return sum(float(np.vdot(x, y).real) for x, y in zip(a, b))
+
+
+@pytest.fixture(scope="module", params=["ogrid", "grid_curved", "s_type"])
+def wall_case(request):
+    w = {"ogrid": lambda: W.small_multipatch(W.ADIABATIC), "grid_curved": W.small_multipatch_grid,
+         "s_type": W.small_multipatch_stype}[request.param]()
+    w = dataclasses.replace(w, params=dataclasses.replace(w.params, wall_form=1))
+    sv = S.Solver(w)
+    st = sv.project(W.random_smooth_state(w, seed=7, amp=0.05))
+    mu = [0.002 * (1 + np.cos(g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    return sv, st, mu
+
+
+def _rand(states, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.normal(size=a.shape) for a in states]
+
+
+def test_rhs_adjoint_dot_product(wall_case):
+    sv, st, mu = wall_case
+    assert any(sv.product_form(g) for g in sv.geos)
+    v, lam = _rand(st, 1), _rand(st, 2)
+    lhs = _dot(A.rhs_jvp_complex(sv, st, mu, v), lam)
+    rhs = _dot(v, A.rhs_adjoint(sv, st, mu, lam))
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs), (lhs, rhs)
+
+
+def test_step_adjoint_with_filter_dot_product(wall_case):
+    sv, st, mu = wall_case
+    dt = 0.5 * sv.dt(st, mu)
+    v, lam = _rand(st, 3), _rand(st, 4)
+    lhs = _dot(A.step_jvp_complex(sv, st, mu, dt, v, filt=True), lam)
+    rhs = _dot(v, A.step_adjoint(sv, st, mu, dt, lam, filt=True)[0])
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (lhs, rhs)
