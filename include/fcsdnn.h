@@ -136,8 +136,8 @@ typedef struct {
    * derivatives by the same rules, and the viscous fluxes mu grad e, with grad E from the
    * product rule, are FC-differentiated as elsewhere. Patches without an adiabatic side
    * keep the flux form. With 1, an AFFINE patch with an ADIABATIC side is FC_ERR_INVALID
-   * at init, and fc_adjoint_step returns FC_ERR_UNIMPLEMENTED when some patch uses the
-   * product-rule form. Other values: FC_ERR_INVALID. */
+   * at init; fc_adjoint_step transposes whichever form each patch uses. Other values:
+   * FC_ERR_INVALID. */
   int wall_form;
 } fc_params;
 

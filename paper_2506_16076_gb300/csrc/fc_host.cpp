@@ -174,7 +174,6 @@ struct fc_ctx {
   WallPt* d_walls = nullptr;  // no-slip adiabatic wall points (of the owned patches, when sharded)
   int nwalls = 0;
   bool any_walls = false;  // the workload has adiabatic walls (the same on every rank)
-  bool any_pform = false;  // some patch uses the product-rule form (fc_params.wall_form)
   Recv* d_recv = nullptr;  // receivers interpolated from 3 x 3 donor stencils
   int nrecv = 0;
   PtCopy* d_rcopy = nullptr;  // receivers that copy a coincident donor point
@@ -1531,6 +1530,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   make_queue(c, c->q_filt1, jf1, B.plans, npatch, ok);
   make_queue(c, c->q_filt2, jf2, B.plans, npatch, ok);
   std::vector<PatchDev> pdev(npatch);
+  bool any_pform = false;
   for (int p = 0; p < npatch; ++p) {
     const HPatch& h = c->hp[p];
     bool wall = false;
@@ -1538,7 +1538,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     const int pform = prm->wall_form == 1 && wall ? 1 : 0;
     if (pform && h.d.kind == FC_PATCH_AFFINE)
       return bad("the product-rule wall form needs adiabatic walls on OGRID or GRID patches");
-    c->any_pform = c->any_pform || pform;
+    any_pform = any_pform || pform;
     pdev[p] = PatchDev{h.off, h.gbase, h.n1, h.n2, h.d.kind, h.periodic1 ? 1 : 0, h.hhat, h.htil, pform, 0};
   }
   const std::vector<double> Rv(prm->R, prm->R + 4);
@@ -1611,6 +1611,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   T.Pg = std::max<long long>(c->Pg, 1);
   T.gamma = prm->gamma;
   T.d = prm->d;
+  T.any_pform = any_pform ? 1 : 0;
   set_kernel_attributes();
   if (!mpts.empty()) {  // metrics of GRID patches given by their points only
     std::vector<double> xy(2 * (size_t)c->P, 0.0);
@@ -1943,9 +1944,9 @@ void adj_stage(fc_ctx* c, const double* u, const double* mu, const double* psi, 
   const DevTables& T = c->T;
   cudaMemsetAsync(c->d_R1, 0, sizeof(double) * 4 * (size_t)c->P, st);
   run_queue(c, c->q_gen1, false, st, "adj_gen_A",
-            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_A(T, j, n, L, c->d_J, psi, c->d_G, s); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_A(T, j, n, L, c->d_J, u, psi, c->d_G, s); });
   if (c->ngfix) {
-    launch_adj_gen_fixA(T, c->d_gfix, c->ngfix, c->d_J, u, mu, c->d_G, st);
+    launch_adj_gen_fixA(T, c->d_gfix, c->ngfix, c->d_J, u, mu, psi, c->d_G, st);
     c->launches++;
   }
   run_queue(c, c->q_cart1, false, st, "adj_cart_q1",
@@ -1959,7 +1960,7 @@ void adj_stage(fc_ctx* c, const double* u, const double* mu, const double* psi, 
   run_queue(c, c->q_cart2, false, st, "adj_cart_q2",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_cart(T, j, n, L, 1, u, mu, psi, c->d_R1, acc, dt, s); });
   run_queue(c, c->q_gen1, false, st, "adj_gen_C",
-            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_C(T, j, n, L, c->d_G, acc, dt, s); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_adj_gen_C(T, j, n, L, u, c->d_G, acc, dt, s); });
   if (c->nfix) {
     launch_adj_fixup(c->d_fix, c->nfix, c->d_R1, acc, c->P, dt, st);
     c->launches++;
@@ -2384,7 +2385,6 @@ fc_status fc_adjoint_step(fc_ctx* c, const double* e_n, const double* mu, const 
                           double* lam_n, double* gbc, double* dparam, int flags, void* stream) {
   if (!c || !e_n || !mu || !dt || !lam_np1 || !lam_n) return FC_ERR_INVALID;
   if (dparam && !c->has_fs) return fail(c, FC_ERR_INVALID, "dparam needs fc_params.freestream");
-  if (c->any_pform) return fail(c, FC_ERR_UNIMPLEMENTED, "adjoint of the product-rule wall form");
   cudaStream_t st = (cudaStream_t)stream;
   if (dparam && !c->d_bcacc && c->nbc > 0) {
     if (!c->alloc(&c->d_bcacc, 2 * (size_t)c->nbc)) return FC_ERR_OOM;

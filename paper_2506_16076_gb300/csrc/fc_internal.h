@@ -137,6 +137,8 @@ struct DevTables {
   int lw[NCLASS];
   // sharded execution: 1 for the patches this rank owns (null: all patches are owned)
   const uint8_t* owned;
+  // 1 when some patch uses the product-rule wall form (fc_params.wall_form)
+  int any_pform;
 };
 
 // ---- launch wrappers (fc_kernels.cu) ----
@@ -153,7 +155,7 @@ void launch_rk_fixup(const DevTables& T, const int* idx, int n, const StageCoef&
 void launch_gen_fix(const DevTables& T, const GFix* f, int n, const double* e, const double* mu, const double* J,
                     double* G, cudaStream_t st);
 void launch_adj_gen_fixA(const DevTables& T, const GFix* f, int n, const double* J, const double* u,
-                         const double* mu, double* G, cudaStream_t st);
+                         const double* mu, const double* psi, double* G, cudaStream_t st);
 void launch_adj_gen_fixB(const DevTables& T, const GFix* f, int n, const double* G, double* R1, cudaStream_t st);
 void launch_bc(const BcPt* bc, int n, double* e, long long P, cudaStream_t st);
 void launch_bc_wall(const WallPt* w, int n, double* e, long long P, double gamma, cudaStream_t st);
@@ -194,12 +196,12 @@ void launch_dt(const DevTables& T, const double* e, const double* mu, unsigned l
 void launch_check_state(const DevTables& T, const double* e, int* flag, cudaStream_t st);
 void launch_adj_cart(const DevTables& T, const Job* jobs, int njobs, int Lmax, int dir, const double* u,
                      const double* mu, const double* psi, double* R1, double* acc, const double* dt, cudaStream_t st);
-void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* psi,
-                      double* G, cudaStream_t st);
+void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
+                      const double* psi, double* G, cudaStream_t st);
 void launch_adj_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
                       const double* mu, const double* psi, double* G, cudaStream_t st);
-void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* G, double* acc,
-                      const double* dt, cudaStream_t st);
+void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* u, const double* G,
+                      double* acc, const double* dt, cudaStream_t st);
 void launch_adj_fixup(const int* idx, int n, const double* R1, double* acc, long long P, const double* dt,
                       cudaStream_t st);
 void launch_exchange_T(const int* dptr, const int* dsrc, const int* drecv, const double* dw, int nd, const Recv* r,

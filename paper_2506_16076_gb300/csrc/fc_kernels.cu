@@ -1216,6 +1216,124 @@ __device__ __forceinline__ double2* line2T(double2* A, const Job& J, const Plan&
   return X;
 }
 
+// ---- transpose of the product-rule wall form's pointwise map (Remark adiabatic)
+// Forward-mode dual number: value and derivative along one input direction.
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, fma(a.v, b.d, a.d * b.v)}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual inv(Dual a) {
+  const double r = 1.0 / a.v;
+  return {r, -a.d * r * r};
+}
+
+// The pointwise map of the product-rule form at one point: from the state u and the x and
+// y derivatives gx, gy of Q = (rho, rho u, rho v, theta) to out = (div f(e), H_x, H_y),
+// H = -mu grad e, with grad p = theta grad rho + rho grad theta (eq. p_T) and
+// grad E = grad p / (gamma - 1) + u grad(rho u) + v grad(rho v) - (u^2 + v^2) / 2 grad rho
+// (eq. perfect_gas_T); written once for the dual numbers of its transpose.
+__device__ __forceinline__ void wall_point(const Dual* u, const Dual* gx, const Dual* gy, double mu, double gam,
+                                           Dual* out) {
+  const Dual ir = inv(u[0]);
+  const Dual U = u[1] * ir, V = u[2] * ir;
+  const Dual p = (gam - 1.0) * (u[3] - 0.5 * (u[1] * U + u[2] * V));
+  const Dual th = p * ir;
+  const Dual k = 0.5 * (U * U + V * V);
+  Dual e[2][4], pd[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const Dual* g = i ? gy : gx;
+    pd[i] = th * g[0] + u[0] * g[3];
+    e[i][0] = g[0];
+    e[i][1] = g[1];
+    e[i][2] = g[2];
+    e[i][3] = (1.0 / (gam - 1.0)) * pd[i] + U * g[1] + V * g[2] - k * g[0];
+  }
+  const Dual ux = (e[0][1] - U * e[0][0]) * ir, vy = (e[1][2] - V * e[1][0]) * ir;
+  out[0] = e[0][1] + e[1][2];
+  out[1] = U * e[0][1] + u[1] * ux + pd[0] + V * e[1][1] + u[1] * vy;
+  out[2] = U * e[0][2] + u[2] * ux + V * e[1][2] + u[2] * vy + pd[1];
+  out[3] = (u[3] + p) * (ux + vy) + U * (e[0][3] + pd[0]) + V * (e[1][3] + pd[1]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    out[4 + c] = (-mu) * e[0][c];
+    out[8 + c] = (-mu) * e[1][c];
+  }
+}
+
+// Transpose of the pointwise map's Jacobian at (u, gx, gy) applied to the output adjoints
+// wbar (12): the adjoints of the 12 inputs, one forward-mode evaluation per input.
+__device__ __forceinline__ void wall_point_T(const double* u, const double* gx, const double* gy, double mu, double gam,
+                                             const double* wbar, double* ubar, double* gxbar, double* gybar) {
+#pragma unroll 1
+  for (int j = 0; j < 12; ++j) {
+    Dual a[4], bx[4], by[4], out[12];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a[c] = {u[c], j == c ? 1.0 : 0.0};
+      bx[c] = {gx[c], j == 4 + c ? 1.0 : 0.0};
+      by[c] = {gy[c], j == 8 + c ? 1.0 : 0.0};
+    }
+    wall_point(a, bx, by, mu, gam, out);
+    double s = 0.0;
+#pragma unroll
+    for (int o = 0; o < 12; ++o) s = fma(wbar[o], out[o].d, s);
+    if (j < 4)
+      ubar[j] = s;
+    else if (j < 8)
+      gxbar[j - 4] = s;
+    else
+      gybar[j - 8] = s;
+  }
+}
+
+// adjoint pass B of the product-rule form at one point: in: D_2 Q at *a, *b (packed), D_1 Q in slot 3, eta in slots 0
+// and 1; out: partial = ubar (slot 2), g1 = -(J1x gxbar + J1y gybar) (slot 3) and
+// g2 = -(J2x gxbar + J2y gybar) packed into *a, *b for its q2 transpose
+__device__ __forceinline__ void adj_wall_point_B(const DevTables& T, long long p, long long g, const double* Jm,
+                                              const double* u, const double* mu, const double* psi, double* G,
+                                              double2* a, double2* b) {
+  const long long cs = T.P, Pg = T.Pg;
+  const double j1x = Jm[g], j1y = Jm[g + Pg], j2x = Jm[g + 2 * Pg], j2y = Jm[g + 3 * Pg];
+  const double d2[4] = {a->x, a->y, b->x, b->y};
+  const bool nod = (T.info[p] & PT_NODIFF) != 0;
+  double u4[4], gx[4], gy[4], wbar[12], ub[4], gxb[4], gyb[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double d1 = gslot(G, Pg, 3, c)[g];
+    u4[c] = u[p + c * cs];
+    gx[c] = fma(j1x, d1, j2x * d2[c]);
+    gy[c] = fma(j1y, d1, j2y * d2[c]);
+    wbar[c] = nod ? 0.0 : -psi[p + c * cs];
+    wbar[4 + c] = gslot(G, Pg, 0, c)[g];
+    wbar[8 + c] = gslot(G, Pg, 1, c)[g];
+  }
+  wall_point_T(u4, gx, gy, mu[p], T.gamma, wbar, ub, gxb, gyb);
+  double g2[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    gslot(G, Pg, 2, c)[g] = ub[c];
+    gslot(G, Pg, 3, c)[g] = -fma(j1x, gxb[c], j1y * gyb[c]);
+    g2[c] = -fma(j2x, gxb[c], j2y * gyb[c]);
+  }
+  *a = cpx(g2[0], g2[1]);
+  *b = cpx(g2[2], g2[3]);
+}
+
+// (dQ/du)^T a for Q = (rho, rho u, rho v, theta), theta = (gamma - 1) (E / rho - |rho u|^2 / (2 rho^2))
+__device__ __forceinline__ void thetaT_add(const double* u, double gam, const double* a, double* out) {
+  const double ir = 1.0 / u[0], g1 = gam - 1.0;
+  const double m2 = fma(u[1], u[1], u[2] * u[2]);
+  out[0] += a[0] + a[3] * g1 * ir * ir * (m2 * ir - u[3]);
+  out[1] += a[1] - a[3] * g1 * u[1] * ir * ir;
+  out[2] += a[2] - a[3] * g1 * u[2] * ir * ir;
+  out[3] += a[3] * g1 * ir;
+}
+
 // A^T eta for the x (dir 0) or y (dir 1) flux Jacobian at state e (eq. euler 2d equation)
 __device__ __forceinline__ void fluxT(int dir, double r, double mx, double my, double E, double gam, const double* eta,
                                       double* out) {
@@ -1313,9 +1431,12 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_cart(DevTables T, const Job* __restrict
 }
 
 // curvilinear patches. scratch G slots: 0 = S1x then eta_x, 1 = S1y, 2 = partial, 3 = g1
+// (product-rule wall form: 3 = D_1 Q, the forward q1 derivative of Q = (rho, rho u, rho v,
+// theta) at the stage state, until pass B replaces it by g1)
 // pass A (q1): S1x = D_1^T(J1x N psi), S1y = D_1^T(J1y N psi)
 __global__ void LINE_KERNEL_BOUNDS k_adj_gen_A(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ Jm,
+                                                          const double* __restrict__ u,
                                                           const double* __restrict__ psi, double* __restrict__ G) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1343,11 +1464,51 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_A(DevTables T, const Job* __restric
       }
       FC_SYNC();
     }
+    if (T.patches[J.patch].pform) {
+      load4_theta(A, L, J, u, cs, T.gamma, lane);
+      deriv2(A, Lmax, J, P, T, lane);
+      for (int t = lane; t < J.n; t += 32) {
+        const long long g = J.gbase + (long long)t * J.stride;
+        gslot(G, Pg, 3, 0)[g] = A[t].x;
+        gslot(G, Pg, 3, 1)[g] = A[t].y;
+        gslot(G, Pg, 3, 2)[g] = A[L + t].x;
+        gslot(G, Pg, 3, 3)[g] = A[L + t].y;
+      }
+      FC_SYNC();
+    }
   }
 }
 
 // pass B (q2): eta_x = -(S1x + D_2^T(J2x N psi)), eta_y = -(S1y + D_2^T(J2y N psi));
 // partial = A_x^T eta_x + A_y^T eta_y - D_2^T(mu (J2x eta_x + J2y eta_y)); g1 = mu (J1x eta_x + J1y eta_y)
+// adjoint pass B, first part (q2 lines): eta_x = -(S1x + D_2^T(J2x N psi)),
+// eta_y = -(S1y + D_2^T(J2y N psi)) into slots 0 and 1
+__device__ __forceinline__ void adj_eta_q2(double2* A, int L, const Job& J, const Plan& P, const DevTables& T,
+                                           const double* __restrict__ Jm, const double* __restrict__ psi,
+                                           double* __restrict__ G, int lane) {
+  const long long cs = T.P, Pg = T.Pg;
+  for (int which = 0; which < 2; ++which) {
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double w = (T.info[p] & PT_NODIFF) ? 0.0 : Jm[g + (2 + which) * Pg];
+      A[t] = cpx(w * psi[p], w * psi[p + cs]);
+      A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
+    }
+    double2* X = line2T<false>(A, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double* s = gslot(G, Pg, which, c);
+        s[g] = -(s[g] + x[c]);  // eta_x (which 0) or eta_y (which 1)
+      }
+    }
+    FC_SYNC();
+  }
+}
+
 __global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                           int Lmax, const double* __restrict__ Jm,
                                                           const double* __restrict__ u, const double* __restrict__ mu,
@@ -1360,26 +1521,8 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restric
     const Job J = jobs[ji];
     const Plan P = T.plans[J.plan];
     const int L = P.L;
-    for (int which = 0; which < 2; ++which) {
-      for (int t = lane; t < J.n; t += 32) {
-        const long long p = J.base + (long long)t * J.stride;
-        const long long g = J.gbase + (long long)t * J.stride;
-        const double w = (T.info[p] & PT_NODIFF) ? 0.0 : Jm[g + (2 + which) * Pg];
-        A[t] = cpx(w * psi[p], w * psi[p + cs]);
-        A[L + t] = cpx(w * psi[p + 2 * cs], w * psi[p + 3 * cs]);
-      }
-      double2* X = line2T<false>(A, J, P, T, lane);
-      for (int t = lane; t < J.n; t += 32) {
-        const long long g = J.gbase + (long long)t * J.stride;
-        const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double* s = gslot(G, Pg, which, c);
-          s[g] = -(s[g] + x[c]);  // eta_x (which 0) or eta_y (which 1)
-        }
-      }
-      FC_SYNC();
-    }
+    if (T.patches[J.patch].pform) continue;  // k_adj_gen_B_wall
+    adj_eta_q2(A, L, J, P, T, Jm, psi, G, lane);
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;
@@ -1414,9 +1557,55 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_B(DevTables T, const Job* __restric
   }
 }
 
+// adjoint pass B of the product-rule wall form (Remark adiabatic; its jobs only): eta as in
+// k_adj_gen_B, then the pointwise map's transpose at the forward derivatives of Q
+// (partial = ubar, g1 = -(J1x gxbar + J1y gybar), g2 = -(J2x gxbar + J2y gybar)) and
+// partial -= (dQ/du)^T D_2^T(g2)
+__global__ void LINE_KERNEL_BOUNDS k_adj_gen_B_wall(DevTables T, const Job* __restrict__ jobs, int njobs,
+                                                               int Lmax, const double* __restrict__ Jm,
+                                                               const double* __restrict__ u,
+                                                               const double* __restrict__ mu,
+                                                               const double* __restrict__ psi,
+                                                               double* __restrict__ G) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* A = sm + warp * (2 * Lmax + CONT_TMP);
+  const long long cs = T.P, Pg = T.Pg;
+  for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
+    const Job J = jobs[ji];
+    if (!T.patches[J.patch].pform) continue;
+    const Plan P = T.plans[J.plan];
+    const int L = P.L;
+    adj_eta_q2(A, L, J, P, T, Jm, psi, G, lane);
+    // product-rule wall form: the pointwise map's transpose at the forward derivatives
+    // of Q; partial = ubar, g1 = -(J1x gxbar + J1y gybar), g2 = -(J2x gxbar + J2y gybar)
+    load4_theta(A, L, J, u, cs, T.gamma, lane);
+    deriv2(A, Lmax, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32)
+      adj_wall_point_B(T, J.base + (long long)t * J.stride, J.gbase + (long long)t * J.stride, Jm, u, mu, psi, G,
+                       A + t, A + L + t);
+    double2* Z = line2T<false>(A, J, P, T, lane);
+    for (int t = lane; t < J.n; t += 32) {
+      const long long p = J.base + (long long)t * J.stride;
+      const long long g = J.gbase + (long long)t * J.stride;
+      const double z[4] = {-Z[t].x, -Z[t].y, -Z[L + t].x, -Z[L + t].y};
+      const double u4[4] = {u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs]};
+      double part[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[c] = gslot(G, Pg, 2, c)[g];
+      thetaT_add(u4, T.gamma, z, part);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) gslot(G, Pg, 2, c)[g] = part[c];
+    }
+    FC_SYNC();
+  }
+}
+
 // pass C (q1): acc += dt (partial - D_1^T(g1))
+// (product-rule wall form: acc += dt (partial - (dQ/du)^T D_1^T(g1)))
 __global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restrict__ jobs, int njobs,
-                                                          int Lmax, const double* __restrict__ G,
+                                                          int Lmax, const double* __restrict__ u,
+                                                          const double* __restrict__ G,
                                                           double* __restrict__ acc, const double* __restrict__ dtp) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1433,10 +1622,18 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restric
       A[L + t] = cpx(gslot(G, Pg, 3, 2)[g], gslot(G, Pg, 3, 3)[g]);
     }
     double2* X = line2T<false>(A, J, P, T, lane);
+    const bool pf = T.patches[J.patch].pform != 0;
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       const long long g = J.gbase + (long long)t * J.stride;
-      const double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+      double x[4] = {X[t].x, X[t].y, X[L + t].x, X[L + t].y};
+      if (pf) {
+        const double u4[4] = {u[p], u[p + cs], u[p + 2 * cs], u[p + 3 * cs]};
+        double y[4] = {0.0, 0.0, 0.0, 0.0};
+        thetaT_add(u4, T.gamma, x, y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = y[c];
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[p + c * cs] = fma(dt, gslot(G, Pg, 2, c)[g] - x[c], acc[p + c * cs]);
     }
@@ -1449,16 +1646,43 @@ __global__ void LINE_KERNEL_BOUNDS k_adj_gen_C(DevTables T, const Job* __restric
 // mode 2 (no long q2 segment): eta = -S1, partial = A_x^T eta_x + A_y^T eta_y and
 // g1 = mu (J1x eta_x + J1y eta_y), which pass C finishes along q1
 __global__ void k_adj_gen_fixA(DevTables T, const GFix* __restrict__ f, int n, const double* __restrict__ Jm,
-                               const double* __restrict__ u, const double* __restrict__ mu, double* __restrict__ G) {
+                               const double* __restrict__ u, const double* __restrict__ mu,
+                               const double* __restrict__ psi, double* __restrict__ G) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const GFix q = f[i];
   const long long Pg = T.Pg, cs = T.P, g = q.g, p = q.p;
+  const bool pf = T.patches[pt_patch(T.info[p])].pform != 0;
   if (q.mode == 1) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       gslot(G, Pg, 0, c)[g] = 0.0;
       gslot(G, Pg, 1, c)[g] = 0.0;
+      if (pf) gslot(G, Pg, 3, c)[g] = 0.0;  // D_1 Q = 0 off the long q1 segments
+    }
+    return;
+  }
+  if (pf) {  // product-rule wall form with D_2 Q = 0
+    const double j1x = Jm[g], j1y = Jm[g + Pg];
+    const bool nod = (T.info[p] & PT_NODIFF) != 0;
+    double u4[4], gx[4], gy[4], wbar[12], ub[4], gxb[4], gyb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double d1 = gslot(G, Pg, 3, c)[g];
+      u4[c] = u[p + c * cs];
+      gx[c] = fma(j1x, d1, 0.0);
+      gy[c] = fma(j1y, d1, 0.0);
+      wbar[c] = nod ? 0.0 : -psi[p + c * cs];
+      wbar[4 + c] = -gslot(G, Pg, 0, c)[g];
+      wbar[8 + c] = -gslot(G, Pg, 1, c)[g];
+      gslot(G, Pg, 0, c)[g] = wbar[4 + c];
+      gslot(G, Pg, 1, c)[g] = wbar[8 + c];
+    }
+    wall_point_T(u4, gx, gy, mu[p], T.gamma, wbar, ub, gxb, gyb);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      gslot(G, Pg, 2, c)[g] = ub[c];
+      gslot(G, Pg, 3, c)[g] = -fma(j1x, gxb[c], j1y * gyb[c]);
     }
     return;
   }
@@ -1928,20 +2152,21 @@ void launch_adj_cart(const DevTables& T, const Job* jobs, int njobs, int Lmax, i
   if (njobs <= 0) return;
   k_adj_cart<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, dir, u, mu, psi, R1, acc, dt);
 }
-void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* psi,
-                      double* G, cudaStream_t st) {
+void launch_adj_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
+                      const double* psi, double* G, cudaStream_t st) {
   if (njobs <= 0) return;
-  k_adj_gen_A<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, psi, G);
+  k_adj_gen_A<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, u, psi, G);
 }
 void launch_adj_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* J, const double* u,
                       const double* mu, const double* psi, double* G, cudaStream_t st) {
   if (njobs <= 0) return;
   k_adj_gen_B<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, u, mu, psi, G);
+  if (T.any_pform) k_adj_gen_B_wall<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, J, u, mu, psi, G);
 }
-void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* G, double* acc,
-                      const double* dt, cudaStream_t st) {
+void launch_adj_gen_C(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* u, const double* G,
+                      double* acc, const double* dt, cudaStream_t st) {
   if (njobs <= 0) return;
-  k_adj_gen_C<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, G, acc, dt);
+  k_adj_gen_C<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, u, G, acc, dt);
 }
 void launch_gen_fix(const DevTables& T, const GFix* f, int n, const double* e, const double* mu, const double* J,
                     double* G, cudaStream_t st) {
@@ -1949,9 +2174,9 @@ void launch_gen_fix(const DevTables& T, const GFix* f, int n, const double* e, c
   k_gen_fix<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, e, mu, J, G);
 }
 void launch_adj_gen_fixA(const DevTables& T, const GFix* f, int n, const double* J, const double* u,
-                         const double* mu, double* G, cudaStream_t st) {
+                         const double* mu, const double* psi, double* G, cudaStream_t st) {
   if (n <= 0) return;
-  k_adj_gen_fixA<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, J, u, mu, G);
+  k_adj_gen_fixA<<<grid_pts(n, 256), 256, 0, st>>>(T, f, n, J, u, mu, psi, G);
 }
 void launch_adj_gen_fixB(const DevTables& T, const GFix* f, int n, const double* G, double* R1, cudaStream_t st) {
   if (n <= 0) return;
@@ -2040,6 +2265,7 @@ void set_kernel_attributes() {
   cudaFuncSetAttribute(k_adj_cart, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_adj_gen_A, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_adj_gen_B, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_adj_gen_B_wall, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_adj_gen_C, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filterT_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_filterT_q2, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);

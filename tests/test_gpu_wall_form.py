@@ -4,15 +4,16 @@ inputs: the RHS with a given viscosity on the O-grid, on the curved, twisted GRI
 and on the S-type arcs (1e-11 relative per component, as every RHS evaluation), ten
 steps of Algorithm 1 with viscosity, filter and CFL step (1e-9), the wall patches' RHS
 against the flux form's (different there, identical on every other patch), and the
-adjoint's refusal. The oracle's product-rule form is pinned against a symbolic operator
-of a manufactured state (tests/test_oracle_wall_form.py)."""
+discrete adjoint of a step with and without the filter (1e-11). The oracle's
+product-rule form is pinned against a symbolic operator of a manufactured state, its
+transpose by dot-product identities (tests/test_oracle_wall_form.py)."""
 import dataclasses
 
 import numpy as np
 import pytest
 import torch
 
-from oracle import solver as S
+from oracle import adjoint as A, solver as S
 from paper_2506_16076_gb300 import workloads as W
 from tests.gpu_helpers import from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
 
@@ -116,16 +117,29 @@ def test_ten_steps_parity(case):
     assert ctx.sync_status(e) == 0
 
 
-def test_adjoint_refuses_the_product_form(case, gpu_lib):
+@pytest.mark.parametrize("filt", [0, 1])
+def test_adjoint_step_parity(case, gpu_lib, filt):
+    # the discrete adjoint of a step with the product-rule wall patches (mu and dt frozen,
+    # with and without the per-step filter) against the oracle's transpose, whose
+    # pointwise Jacobians come from the complex step
     w, ctx, sv = case
-    e = to_dev(W.initial_state(w))
-    mu = torch.zeros(e.shape[1], dtype=torch.float64, device="cuda")
-    dt = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
-    lam = torch.zeros_like(e)
-    out = torch.empty_like(e)
-    with pytest.raises(gpu_lib.FcError) as ex:
-        ctx.adjoint_step(e, mu, dt, lam, out)
-    assert ex.value.status == 7  # FC_ERR_UNIMPLEMENTED
+    st = sv.project(W.random_smooth_state(w, seed=43 + filt, amp=0.1))
+    mu = [0.003 * (1 + np.cos(2 * g.x) * np.sin(g.y)) ** 2 for g in sv.geos]
+    dt = 0.5 * sv.dt(st, mu)
+    rng = np.random.default_rng(7 + filt)
+    lam = [rng.normal(size=a.shape) for a in st]
+    ref_lam, ref_gbc = A.step_adjoint(sv, st, mu, dt, lam, filt=bool(filt))
+    lam_n = torch.empty_like(to_dev(st))
+    gbc = torch.zeros_like(lam_n)
+    dtt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    ctx.adjoint_step(to_dev(st), to_dev_scalar_field(mu), dtt, to_dev(lam), lam_n, gbc,
+                     gpu_lib.STEP_FILTER if filt else 0)
+    torch.cuda.synchronize()
+    errs = rel_err(from_dev(lam_n, w), ref_lam)
+    assert max(errs) < 1e-11, errs
+    if any(np.abs(g).max() > 0 for g in ref_gbc):
+        errs = rel_err(from_dev(gbc, w), ref_gbc)
+        assert max(errs) < 1e-11, errs
 
 
 def test_affine_wall_patch_is_refused(gpu_lib):
