@@ -7,6 +7,7 @@
 // functions have no intra-warp register dependencies.
 #pragma once
 #include <math.h>
+#include <string.h>
 
 #include "fc_internal.h"
 
@@ -219,6 +220,93 @@ FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2*
   }
 }
 
+// ---- FMA-form inverse (decimation in time) stages of radix 2, 4, 8 (span > 1): each
+// twiddled input w_q x_q is S_q u_q with u_q = x'_q + i t_q x'_q (x' = x, or i x when
+// the record's flag bit q-1 is set: the ratio form of w_q in the plan's records), two
+// FMAs, and the real S_q (or its ratio to a partner's) multiplies inside the butterfly's
+// FMAs, so a radix-4 butterfly with twiddles is 22 FMAs instead of 16 adds and 3
+// complex products (28), a radix-8 one 62 FMAs and 4 adds instead of 80 operations. The
+// records (Builder::fma_tables) hold t_q, the flags and the scale ratios per offset j.
+FC_HD long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long v;
+  memcpy(&v, &x, sizeof(v));
+  return v;
+#endif
+}
+FC_HD double2 rot_u(double2 b, double t, bool f) {
+  const double bx = f ? -b.y : b.x, by = f ? b.x : b.y;
+  return cpx(fma(-t, by, bx), fma(t, bx, by));
+}
+FC_HD double2 fma2(double s, double2 u, double2 a) { return cpx(fma(s, u.x, a.x), fma(s, u.y, a.y)); }
+// a + s i u and a - s i u
+FC_HD double2 fma2_pi(double s, double2 u, double2 a) { return cpx(fma(-s, u.y, a.x), fma(s, u.x, a.y)); }
+FC_HD double2 fma2_mi(double s, double2 u, double2 a) { return cpx(fma(s, u.y, a.x), fma(-s, u.x, a.y)); }
+
+template <int R>
+FC_HD void inplace_stage_dit_fma(double2* a, int L, int span, int nseq, const double2* __restrict__ rec, int lane,
+                                 int nl) {
+  constexpr int RS = R == 2 ? 2 : (R == 4 ? 4 : 8);  // record length in double2
+  const int nbf = L / R;
+  for (int idx = lane; idx < nseq * nbf; idx += nl) {
+    const int s = idx / nbf;
+    const int t = idx - s * nbf;
+    const int bb = t / span;
+    const int j = t - bb * span;
+    double2* x = a + s * L + bb * R * span + j;
+    const double2* q = rec + j * RS;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[r * span];
+    const double2 h0 = q[0];
+    const long long fl = dbits(h0.x);
+    if (R == 2) {
+      const double2 u1 = rot_u(v[1], h0.y, fl & 1);
+      const double S1 = q[1].x;
+      x[0] = fma2(S1, u1, v[0]);
+      x[span] = fma2(-S1, u1, v[0]);
+    } else if (R == 4) {
+      const double2 h1 = q[1], h2 = q[2], h3 = q[3];
+      const double2 u1 = rot_u(v[1], h0.y, fl & 1), u2 = rot_u(v[2], h1.x, fl & 2), u3 = rot_u(v[3], h1.y, fl & 4);
+      const double S2 = h2.x, S1 = h2.y, rho = h3.x;
+      const double2 A = fma2(S2, u2, v[0]), B = fma2(-S2, u2, v[0]);
+      const double2 p = fma2(rho, u3, u1), m = fma2(-rho, u3, u1);  // (v1 + v3) / S1, (v1 - v3) / S1
+      x[0] = fma2(S1, p, A);
+      x[2 * span] = fma2(-S1, p, A);
+      x[span] = fma2_pi(S1, m, B);
+      x[3 * span] = fma2_mi(S1, m, B);
+    } else {
+      const double2 h1 = q[1], h2 = q[2], h3 = q[3], h4 = q[4], h5 = q[5], h6 = q[6], h7 = q[7];
+      // even half: DFT4 of (x0, S2 u2, S4 u4, S6 u6)
+      const double2 u2 = rot_u(v[2], h1.x, fl & 2), u4 = rot_u(v[4], h2.x, fl & 8), u6 = rot_u(v[6], h3.x, fl & 32);
+      const double S4 = h4.x, S2 = h4.y, r62 = h5.x;
+      const double2 A = fma2(S4, u4, v[0]), B = fma2(-S4, u4, v[0]);
+      const double2 p = fma2(r62, u6, u2), m = fma2(-r62, u6, u2);
+      const double2 E0 = fma2(S2, p, A), E2 = fma2(-S2, p, A), E1 = fma2_pi(S2, m, B), E3 = fma2_mi(S2, m, B);
+      // odd half: DFT4 of (S1 u1, S3 u3, S5 u5, S7 u7) / S1
+      const double2 u1 = rot_u(v[1], h0.y, fl & 1), u3 = rot_u(v[3], h1.y, fl & 4);
+      const double2 u5 = rot_u(v[5], h2.y, fl & 16), u7 = rot_u(v[7], h3.y, fl & 64);
+      const double r51 = h5.y, r73 = h6.x, r31 = h6.y, S1 = h7.x, S1r = h7.y;
+      const double2 al = fma2(r51, u5, u1), be = fma2(-r51, u5, u1);
+      const double2 ga = fma2(r73, u7, u3), de = fma2(-r73, u7, u3);
+      const double2 o0 = fma2(r31, ga, al), o2 = fma2(-r31, ga, al);
+      const double2 o1 = fma2_pi(r31, de, be), o3 = fma2_mi(r31, de, be);
+      // y_k = E_k + W^k S1 o_k, y_{k+4} = E_k - W^k S1 o_k, W = exp(2 pi i / 8)
+      x[0] = fma2(S1, o0, E0);
+      x[4 * span] = fma2(-S1, o0, E0);
+      x[2 * span] = fma2_pi(S1, o2, E2);
+      x[6 * span] = fma2_mi(S1, o2, E2);
+      const double2 w1 = cpx(o1.x - o1.y, o1.x + o1.y), w3 = cpx(-(o3.x + o3.y), o3.x - o3.y);
+      x[span] = fma2(S1r, w1, E1);
+      x[5 * span] = fma2(-S1r, w1, E1);
+      x[3 * span] = fma2(S1r, w3, E3);
+      x[7 * span] = fma2(-S1r, w3, E3);
+    }
+  }
+}
+
 template <bool INV, bool DIF>
 FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const double2* __restrict__ tw, int lane,
                              int nl) {
@@ -288,8 +376,21 @@ FC_HD void fft_inplace(double2* a, const Plan& P, int nseq, const double2* twpoo
     }
   } else {
     int span = 1;
+    const double2* rec = twpool + P.fmd;
     for (int st = P.nst - 1; st >= 0; --st) {
       const int R = P.rad[st];
+      if (span > 1 && (R == 2 || R == 4 || R == 8)) {
+        if (R == 2)
+          inplace_stage_dit_fma<2>(a, L, span, nseq, rec, lane, nl);
+        else if (R == 4)
+          inplace_stage_dit_fma<4>(a, L, span, nseq, rec, lane, nl);
+        else
+          inplace_stage_dit_fma<8>(a, L, span, nseq, rec, lane, nl);
+        rec += span * (R == 2 ? 2 : (R == 4 ? 4 : 8));
+        FC_SYNC();
+        span *= R;
+        continue;
+      }
       switch (R) {
         case 2: inplace_stage_r<2, true, false>(a, L, span, nseq, tw, lane, nl); break;
         case 3: inplace_stage_r<3, true, false>(a, L, span, nseq, tw, lane, nl); break;
