@@ -358,7 +358,7 @@ fc_status fc_probe_fp64(double *dfma_gflops, double *dmma_gflops, void *stream);
  * d x d Q, C x d A_l and C x d A_r blocks (one C block of the fc_params tables), of
  * table_len = d d + 2 C d values (any other length: FC_ERR_INVALID).
  * No boundary condition is applied (as in fc_rhs). The scratch is one static device
- * array of 9.6 MB (9,597,184 bytes) held by every GPU that loads the library until exit; limits:
+ * array of 10.0 MB (9,990,656 bytes) held by every GPU that loads the library until exit; limits:
  * n1 n2 <= 262144, n + C <= 1024, C <= 128, d <= 8 (beyond them the call prints the
  * limits to stderr and returns FC_ERR_INVALID). All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU (other streams, other host

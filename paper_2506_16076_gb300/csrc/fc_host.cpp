@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "fc_internal.h"
+#include "fc_tables.h"
 
 using namespace fcx;
 
@@ -866,69 +867,12 @@ struct Builder {
     }
   }
 
-  // Records of the inverse transform's radix-2/4/8 stages of span > 1 in the FMA form
-  // (fcx::inplace_stage_dit_fma): per butterfly offset j the twiddles w_q = exp(2 pi i q j
-  // tws / L), q = 1..R-1, each as w_q = S_q (1 + i t_q) (|Re w| >= |Im w|) or
-  // w_q = S_q i (1 - i t_q) with t_q = -Re w / Im w (flag bit q-1), so that w_q b costs
-  // two FMAs and the real S_q folds into the butterfly's FMAs, and the butterfly's scale
-  // ratios. Layout in double2 units: R = 2: (flags, t1), (S1, 0); R = 4: (flags, t1),
-  // (t2, t3), (S2, S1), (S3/S1, 0); R = 8: (flags, t1), (t2, t3), (t4, t5), (t6, t7),
-  // (S4, S2), (S6/S2, S5/S1), (S7/S3, S3/S1), (S1, S1/sqrt 2).
+  // the FMA-form records of p (fc_tables.h): inverse, then forward with the filter table
   void fma_tables(Plan& p) {
-    const int L = p.L;
-    p.fmd = (int)tw.size();
-    int span = 1;
-    for (int st = p.nst - 1; st >= 0; --st) {
-      const int R = p.rad[st];
-      if (span > 1 && (R == 2 || R == 4 || R == 8)) {
-        const int tws = L / (R * span);
-        for (int j = 0; j < span; ++j) {
-          long double S[8] = {1.0L}, t[8] = {0.0L};
-          long long flags = 0;
-          for (int q = 1; q < R; ++q) {
-            const long long e = ((long long)q * j * tws) % L;
-            const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
-            const long double cw = cosl(ang), sw = sinl(ang);
-            if (fabsl(cw) >= fabsl(sw)) {
-              S[q] = cw;
-              t[q] = sw / cw;
-            } else {
-              S[q] = sw;
-              t[q] = -cw / sw;
-              flags |= 1LL << (q - 1);
-            }
-          }
-          double fl;
-          std::memcpy(&fl, &flags, sizeof(fl));
-          auto push = [&](long double x, long double y) {
-            double2 v;
-            v.x = (double)x;
-            v.y = (double)y;
-            tw.push_back(v);
-          };
-          double2 h0;
-          h0.x = fl;
-          h0.y = (double)t[1];
-          tw.push_back(h0);
-          if (R == 2) {
-            push(S[1], 0.0L);
-          } else if (R == 4) {
-            push(t[2], t[3]);
-            push(S[2], S[1]);
-            push(S[3] / S[1], 0.0L);
-          } else {
-            push(t[2], t[3]);
-            push(t[4], t[5]);
-            push(t[6], t[7]);
-            push(S[4], S[2]);
-            push(S[6] / S[2], S[5] / S[1]);
-            push(S[7] / S[3], S[3] / S[1]);
-            push(S[1], S[1] * 0.70710678118654752440084436210484903928L);
-          }
-        }
-      }
-      span *= R;
-    }
+    fma_inverse_records(p, tw);
+    const std::vector<int> rev(ip.begin() + p.rev, ip.begin() + p.rev + p.L);
+    const std::vector<double> sig(rp.begin() + p.sig, rp.begin() + p.sig + p.L);
+    fma_forward_records(p, tw, rp, rev.data(), sig.data());
   }
 
   int plan(int L) {
@@ -949,7 +893,6 @@ struct Builder {
       tw.push_back(w);
     }
     rev_table(p);
-    fma_tables(p);
     p.sig = (int)rp.size();
     const fc_params& prm = c->prm;
     for (int t = 0; t < L; ++t) {
@@ -958,6 +901,7 @@ struct Builder {
       const long double z = 2.0L * k / (long double)L;
       rp.push_back((double)(expl(-(long double)prm.alpha_f * powl(z, prm.p_f)) / (long double)L));
     }
+    fma_tables(p);
     plans.push_back(p);
     std::vector<Plan> alt{p};
     for (size_t o = 1; o < orders.size(); ++o) {

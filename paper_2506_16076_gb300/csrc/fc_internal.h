@@ -37,8 +37,11 @@ struct Plan {
   int tw;     // offset of the L-entry forward twiddle table exp(-2 pi i e / L) in the twiddle pool
   int sig;    // offset of the L-entry filter table sigma(2k/L)/L in the real pool (-1: none)
   int rev;    // offset of the L-entry slot -> mode table of the in-place transforms in the int pool
-  int fmd;    // offset in the twiddle pool of the inverse transform's FMA-form butterfly records
-              // (radix 2, 4, 8 stages of span > 1, in the inverse transform's stage order)
+  // FMA-form butterfly records and scale tables (fc_tables.h): offsets in the twiddle pool
+  // of the inverse (fmd) and forward (fmf) records; bit st of fmsc: forward stage st
+  // multiplies its inputs by the L pending factors that follow psc in the real pool;
+  // per-slot derivative (dmul) and filter (sigp, -1: none) factors in the real pool
+  int fmd, fmf, fmsc, psc, dmul, sigp;
 };
 
 // One line segment processed by one warp.

@@ -157,9 +157,8 @@ __device__ __forceinline__ void deriv2(double2* A, int Lmax, const Job& J, const
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
-  fft_forward_mul<MUL_DERIV>(A, P, 2, T.tw, J.scale * TWO_PI / ((double)P.L * (double)P.L), T.ip + P.rev, nullptr,
-                             lane, 32);
-  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
+  fft_forward_mul<MUL_DERIV>(A, P, 2, T.tw, T.rp, J.scale * TWO_PI / ((double)P.L * (double)P.L), lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, T.rp, lane, 32);
 }
 
 // true on every lane when mu != 0 somewhere on the line (warp vote)
@@ -821,8 +820,8 @@ __device__ __forceinline__ void filter2(double2* A, int Lmax, const Job& J, cons
     continue_lines(A, P.L, J.n, J.C, T.d, T.rp + J.fcm, 2, lane, 32, A + 2 * Lmax);
   }
   FC_SYNC();
-  fft_forward_mul<MUL_FILTER>(A, P, 2, T.tw, 0.0, T.ip + P.rev, T.rp + P.sig, lane, 32);
-  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
+  fft_forward_mul<MUL_FILTER>(A, P, 2, T.tw, T.rp, 0.0, lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, T.rp, lane, 32);
 }
 
 __global__ void LINE_KERNEL_BOUNDS k_filter_q1(DevTables T, const Job* __restrict__ jobs, int njobs,
@@ -1183,13 +1182,13 @@ __device__ __forceinline__ double2* line2T(double2* A, const Job& J, const Plan&
     A[s * L + n + k] = cpx(0.0, 0.0);
   }
   FC_SYNC();
-  fft_inplace<false>(A, P, 2, T.tw, lane, 32);
+  fft_inplace<false>(A, P, 2, T.tw, T.rp, lane, 32);
   if (FILT)
-    mul_filter_rev(A, L, 2, T.rp + P.sig, T.ip + P.rev, lane, 32);
+    mul_filter_slot(A, L, 2, T.rp + P.sigp, lane, 32);
   else
-    mul_deriv_rev(A, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), T.ip + P.rev, lane, 32);
+    mul_deriv_slot(A, L, 2, -J.scale * TWO_PI / ((double)L * (double)L), T.rp + P.dmul, lane, 32);
   FC_SYNC();
-  fft_inplace<true>(A, P, 2, T.tw, lane, 32);
+  fft_inplace<true>(A, P, 2, T.tw, T.rp, lane, 32);
   double2* X = A;
   if (J.fcm >= 0) {
     const double* ML = T.rp + J.fcm;

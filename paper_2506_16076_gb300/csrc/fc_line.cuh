@@ -166,20 +166,25 @@ struct Dft<7, INV> : DftOdd<7, INV> {};
 // transform takes that order back to natural order, so no permutation pass is needed
 // and spectral multipliers look up each slot's mode number.
 // spectral multipliers folded into the last stage of a forward transform (span 1, where
-// the R outputs of butterfly bb land in slots bb R + r): MUL_DERIV: i m_k (eq. fc_der),
-// MUL_FILTER: sigma(2k/L)/L (eq. filtering), with k = rev[slot]
+// the R outputs of butterfly bb land in slots bb R + r), from per-slot tables that also
+// hold the transform's pending factors (fc_tables.h): MUL_DERIV: i fac dmul[slot] (eq.
+// fc_der, dmul = k P), MUL_FILTER: sigp[slot] (eq. filtering, sigp = sigma(2k/L)/L P)
 enum { MUL_NONE = 0, MUL_DERIV = 1, MUL_FILTER = 2 };
-FC_HD double2 deriv_mult(double2 z, int k, int L, double fac) {
-  int kk = (2 * k <= L) ? k : k - L;
-  if (2 * k == L) kk = 0;
-  const double m = (fac * (double)kk);
-  return cpx(-m * z.y, m * z.x);
+template <int MUL>
+FC_HD double2 apply_mult(double2 z, double m, double fac) {
+  if (MUL == MUL_DERIV) {
+    const double f = fac * m;
+    return cpx(-f * z.y, f * z.x);
+  }
+  return cscl(z, m);
 }
 
+// psc (forward only, may be null): pending factors of the inputs, multiplied in first;
+// mt: the multiplier table of MUL
 template <int R, bool INV, bool DIF, int MUL = MUL_NONE>
 FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2* __restrict__ tw, int lane, int nl,
-                           double fac = 0.0, const int* __restrict__ rev = nullptr,
-                           const double* __restrict__ sig = nullptr) {
+                           double fac = 0.0, const double* __restrict__ mt = nullptr,
+                           const double* __restrict__ psc = nullptr) {
   const int nbf = L / R;
   const int tws = L / (R * span);
   for (int idx = lane; idx < nseq * nbf; idx += nl) {
@@ -191,6 +196,11 @@ FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2*
     double2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = x[r * span];
+    if (DIF && psc) {
+      const double* ps = psc + bb * R * span + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = cscl(v[r], ps[r * span]);
+    }
     if (!DIF && j != 0) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
@@ -208,12 +218,9 @@ FC_HD void inplace_stage_r(double2* a, int L, int span, int nseq, const double2*
         v[q] = cmul(v[q], w);
       }
     }
-    if (MUL == MUL_DERIV) {
+    if (MUL != MUL_NONE) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = deriv_mult(v[r], rev[bb * R + r], L, fac);
-    } else if (MUL == MUL_FILTER) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = cscl(v[r], sig[rev[bb * R + r]]);
+      for (int r = 0; r < R; ++r) v[r] = apply_mult<MUL>(v[r], mt[bb * R + r], fac);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r * span] = v[r];
@@ -307,9 +314,89 @@ FC_HD void inplace_stage_dit_fma(double2* a, int L, int span, int nseq, const do
   }
 }
 
+// FMA-form forward (decimation in frequency) stage of radix 2, 4, 8: the inputs carry
+// pending real factors, combined through the ratios of the butterfly's record rat (per
+// butterfly); the outputs keep the factor of the first input; outputs 1..R-1 are then
+// rotated by u = y' + i t y' with the rotation record rot (per offset j, span > 1) and
+// their factor multiplied by the twiddle's S (host-side bookkeeping, fc_tables.h). A
+// radix-4 butterfly with twiddles is 22 FMAs instead of 28 operations. In the last stage
+// (span 1) the multiplier table mt applies MUL with the final factors folded in.
+template <int R, int MUL>
+FC_HD void inplace_stage_dif_fma(double2* a, int L, int span, int nseq, const double2* __restrict__ rot,
+                                 const double2* __restrict__ rat, int lane, int nl, double fac,
+                                 const double* __restrict__ mt) {
+  constexpr int RH = R / 2;  // rotation and ratio record lengths in double2
+  const int nbf = L / R;
+  for (int idx = lane; idx < nseq * nbf; idx += nl) {
+    const int s = idx / nbf;
+    const int t = idx - s * nbf;
+    const int bb = t / span;
+    const int j = t - bb * span;
+    double2* x = a + s * L + bb * R * span + j;
+    const double2* g = rat + t * RH;
+    double2 v[R], y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[r * span];
+    if (R == 2) {
+      const double r10 = g[0].x;
+      y[0] = fma2(r10, v[1], v[0]);
+      y[1] = fma2(-r10, v[1], v[0]);
+    } else if (R == 4) {
+      const double2 g0 = g[0];
+      const double s10 = g[1].x;
+      const double2 A = fma2(g0.x, v[2], v[0]), B = fma2(-g0.x, v[2], v[0]);
+      const double2 C = fma2(g0.y, v[3], v[1]), M = fma2(-g0.y, v[3], v[1]);
+      y[0] = fma2(s10, C, A);
+      y[2] = fma2(-s10, C, A);
+      y[1] = fma2_mi(s10, M, B);
+      y[3] = fma2_pi(s10, M, B);
+    } else {
+      const double2 g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+      // even half: DFT4 of (v0, v2, v4, v6) with factors relative to v0's
+      const double2 A = fma2(g0.x, v[4], v[0]), B = fma2(-g0.x, v[4], v[0]);
+      const double2 C = fma2(g0.y, v[6], v[2]), M = fma2(-g0.y, v[6], v[2]);
+      const double2 E0 = fma2(g1.x, C, A), E2 = fma2(-g1.x, C, A);
+      const double2 E1 = fma2_mi(g1.x, M, B), E3 = fma2_pi(g1.x, M, B);
+      // odd half: DFT4 of (v1, v3, v5, v7) relative to v1's factor
+      const double2 al = fma2(g1.y, v[5], v[1]), be = fma2(-g1.y, v[5], v[1]);
+      const double2 ga = fma2(g2.x, v[7], v[3]), de = fma2(-g2.x, v[7], v[3]);
+      const double2 o0 = fma2(g2.y, ga, al), o2 = fma2(-g2.y, ga, al);
+      const double2 o1 = fma2_mi(g2.y, de, be), o3 = fma2_pi(g2.y, de, be);
+      // y_k = E_k + W^k (P1/P0) o_k, y_{k+4} = E_k - W^k (P1/P0) o_k, W = exp(-2 pi i / 8)
+      const double tau = g3.x, taur = g3.y;
+      y[0] = fma2(tau, o0, E0);
+      y[4] = fma2(-tau, o0, E0);
+      y[2] = fma2_mi(tau, o2, E2);
+      y[6] = fma2_pi(tau, o2, E2);
+      const double2 w1 = cpx(o1.x + o1.y, o1.y - o1.x), w3 = cpx(o3.y - o3.x, -(o3.x + o3.y));
+      y[1] = fma2(taur, w1, E1);
+      y[5] = fma2(-taur, w1, E1);
+      y[3] = fma2(taur, w3, E3);
+      y[7] = fma2(-taur, w3, E3);
+    }
+    if (span > 1) {
+      const double2* h = rot + j * RH;
+      const long long fl = dbits(h[0].x);
+      y[1] = rot_u(y[1], h[0].y, fl & 1);
+#pragma unroll
+      for (int q = 2; q < R; q += 2) {
+        const double2 hq = h[q / 2];
+        y[q] = rot_u(y[q], hq.x, (fl >> (q - 1)) & 1);
+        y[q + 1] = rot_u(y[q + 1], hq.y, (fl >> q) & 1);
+      }
+    }
+    if (MUL != MUL_NONE) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[r] = apply_mult<MUL>(y[r], mt[bb * R + r], fac);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r * span] = y[r];
+  }
+}
+
 template <bool INV, bool DIF>
 FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const double2* __restrict__ tw, int lane,
-                             int nl) {
+                             int nl, const double* __restrict__ psc = nullptr) {
   const int nbf = L / R;
   const int tws = L / (R * span);
   const int wr = L / R;  // exp(s 2 pi i / R) = tw[wr]
@@ -322,6 +409,7 @@ FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const
     double2 v[MAX_GENERIC_RADIX], y[MAX_GENERIC_RADIX];
     for (int r = 0; r < R; ++r) {
       v[r] = x[r * span];
+      if (DIF && psc) v[r] = cscl(v[r], psc[bb * R * span + r * span + j]);
       if (!DIF && j != 0 && r) {
         double2 w = tw[r * j * tws];
         if (INV) w.y = -w.y;
@@ -353,27 +441,20 @@ FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const
   }
 }
 
-// forward (DIF) or inverse (DIT) in-place transform of nseq sequences of length P.L in a
+template <int MUL>
+FC_HD void fft_forward_mul(double2* a, const Plan& P, int nseq, const double2* twpool, const double* rp, double fac,
+                           int lane, int nl);
+
+// forward (DIF) or inverse (DIT) in-place transform of nseq sequences of length P.L in a.
+// The forward transform's outputs carry the plan's per-slot pending factors (fc_tables.h):
+// its consumers multiply through the per-slot tables (mul_deriv_slot, mul_filter_slot).
 template <bool INV>
-FC_HD void fft_inplace(double2* a, const Plan& P, int nseq, const double2* twpool, int lane, int nl) {
+FC_HD void fft_inplace(double2* a, const Plan& P, int nseq, const double2* twpool, const double* rp, int lane,
+                       int nl) {
   const double2* tw = twpool + P.tw;
   const int L = P.L;
   if (!INV) {
-    int span = L;
-    for (int st = 0; st < P.nst; ++st) {
-      const int R = P.rad[st];
-      span /= R;
-      switch (R) {
-        case 2: inplace_stage_r<2, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 3: inplace_stage_r<3, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 4: inplace_stage_r<4, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 5: inplace_stage_r<5, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 7: inplace_stage_r<7, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 8: inplace_stage_r<8, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        default: inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl); break;
-      }
-      FC_SYNC();
-    }
+    fft_forward_mul<MUL_NONE>(a, P, nseq, twpool, rp, 0.0, lane, nl);
   } else {
     int span = 1;
     const double2* rec = twpool + P.fmd;
@@ -406,63 +487,81 @@ FC_HD void fft_inplace(double2* a, const Plan& P, int nseq, const double2* twpoo
   }
 }
 
-// Z at slot t <- i m_k Z with k = rev[t] the mode held there (derivative, eq. fc_der)
-FC_HD void mul_deriv_rev(double2* a, int L, int nseq, double fac, const int* __restrict__ rev, int lane, int nl) {
-  for (int idx = lane; idx < nseq * L; idx += nl) {
-    const int s = idx / L;
-    const int t = idx - s * L;
-    a[idx] = deriv_mult(a[idx], rev[t], L, fac);
-  }
+// the multipliers as a pass of their own after fft_inplace<false> (per-slot tables with
+// the pending factors folded in): derivative i fac dmul[slot] (eq. fc_der), filter
+// sigp[slot] (eq. filtering)
+FC_HD void mul_deriv_slot(double2* a, int L, int nseq, double fac, const double* __restrict__ dmul, int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) a[idx] = apply_mult<MUL_DERIV>(a[idx], dmul[idx % L], fac);
+}
+FC_HD void mul_filter_slot(double2* a, int L, int nseq, const double* __restrict__ sigp, int lane, int nl) {
+  for (int idx = lane; idx < nseq * L; idx += nl) a[idx] = apply_mult<MUL_FILTER>(a[idx], sigp[idx % L], 0.0);
 }
 
-// Z at slot t <- sig[rev[t]] Z (eq. filtering; sig already divided by L)
-FC_HD void mul_filter_rev(double2* a, int L, int nseq, const double* __restrict__ sig, const int* __restrict__ rev,
-                          int lane, int nl) {
-  for (int idx = lane; idx < nseq * L; idx += nl) {
-    const int s = idx / L;
-    const int t = idx - s * L;
-    a[idx] = cscl(a[idx], sig[rev[t]]);
-  }
-}
-
-// forward transform (as fft_inplace<false>) followed by the derivative (MUL_DERIV) or
-// filter (MUL_FILTER) multiplier, the multiplier applied inside the last stage when its
-// radix has a fixed butterfly (one shared-memory pass and one barrier fewer)
+// forward transform followed by the derivative (MUL_DERIV) or filter (MUL_FILTER)
+// multiplier (MUL_NONE: the transform alone, outputs with pending factors), the
+// multiplier applied inside the last stage when its radix has a fixed butterfly (one
+// shared-memory pass and one barrier fewer); radix-2/4/8 stages in the FMA form
 template <int MUL>
-FC_HD void fft_forward_mul(double2* a, const Plan& P, int nseq, const double2* twpool, double fac,
-                           const int* __restrict__ rev, const double* __restrict__ sig, int lane, int nl) {
+FC_HD void fft_forward_mul(double2* a, const Plan& P, int nseq, const double2* twpool, const double* rp, double fac,
+                           int lane, int nl) {
   const double2* tw = twpool + P.tw;
+  const double2* rec = twpool + P.fmf;
+  const double* psc = rp + P.psc;
+  const double* mt = MUL == MUL_DERIV ? rp + P.dmul : (MUL == MUL_FILTER ? rp + P.sigp : nullptr);
   const int L = P.L;
   int span = L;
   for (int st = 0; st < P.nst; ++st) {
     const int R = P.rad[st];
     span /= R;
-    if (st == P.nst - 1) {
+    const bool last = st == P.nst - 1;
+    if (R == 2 || R == 4 || R == 8) {
+      const double2* rot = rec;
+      if (span > 1) rec += span * (R / 2);
+      const double2* rat = rec;
+      rec += (L / R) * (R / 2);
+      if (last) {
+        if (R == 2)
+          inplace_stage_dif_fma<2, MUL>(a, L, span, nseq, rot, rat, lane, nl, fac, mt);
+        else if (R == 4)
+          inplace_stage_dif_fma<4, MUL>(a, L, span, nseq, rot, rat, lane, nl, fac, mt);
+        else
+          inplace_stage_dif_fma<8, MUL>(a, L, span, nseq, rot, rat, lane, nl, fac, mt);
+      } else {
+        if (R == 2)
+          inplace_stage_dif_fma<2, MUL_NONE>(a, L, span, nseq, rot, rat, lane, nl, 0.0, nullptr);
+        else if (R == 4)
+          inplace_stage_dif_fma<4, MUL_NONE>(a, L, span, nseq, rot, rat, lane, nl, 0.0, nullptr);
+        else
+          inplace_stage_dif_fma<8, MUL_NONE>(a, L, span, nseq, rot, rat, lane, nl, 0.0, nullptr);
+      }
+      FC_SYNC();
+      continue;
+    }
+    const double* ps = nullptr;
+    if ((P.fmsc >> st) & 1) {
+      ps = psc;
+      psc += L;
+    }
+    if (last && MUL != MUL_NONE) {
       switch (R) {
-        case 2: inplace_stage_r<2, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
-        case 3: inplace_stage_r<3, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
-        case 4: inplace_stage_r<4, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
-        case 5: inplace_stage_r<5, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
-        case 7: inplace_stage_r<7, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
-        case 8: inplace_stage_r<8, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, rev, sig); break;
+        case 3: inplace_stage_r<3, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, mt, ps); break;
+        case 5: inplace_stage_r<5, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, mt, ps); break;
+        case 7: inplace_stage_r<7, false, true, MUL>(a, L, span, nseq, tw, lane, nl, fac, mt, ps); break;
         default:
-          inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl);
+          inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl, ps);
           FC_SYNC();
           if (MUL == MUL_DERIV)
-            mul_deriv_rev(a, L, nseq, fac, rev, lane, nl);
+            mul_deriv_slot(a, L, nseq, fac, mt, lane, nl);
           else
-            mul_filter_rev(a, L, nseq, sig, rev, lane, nl);
+            mul_filter_slot(a, L, nseq, mt, lane, nl);
           break;
       }
     } else {
       switch (R) {
-        case 2: inplace_stage_r<2, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 3: inplace_stage_r<3, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 4: inplace_stage_r<4, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 5: inplace_stage_r<5, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 7: inplace_stage_r<7, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        case 8: inplace_stage_r<8, false, true>(a, L, span, nseq, tw, lane, nl); break;
-        default: inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl); break;
+        case 3: inplace_stage_r<3, false, true>(a, L, span, nseq, tw, lane, nl, 0.0, nullptr, ps); break;
+        case 5: inplace_stage_r<5, false, true>(a, L, span, nseq, tw, lane, nl, 0.0, nullptr, ps); break;
+        case 7: inplace_stage_r<7, false, true>(a, L, span, nseq, tw, lane, nl, 0.0, nullptr, ps); break;
+        default: inplace_stage_gen<false, true>(a, L, span, R, nseq, tw, lane, nl, ps); break;
       }
     }
     FC_SYNC();

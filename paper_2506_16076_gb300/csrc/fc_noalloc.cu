@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "fc_internal.h"
+#include "fc_tables.h"
 
 using namespace fcx;
 
@@ -25,8 +26,13 @@ constexpr int NA_MAX_C = 128;
 constexpr int NA_MAX_D = 8;
 constexpr size_t NA_R1 = 4 * NA_MAX_POINTS * sizeof(double);
 constexpr size_t NA_INFO = NA_MAX_POINTS * sizeof(uint32_t);
-constexpr size_t NA_TW = 2 * NA_MAX_L * sizeof(double2);
-constexpr size_t NA_RP = (2 * NA_MAX_C * NA_MAX_D + 4 * NA_MAX_C) * sizeof(double);
+// per continued length: the twiddles (L) and the FMA-form records (fc_tables.h: at most
+// 2 L inverse, L forward rotation and L/2 per forward stage), and in the real pool its
+// per-slot derivative factors (L) and pending-factor tables (at most L per stage)
+constexpr int NA_TW_PER_L = 9;
+constexpr int NA_RP_PER_L = 8;
+constexpr size_t NA_TW = 2 * NA_TW_PER_L * NA_MAX_L * sizeof(double2);
+constexpr size_t NA_RP = (2 * NA_MAX_C * NA_MAX_D + 4 * NA_MAX_C + 2 * NA_RP_PER_L * NA_MAX_L) * sizeof(double);
 constexpr size_t NA_PLANS = 2 * sizeof(Plan);
 constexpr size_t NA_JOBS = 2 * NA_MAX_L * sizeof(Job);
 constexpr size_t NA_IP = 2 * NA_MAX_L * sizeof(int);
@@ -133,6 +139,7 @@ extern "C" fc_status fc_rhs_patch_noalloc(const double* e_dev, const double* mu_
       w.y = (double)sinl(a);
       tw.push_back(w);
     }
+    fma_inverse_records(pl, tw);
   }
   const double* Q = table;
   const double* AL = Q + d * d;
@@ -160,6 +167,14 @@ extern "C" fc_status fc_rhs_patch_noalloc(const double* e_dev, const double* mu_
         }
         rp.push_back((double)s);
       }
+  for (int k = 0; k < 2; ++k) {  // forward records after the continuation matrices (fcm = 0)
+    const std::vector<int> rev(ip.begin() + plans[k].rev, ip.begin() + plans[k].rev + L[k]);
+    fma_forward_records(plans[k], tw, rp, rev.data(), nullptr);
+  }
+  if (tw.size() * sizeof(double2) > NA_TW || rp.size() * sizeof(double) > NA_RP) {
+    fprintf(stderr, "fc_rhs_patch_noalloc: the transform tables exceed the static scratch\n");
+    return FC_ERR_INVALID;
+  }
   std::vector<Job> jobs;
   for (int dir = 0; dir < 2; ++dir) {
     const int nl = dir ? n1 : n2, n = dir ? n2 : n1;

@@ -50,12 +50,12 @@ void derive(double2* A, int Lmax, const fcx::Plan& P, int n, int C, int fcm, dou
             const Builder& B, bool filter = false) {
   using namespace fcx;
   if (fcm >= 0) continue_lines(A, P.L, n, C, d, B.rp.data() + fcm, 2, 0, 1, A + 2 * Lmax);
-  fft_inplace<false>(A, P, 2, B.tw.data(), 0, 1);
+  fft_inplace<false>(A, P, 2, B.tw.data(), B.rp.data(), 0, 1);
   if (filter)
-    mul_filter_rev(A, P.L, 2, B.rp.data() + P.sig, B.ip.data() + P.rev, 0, 1);
+    mul_filter_slot(A, P.L, 2, B.rp.data() + P.sigp, 0, 1);
   else
-    mul_deriv_rev(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.ip.data() + P.rev, 0, 1);
-  fft_inplace<true>(A, P, 2, B.tw.data(), 0, 1);
+    mul_deriv_slot(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.rp.data() + P.dmul, 0, 1);
+  fft_inplace<true>(A, P, 2, B.tw.data(), B.rp.data(), 0, 1);
 }
 
 int run_plans(int argc, char** argv) {
