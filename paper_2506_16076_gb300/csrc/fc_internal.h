@@ -40,8 +40,10 @@ struct Plan {
   // FMA-form butterfly records and scale tables (fc_tables.h): offsets in the twiddle pool
   // of the inverse (fmd) and forward (fmf) records; bit st of fmsc: forward stage st
   // multiplies its inputs by the L pending factors that follow psc in the real pool;
-  // per-slot derivative (dmul) and filter (sigp, -1: none) factors in the real pool
-  int fmd, fmf, fmsc, psc, dmul, sigp;
+  // per-slot derivative (dmul) and filter (sigp, -1: none) factors in the real pool; bit
+  // st of fmod: forward stage st (odd radix, span 1) folds its inputs' factors into the
+  // butterfly through per-butterfly records among the forward records
+  int fmd, fmf, fmsc, psc, dmul, sigp, fmod;
 };
 
 // One line segment processed by one warp.

@@ -314,12 +314,14 @@ __global__ void LINE_KERNEL_BOUNDS k_cart_q2(DevTables T, const Job* __restrict_
 // points row by row (TW consecutive doubles per row: whole 32-byte sectors) into the
 // warps' line buffers, and writes the stage result the same way; in between each warp
 // transforms its own column. Other job sets run one line per warp as in k_cart_q2.
+// Registers are held to 5 resident CTAs per SM (measured a little faster than 4 CTAs
+// with more registers and no spills).
 constexpr int TW = 4;
 __host__ __device__ inline int tiled_stride(int Lmax) {
   const int b = 2 * Lmax + CONT_TMP;
   return b + ((2 - b % 8) + 8) % 8;  // = 2 (mod 8): conflict-free row-by-column smem access
 }
-__global__ void __launch_bounds__(TW * 32) k_cart_q2_tiled(DevTables T, const Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(TW * 32, 5) k_cart_q2_tiled(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                             int Lmax, const double* __restrict__ mu,
                                                             const double* __restrict__ R1, StageCoef sc) {
   extern __shared__ double2 sm[];

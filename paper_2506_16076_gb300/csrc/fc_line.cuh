@@ -178,6 +178,10 @@ FC_HD double2 apply_mult(double2 z, double m, double fac) {
   }
   return cscl(z, m);
 }
+template <int MUL>
+FC_HD double2 apply_out(double2 z, const double* __restrict__ mt, int slot, double fac) {
+  return MUL == MUL_NONE ? z : apply_mult<MUL>(z, mt[slot], fac);
+}
 
 // psc (forward only, may be null): pending factors of the inputs, multiplied in first;
 // mt: the multiplier table of MUL
@@ -394,6 +398,49 @@ FC_HD void inplace_stage_dif_fma(double2* a, int L, int span, int nseq, const do
   }
 }
 
+// last forward stage (span 1) of odd radix R with the inputs' pending factors folded
+// into the butterfly (records of fc_tables.h): the DftOdd computation with every
+// coefficient multiplied by the factor ratios, the outputs left with the first input's
+// factor (in the multiplier table mt)
+template <int R, int MUL>
+FC_HD void inplace_stage_odd_fold(double2* a, int L, int nseq, const double2* __restrict__ rec, int lane, int nl,
+                                  double fac, const double* __restrict__ mt) {
+  constexpr int H = (R - 1) / 2;
+  constexpr int RS2 = (2 * H + 2 * H * H + 1) / 2;  // record length in double2
+  const int nbf = L / R;
+  for (int idx = lane; idx < nseq * nbf; idx += nl) {
+    const int s = idx / nbf;
+    const int bb = idx - s * nbf;
+    double2* x = a + s * L + bb * R;
+    const double* c = (const double*)(rec + bb * RS2);
+    double2 v[R], ap[H], bp[H];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[r];
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      ap[m - 1] = fma2(c[m - 1], v[R - m], v[m]);
+      bp[m - 1] = fma2(-c[m - 1], v[R - m], v[m]);
+    }
+    double2 y0 = v[0];
+#pragma unroll
+    for (int m = 0; m < H; ++m) y0 = fma2(c[H + m], ap[m], y0);
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      double2 t = v[0], u;
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        t = fma2(c[2 * H + (q - 1) * H + m], ap[m], t);
+        const double sq = c[2 * H + H * H + (q - 1) * H + m];
+        u = m == 0 ? cscl(bp[0], sq) : fma2(sq, bp[m], u);
+      }
+      const double2 iu = mul_si<false>(u);
+      x[q] = apply_out<MUL>(cadd(t, iu), mt, bb * R + q, fac);
+      x[R - q] = apply_out<MUL>(csub(t, iu), mt, bb * R + R - q, fac);
+    }
+    x[0] = apply_out<MUL>(y0, mt, bb * R, fac);
+  }
+}
+
 template <bool INV, bool DIF>
 FC_HD void inplace_stage_gen(double2* a, int L, int span, int R, int nseq, const double2* __restrict__ tw, int lane,
                              int nl, const double* __restrict__ psc = nullptr) {
@@ -534,6 +581,19 @@ FC_HD void fft_forward_mul(double2* a, const Plan& P, int nseq, const double2* t
         else
           inplace_stage_dif_fma<8, MUL_NONE>(a, L, span, nseq, rot, rat, lane, nl, 0.0, nullptr);
       }
+      FC_SYNC();
+      continue;
+    }
+    if ((P.fmod >> st) & 1) {  // odd last stage with the pending factors folded in
+      const int rs2 = (R - 1 + (R - 1) * (R - 1) / 2 + 1) / 2;
+      const double2* rr = rec;
+      rec += (L / R) * rs2;
+      if (R == 3)
+        inplace_stage_odd_fold<3, MUL>(a, L, nseq, rr, lane, nl, fac, mt);
+      else if (R == 5)
+        inplace_stage_odd_fold<5, MUL>(a, L, nseq, rr, lane, nl, fac, mt);
+      else
+        inplace_stage_odd_fold<7, MUL>(a, L, nseq, rr, lane, nl, fac, mt);
       FC_SYNC();
       continue;
     }

@@ -21,9 +21,12 @@
 //   R = 2: (P1/P0, 0)
 //   R = 4: (P2/P0, P3/P1), (P1/P0, 0)
 //   R = 8: (P4/P0, P6/P2), (P2/P0, P5/P1), (P7/P3, P3/P1), (P1/P0, P1/P0/sqrt 2)
-// A stage of another radix whose inputs carry factors other than 1 multiplies them in
-// first (bit st of Plan::fmsc, L factors per such stage in the real pool from
-// Plan::psc). The factors left after the last stage are folded into the per-slot
+// A last stage (span 1) of radix 3, 5 or 7 whose inputs carry factors folds them into its
+// FMAs (bit st of Plan::fmod): per butterfly, H = (R-1)/2, the doubles rho_m =
+// P_{R-m}/P_m, pi_m = P_m/P_0, cos(2 pi q m/R) pi_m and sin(2 pi q m/R) pi_m (q, m = 1..H,
+// q major), padded to whole double2; its outputs keep P_0. A stage of another radix whose
+// inputs carry factors other than 1 multiplies them in first (bit st of Plan::fmsc, L
+// factors per such stage in the real pool from Plan::psc). The factors left after the last stage are folded into the per-slot
 // derivative table (Plan::dmul: k P for the mode k held at the slot, 0 for the Nyquist
 // mode) and filter table (Plan::sigp: sigma(2k/L)/L P).
 #pragma once
@@ -116,6 +119,7 @@ inline void fma_forward_records(Plan& p, std::vector<double2>& tw, std::vector<d
   std::vector<long double> P((size_t)L, 1.0L);
   p.fmf = (int)tw.size();
   p.fmsc = 0;
+  p.fmod = 0;
   p.psc = (int)rp.size();
   int span = L;
   for (int st = 0; st < p.nst; ++st) {
@@ -124,6 +128,27 @@ inline void fma_forward_records(Plan& p, std::vector<double2>& tw, std::vector<d
     if (!fma_radix(R)) {
       bool scaled = false;
       for (long double v : P) scaled = scaled || v != 1.0L;
+      if (scaled && span == 1 && (R == 3 || R == 5 || R == 7)) {
+        p.fmod |= 1 << st;
+        const int H = (R - 1) / 2;
+        for (int bb = 0; bb < L / R; ++bb) {
+          const long double* Pr = P.data() + (size_t)bb * R;
+          std::vector<long double> rec;
+          for (int m = 1; m <= H; ++m) rec.push_back(Pr[R - m] / Pr[m]);
+          for (int m = 1; m <= H; ++m) rec.push_back(Pr[m] / Pr[0]);
+          for (int q = 1; q <= H; ++q)
+            for (int m = 1; m <= H; ++m)
+              rec.push_back(cosl(2.0L * TABLE_PI * (long double)(q * m) / (long double)R) * (Pr[m] / Pr[0]));
+          for (int q = 1; q <= H; ++q)
+            for (int m = 1; m <= H; ++m)
+              rec.push_back(sinl(2.0L * TABLE_PI * (long double)(q * m) / (long double)R) * (Pr[m] / Pr[0]));
+          if (rec.size() % 2) rec.push_back(0.0L);
+          for (size_t i = 0; i < rec.size(); i += 2) tw.push_back(table_pair(rec[i], rec[i + 1]));
+        }
+        for (int bb = 0; bb < L / R; ++bb)
+          for (int r = 1; r < R; ++r) P[(size_t)(bb * R + r)] = P[(size_t)(bb * R)];
+        continue;
+      }
       if (scaled) {
         p.fmsc |= 1 << st;
         for (long double v : P) rp.push_back((double)v);
