@@ -129,6 +129,12 @@ struct fc_ctx {
   Queue q_cart1, q_cart2, q_gen1, q_gen2, q_filt1, q_filt2;
   int* d_fix = nullptr;
   int nfix = 0;
+  // the y fluxes of the affine patches' points, written by the q1 pass for the q2 pass, and
+  // the points on affine q2 lines that no affine q1 line visits (their y flux comes from
+  // k_flux_y_points)
+  double* d_Fy = nullptr;
+  int* d_fyfix = nullptr;
+  int nfyfix = 0;
   GFix* d_gfix = nullptr;
   int ngfix = 0;
   int* d_fcopy1 = nullptr;
@@ -141,7 +147,7 @@ struct fc_ctx {
   std::vector<Recv> h_recv;
   std::vector<BcPt> h_bc;
   std::vector<WallPt> h_walls;
-  std::vector<int> h_fix, h_fcopy1, h_fcopy2, h_cdst, h_cptr, h_csrc;
+  std::vector<int> h_fix, h_fcopy1, h_fcopy2, h_cdst, h_cptr, h_csrc, h_fyfix;
   std::vector<GFix> h_gfix;
   // sharded execution (fc_shard): this rank of nranks, patch owners, the caller's transport
   int nranks = 1, rank = 0;
@@ -1426,7 +1432,17 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
     for (long long k = 0; k < (long long)h.n1 * h.n2; ++k)
       mpts.push_back(GFix{(int)(h.off + k), (int)(h.gbase + k), 0, 0});
   }
-  std::vector<int> fix, fc1, fc2;
+  std::vector<int> fix, fc1, fc2, fyfix;
+  {
+    std::vector<uint8_t> cov1c((size_t)c->P, 0);
+    for (const Job& J : jc1)
+      for (int t = 0; t < J.n; ++t) cov1c[(size_t)(J.base + (long long)t * J.stride)] = 1;
+    for (const Job& J : jc2)
+      for (int t = 0; t < J.n; ++t) {
+        const long long k = J.base + (long long)t * J.stride;
+        if (!cov1c[(size_t)k]) fyfix.push_back((int)k);
+      }
+  }
   for (long long k = 0; k < c->P; ++k) {
     if (!cov2[k]) fix.push_back((int)k);
     if (!(info[k] & PT_BLANK)) {
@@ -1563,7 +1579,8 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->upload(&c->d_ip, B.ip) &&
        c->upload(&c->d_info, info) && c->upload(&c->d_patches, pdev) && c->upload(&c->d_J, Jm) &&
        c->upload(&c->d_sdnn, c->sdnn) && c->upload(&c->d_R, Rv) && c->upload(&c->d_wtab, wtab) &&
-       c->upload(&c->d_fix, fix) && c->upload(&c->d_gfix, gfix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
+       c->upload(&c->d_fix, fix) && c->upload(&c->d_fyfix, fyfix) && c->upload(&c->d_gfix, gfix) &&
+       c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) &&
        c->upload(&c->d_bc, bcs) && c->upload(&c->d_walls, walls) && c->upload(&c->d_recv, rinterp) &&
        c->upload(&c->d_rcopy, rcopy) && c->upload(&c->d_recv_all, recv) && c->upload(&c->d_cross_dst, cdst) &&
        c->upload(&c->d_cross_ptr, cptr) && c->upload(&c->d_cross_src, csrc) && c->upload(&c->d_dptr, dptr) &&
@@ -1575,6 +1592,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->h_bc = bcs;
   c->h_walls = walls;
   c->h_fix = fix;
+  c->h_fyfix = fyfix;
   c->h_gfix = gfix;
   c->h_fcopy1 = fc1;
   c->h_fcopy2 = fc2;
@@ -1584,6 +1602,7 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
   c->ndon = (int)dsrc.size();
   c->nwall = (int)wall.size();
   c->nfix = (int)fix.size();
+  c->nfyfix = (int)fyfix.size();
   c->ngfix = (int)gfix.size();
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
@@ -1599,7 +1618,8 @@ fc_status fc_init_patches(fc_ctx** out, const fc_patch_desc* patches, int npatch
        c->alloc(&c->d_R1, 4 * P) && c->alloc(&c->d_G, 16 * Pg) && c->alloc(&c->d_phi, P) && c->alloc(&c->d_S, P) &&
        c->alloc(&c->d_muhat, P) && c->alloc(&c->d_num, P) && c->alloc(&c->d_tmp, P) && c->alloc(&c->d_mu, P) &&
        c->alloc(&c->d_den, P) && c->alloc(&c->d_dt, 1) && c->alloc(&c->d_pmax, 2 * (size_t)npatch) &&
-       c->alloc(&c->d_flag, 1) && c->alloc(&c->d_skip_lines, 2) && c->alloc(&c->d_skip_flops, 2);
+       c->alloc(&c->d_flag, 1) && c->alloc(&c->d_skip_lines, 2) && c->alloc(&c->d_skip_flops, 2) &&
+       (jc2.empty() || c->alloc(&c->d_Fy, 4 * P));
   if (!ok) {
     fprintf(stderr, "fc_init_patches: %s\n", c->err.c_str());
     delete c;
@@ -1780,13 +1800,18 @@ void stage(fc_ctx* c, const StageCoef& sc, const double* mu, bool per_patch, cud
     launch_gen_fix(T, c->d_gfix, c->ngfix, e, mu, c->d_J, c->d_G, sg);
     c->launches++;
   }
-  run_queue(c, c->q_cart1, per_patch, st, "cart_q1",
-            [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q1(T, j, n, L, e, mu, c->d_R1, s); });
+  if (c->nfyfix) {
+    launch_flux_y_points(T, c->d_fyfix, c->nfyfix, e, c->d_Fy, st);
+    c->launches++;
+  }
+  run_queue(c, c->q_cart1, per_patch, st, "cart_q1", [&](const Job* j, int n, int L, cudaStream_t s) {
+    launch_cart_q1(T, j, n, L, e, mu, c->d_R1, c->d_Fy, s);
+  });
   run_queue(c, c->q_gen2, per_patch, sg, "gen_B",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_B(T, j, n, L, e, mu, c->d_J, c->d_G, s); },
             gside);
   run_queue(c, c->q_cart2, per_patch, st, "cart_q2",
-            [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q2(T, j, n, L, mu, c->d_R1, sc, s); });
+            [&](const Job* j, int n, int L, cudaStream_t s) { launch_cart_q2(T, j, n, L, mu, c->d_R1, c->d_Fy, sc, s); });
   run_queue(c, c->q_gen1, per_patch, sg, "gen_C",
             [&](const Job* j, int n, int L, cudaStream_t s) { launch_gen_C(T, j, n, L, c->d_J, c->d_G, sc, s); },
             gside);
@@ -2108,11 +2133,11 @@ fc_status fc_autotune(fc_ctx* c, int flags, double* report, void* stream) {
   if (!c->d_tune_jobs && !c->alloc(&c->d_tune_jobs, MAXT)) return fail(c, FC_ERR_OOM, c->err);
   Job* d_tj = c->d_tune_jobs;
   auto time_q1 = [&](const Job* jobs, int n, int Lmax) {
-    launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, st);  // warm-up
+    launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, c->d_Fy, st);  // warm-up
     float best = 1e30f;
     for (int r = 0; r < REPS; ++r) {
       cudaEventRecord(ea, st);
-      launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, st);
+      launch_cart_q1(c->T, jobs, n, Lmax, e, c->d_mu, c->d_R1, c->d_Fy, st);
       cudaEventRecord(eb, st);
       cudaEventSynchronize(eb);
       float ms = 0.f;
@@ -2645,9 +2670,11 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   std::vector<WallPt> walls;
   for (const WallPt& wp : c->h_walls)
     if (mine(wp.idx)) walls.push_back(wp);
-  std::vector<int> fix, fc1, fc2;
+  std::vector<int> fix, fc1, fc2, fyfix;
   for (int k : c->h_fix)
     if (mine(k)) fix.push_back(k);
+  for (int k : c->h_fyfix)
+    if (mine(k)) fyfix.push_back(k);
   for (int k : c->h_fcopy1)
     if (mine(k)) fc1.push_back(k);
   for (int k : c->h_fcopy2)
@@ -2711,7 +2738,7 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   std::vector<int> xsend_dst;
   for (const Recv& r : xsend) xsend_dst.push_back(r.dst);
   ok = ok && c->upload(&c->d_bc, bc) && c->upload(&c->d_walls, walls) && c->upload(&c->d_fix, fix) &&
-       c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) && c->upload(&c->d_gfix, gfix) &&
+       c->upload(&c->d_fyfix, fyfix) && c->upload(&c->d_fcopy1, fc1) && c->upload(&c->d_fcopy2, fc2) && c->upload(&c->d_gfix, gfix) &&
        c->upload(&c->d_recv, loc_interp) && c->upload(&c->d_rcopy, loc_copy) && c->upload(&c->d_xsend, xsend) &&
        c->upload(&c->d_xsend_dst, xsend_dst) &&
        c->upload(&c->d_xrecv, xrecv) &&
@@ -2724,6 +2751,7 @@ fc_status fc_shard(fc_ctx* c, int nranks, int rank, const int* owner, fc_comm_fn
   c->nbc = (int)bc.size();
   c->nwalls = (int)walls.size();
   c->nfix = (int)fix.size();
+  c->nfyfix = (int)fyfix.size();
   c->nfcopy1 = (int)fc1.size();
   c->nfcopy2 = (int)fc2.size();
   c->ngfix = (int)gfix.size();

@@ -149,10 +149,14 @@ struct DevTables {
 };
 
 // ---- launch wrappers (fc_kernels.cu) ----
+// Fy (nullable): the y fluxes of the affine points, written by the q1 pass (and by
+// launch_flux_y_points where no q1 line passes) and read by the q2 pass instead of
+// recomputing them from the state; null: the q2 pass computes them
 void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
-                    double* R1, cudaStream_t st);
+                    double* R1, double* Fy, cudaStream_t st);
 void launch_cart_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* mu, const double* R1,
-                    const StageCoef& sc, cudaStream_t st);
+                    const double* Fy, const StageCoef& sc, cudaStream_t st);
+void launch_flux_y_points(const DevTables& T, const int* idx, int n, const double* e, double* Fy, cudaStream_t st);
 void launch_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* G, cudaStream_t st);
 void launch_gen_B(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
                   const double* J, double* G, cudaStream_t st);

@@ -202,9 +202,10 @@ __device__ __forceinline__ void stage_write(const StageCoef& sc, long long p, lo
 
 // ---------------------------------------------------------------- affine patches, q1 lines
 // d/dx of e -> H_x = f_x(e) - mu d/dx e -> R1 = d/dx H_x  (J11 folded into J.scale = 1/hx)
+// Fy (nullable): the y fluxes of the line's points, from the same primitives, for the q2 pass
 __global__ void LINE_KERNEL_BOUNDS k_cart_q1(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                         const double* __restrict__ e, const double* __restrict__ mu,
-                                                        double* __restrict__ R1) {
+                                                        double* __restrict__ R1, double* __restrict__ Fy) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double2* A = sm + warp * (2 * Lmax + CONT_TMP);
@@ -223,7 +224,14 @@ __global__ void LINE_KERNEL_BOUNDS k_cart_q1(DevTables T, const Job* __restrict_
     for (int t = lane; t < J.n; t += 32) {
       const long long p = J.base + (long long)t * J.stride;
       double f[4];
-      flux_x(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+      if (Fy) {
+        double fy[4];
+        flux_xy(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f, fy);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Fy[p + c * cs] = fy[c];
+      } else {
+        flux_x(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+      }
       if (visc) {
         const double m = mu[p];
         const double2 g0 = A[t], g1 = A[L + t];
@@ -250,9 +258,10 @@ __global__ void LINE_KERNEL_BOUNDS k_cart_q1(DevTables T, const Job* __restrict_
 
 // ---------------------------------------------------------------- affine patches, q2 lines
 // d/dy of e -> H_y -> R2 = d/dy H_y; L = -(R1 + R2) (0 on PT_NODIFF points); stage combination.
+// Fy (nullable): the y fluxes written by the q1 pass, read instead of computed
 __device__ __forceinline__ void q2_line(const DevTables& T, const Job& J, const Plan& P, double2* A, int Lmax,
                                         const double* __restrict__ mu, const double* __restrict__ R1,
-                                        const StageCoef& sc, int lane) {
+                                        const double* __restrict__ Fy, const StageCoef& sc, int lane) {
   const long long cs = T.P;
   const double* e = sc.Ucur;
   const int L = P.L;
@@ -266,7 +275,12 @@ __device__ __forceinline__ void q2_line(const DevTables& T, const Job& J, const 
   for (int t = lane; t < J.n; t += 32) {
     const long long p = J.base + (long long)t * J.stride;
     double f[4];
-    flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+    if (Fy) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) f[c] = Fy[p + c * cs];
+    } else {
+      flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+    }
     if (visc) {
       const double m = mu[p];
       const double2 g0 = A[t], g1 = A[L + t];
@@ -297,13 +311,13 @@ __device__ __forceinline__ void q2_line(const DevTables& T, const Job& J, const 
 // one warp per line
 __global__ void LINE_KERNEL_BOUNDS k_cart_q2(DevTables T, const Job* __restrict__ jobs, int njobs, int Lmax,
                                                         const double* __restrict__ mu, const double* __restrict__ R1,
-                                                        StageCoef sc) {
+                                                        const double* __restrict__ Fy, StageCoef sc) {
   extern __shared__ double2 sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double2* A = sm + warp * (2 * Lmax + CONT_TMP);
   for (int ji = blockIdx.x * nw + warp; ji < njobs; ji += gridDim.x * nw) {
     const Job J = jobs[ji];
-    q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, sc, lane);
+    q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, Fy, sc, lane);
     FC_SYNC();
   }
 }
@@ -323,7 +337,8 @@ __host__ __device__ inline int tiled_stride(int Lmax) {
 }
 __global__ void __launch_bounds__(TW * 32, 5) k_cart_q2_tiled(DevTables T, const Job* __restrict__ jobs, int njobs,
                                                             int Lmax, const double* __restrict__ mu,
-                                                            const double* __restrict__ R1, StageCoef sc) {
+                                                            const double* __restrict__ R1,
+                                                            const double* __restrict__ Fy, StageCoef sc) {
   extern __shared__ double2 sm[];
   __shared__ int vflag[TW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -343,7 +358,7 @@ __global__ void __launch_bounds__(TW * 32, 5) k_cart_q2_tiled(DevTables T, const
     if (!tiled) {
       if (warp < nc) {
         const Job J = jobs[g0 + warp];
-        q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, sc, lane);
+        q2_line(T, J, T.plans[J.plan], A, Lmax, mu, R1, Fy, sc, lane);
       }
       __syncthreads();
       continue;
@@ -352,27 +367,38 @@ __global__ void __launch_bounds__(TW * 32, 5) k_cart_q2_tiled(DevTables T, const
     const int L = P.L, n = J0.n, st = J0.stride;
     if (threadIdx.x < TW) vflag[threadIdx.x] = 0;
     __syncthreads();
-    // rows of the TW columns: e into the line buffers, viscosity vote per column
+    // rows of the TW columns: the y fluxes (Fy) or e into the line buffers, viscosity
+    // vote per column
+    const double* src = Fy ? Fy : e;
     for (int k = threadIdx.x; k < n * TW; k += TW * 32) {
       const int r = k / TW, c = k % TW;
       if (c < nc) {
         const long long p = J0.base + c + (long long)r * st;
         if (mu[p] != 0.0) vflag[c] = 1;
         double2* Ac = sm + c * sA;
-        Ac[r] = cpx(e[p], e[p + cs]);
-        Ac[L + r] = cpx(e[p + 2 * cs], e[p + 3 * cs]);
+        Ac[r] = cpx(src[p], src[p + cs]);
+        Ac[L + r] = cpx(src[p + 2 * cs], src[p + 3 * cs]);
       }
     }
     __syncthreads();
     if (warp < nc) {
       const Job J = jobs[g0 + warp];
       const bool visc = vflag[warp] != 0;
-      if (visc) {  // gradient of e first; the flux then reads e again from memory
+      if (visc) {  // gradient of e first (e of this column again if the rows held Fy)
+        if (Fy) {
+          FC_SYNC();
+          load4(A, L, J, e, cs, lane);
+        }
         deriv2(A, Lmax, J, P, T, lane);
         for (int t = lane; t < n; t += 32) {
           const long long p = J.base + (long long)t * st;
           double f[4];
-          flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+          if (Fy) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f[c] = Fy[p + c * cs];
+          } else {
+            flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+          }
           const double m = mu[p];
           const double2 g0v = A[t], g1v = A[L + t];
           A[t] = cpx(fma(-m, g0v.x, f[0]), fma(-m, g0v.y, f[1]));
@@ -380,12 +406,14 @@ __global__ void __launch_bounds__(TW * 32, 5) k_cart_q2_tiled(DevTables T, const
         }
       } else {
         count_skip(T, 1, J, L, lane);
-        for (int t = lane; t < n; t += 32) {
-          const double2 a = A[t], b = A[L + t];
-          double f[4];
-          flux_y(a.x, a.y, b.x, b.y, T.gamma, f);
-          A[t] = cpx(f[0], f[1]);
-          A[L + t] = cpx(f[2], f[3]);
+        if (!Fy) {
+          for (int t = lane; t < n; t += 32) {
+            const double2 a = A[t], b = A[L + t];
+            double f[4];
+            flux_y(a.x, a.y, b.x, b.y, T.gamma, f);
+            A[t] = cpx(f[0], f[1]);
+            A[L + t] = cpx(f[2], f[3]);
+          }
         }
       }
       deriv2(A, Lmax, J, P, T, lane);
@@ -711,6 +739,18 @@ __global__ void k_rk_fixup(DevTables T, const int* __restrict__ idx, int n, Stag
 }
 
 // ---------------------------------------------------------------- boundary overwrite (Sec. 4.2)
+// y fluxes of listed affine points that no q1 line visits (read by the q2 pass)
+__global__ void k_flux_y_points(DevTables T, const int* __restrict__ idx, int n, const double* __restrict__ e,
+                                double* __restrict__ Fy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long p = idx[i], cs = T.P;
+  double f[4];
+  flux_y(e[p], e[p + cs], e[p + 2 * cs], e[p + 3 * cs], T.gamma, f);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Fy[p + c * cs] = f[c];
+}
+
 __global__ void k_bc(const BcPt* __restrict__ bc, int n, double* __restrict__ e, long long P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -2034,18 +2074,22 @@ static inline int grid_lines(const DevTables& T, int njobs, int Lmax) {
 static inline unsigned grid_pts(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void launch_cart_q1(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, const double* mu,
-                    double* R1, cudaStream_t st) {
+                    double* R1, double* Fy, cudaStream_t st) {
   if (njobs <= 0) return;
-  k_cart_q1<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, mu, R1);
+  k_cart_q1<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, e, mu, R1, Fy);
 }
 void launch_cart_q2(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* mu, const double* R1,
-                    const StageCoef& sc, cudaStream_t st) {
+                    const double* Fy, const StageCoef& sc, cudaStream_t st) {
   if (njobs <= 0) return;
   const size_t smem = (size_t)TW * tiled_stride(Lmax) * sizeof(double2);
   if (smem <= SMEM_CAP)
-    k_cart_q2_tiled<<<(njobs + TW - 1) / TW, TW * 32, smem, st>>>(T, jobs, njobs, Lmax, mu, R1, sc);
+    k_cart_q2_tiled<<<(njobs + TW - 1) / TW, TW * 32, smem, st>>>(T, jobs, njobs, Lmax, mu, R1, Fy, sc);
   else
-    k_cart_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, mu, R1, sc);
+    k_cart_q2<<<LINE_CFG(njobs, Lmax)>>>(T, jobs, njobs, Lmax, mu, R1, Fy, sc);
+}
+void launch_flux_y_points(const DevTables& T, const int* idx, int n, const double* e, double* Fy, cudaStream_t st) {
+  if (n <= 0) return;
+  k_flux_y_points<<<grid_pts(n, 256), 256, 0, st>>>(T, idx, n, e, Fy);
 }
 void launch_gen_A(const DevTables& T, const Job* jobs, int njobs, int Lmax, const double* e, double* G,
                   cudaStream_t st) {

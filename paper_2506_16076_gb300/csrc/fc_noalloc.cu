@@ -232,7 +232,7 @@ extern "C" fc_status fc_rhs_patch_noalloc(const double* e_dev, const double* mu_
   sc.Ucur = e_dev;
   sc.out = rhs_dev;
   sc.rhs_only = 1;
-  launch_cart_q1(T, jq1, n2, L[0], e_dev, mu_dev, R1, st);
-  launch_cart_q2(T, jq2, n1, L[1], mu_dev, R1, sc, st);
+  launch_cart_q1(T, jq1, n2, L[0], e_dev, mu_dev, R1, nullptr, st);  // no y-flux buffer: q2 computes the fluxes
+  launch_cart_q2(T, jq2, n1, L[1], mu_dev, R1, nullptr, sc, st);
   return cudaGetLastError() == cudaSuccess ? FC_OK : FC_ERR_CUDA;
 }
