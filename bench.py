@@ -240,7 +240,7 @@ def peaks():
 
 
 # the kernels and the host code that chooses their plans and launch shapes
-KERNEL_SOURCES = ["fc_kernels.cu", "fc_line.cuh", "fc_internal.h", "fc_host.cpp"]
+KERNEL_SOURCES = ["fc_kernels.cu", "fc_line.cuh", "fc_internal.h", "fc_host.cpp", "fc_tables.h"]
 
 
 def kernel_sources_sha():
