@@ -2349,12 +2349,12 @@ fc_status fc_pass_stats(const fc_ctx* c, const char* pass, double* flops, double
   const std::string n(pass);
   if (n == "cart_q1") {
     q = &c->q_cart1;
-    pw = 20.0;
-    bw = 72.0;    // read e (32) and mu (8), write R1 (32)
+    pw = 25.0;    // primitives once, x and y fluxes
+    bw = 104.0;   // read e (32) and mu (8), write R1 (32) and the y fluxes (32)
   } else if (n == "cart_q2") {
     q = &c->q_cart2;
-    pw = 52.0;
-    bw = 168.0;   // read e, mu, R1, one more stage operand; write the stage output
+    pw = 37.0;    // L assembly and stage combination (the y fluxes come from the q1 pass)
+    bw = 200.0;   // read the y fluxes, e, mu, R1, one more stage operand; write the stage output(s)
   } else if (n == "filter_q1" || n == "filter_q2") {
     q = n == "filter_q1" ? &c->q_filt1 : &c->q_filt2;
     rounds = 1;
