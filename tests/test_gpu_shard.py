@@ -66,10 +66,17 @@ def _run_sharded(gpu_lib, w, st0, owner, nranks):
     return ctxs, out
 
 
-@pytest.mark.parametrize("name,nranks", [("multi", 2), ("multi_adiabatic", 3), ("grid_curved", 2)])
+def _wall_form(w):
+    import dataclasses
+    return dataclasses.replace(w, params=dataclasses.replace(w.params, wall_form=1))
+
+
+@pytest.mark.parametrize("name,nranks", [("multi", 2), ("multi_adiabatic", 3), ("grid_curved", 2),
+                                         ("grid_curved_product_wall", 2)])
 def test_sharded_steps_equal_unsharded(gpu_lib, name, nranks):
     w = {"multi": W.small_multipatch, "multi_adiabatic": lambda: W.small_multipatch(W.ADIABATIC),
-         "grid_curved": W.small_multipatch_grid}[name]()
+         "grid_curved": W.small_multipatch_grid,
+         "grid_curved_product_wall": lambda: _wall_form(W.small_multipatch_grid())}[name]()
     st0 = W.random_smooth_state(w, seed=21, amp=0.05)
     owner = shard.partition(w, nranks)
     assert sorted(set(owner)) == list(range(nranks))

@@ -4,17 +4,19 @@ inputs: the RHS with a given viscosity on the O-grid, on the curved, twisted GRI
 and on the S-type arcs (1e-11 relative per component, as every RHS evaluation), ten
 steps of Algorithm 1 with viscosity, filter and CFL step (1e-9), the wall patches' RHS
 against the flux form's (different there, identical on every other patch), and the
-discrete adjoint of a step with and without the filter (1e-11). The oracle's
+discrete adjoint of a step with and without the filter (1e-11), and the wall-drag
+gradients through the checkpointed adjoint against central differences. The oracle's
 product-rule form is pinned against a symbolic operator of a manufactured state, its
 transpose by dot-product identities (tests/test_oracle_wall_form.py)."""
 import dataclasses
+import math
 
 import numpy as np
 import pytest
 import torch
 
 from oracle import adjoint as A, solver as S
-from paper_2506_16076_gb300 import workloads as W
+from paper_2506_16076_gb300 import adjoint as ADJ, workloads as W
 from tests.gpu_helpers import from_dev, rel_err, smooth_mu, to_dev, to_dev_scalar_field
 
 pytestmark = pytest.mark.gpu
@@ -150,3 +152,37 @@ def test_affine_wall_patch_is_refused(gpu_lib):
     with pytest.raises(gpu_lib.FcError):
         gpu_lib.Context(w)
     gpu_lib.Context(_pform(w, 0))  # the flux form accepts it
+
+
+def _m2_wall(mach=2.0, alpha_deg=2.0):
+    # the small cylinder with the no-slip adiabatic wall under a Mach-M stream at angle alpha
+    w = W.small_multipatch(W.ADIABATIC)
+    a = math.radians(alpha_deg)
+    fs = (1.4, mach * math.cos(a), mach * math.sin(a), 1.0)
+    pts = [dataclasses.replace(p, bc=(fs,) * 4) for p in w.patches]
+    return _pform(W.Workload(f"small_M{mach}_wall", pts, w.params, fs, "freestream", 10))
+
+
+def test_drag_gradients_vs_central_differences(gpu_lib):
+    # dJ/dM and dJ/dalpha of the wall drag after a few steps with the viscosity and the
+    # steps frozen (the checkpointed adjoint through the product-rule wall patch) against
+    # central differences of the same frozen march
+    nsteps, K, h = 6, 3, 1e-6
+    w = _m2_wall()
+    ctx = gpu_lib.Context(w)
+    J, dJdM, dJda, dJdrho, tr = ADJ.drag_gradients(w, ctx, to_dev(W.initial_state(w)), nsteps, K)
+
+    def J_frozen(mach, alpha):
+        ww = _m2_wall(mach, alpha)
+        c = gpu_lib.Context(ww)
+        e = to_dev(W.initial_state(ww))
+        for n in range(nsteps):
+            c.rk_step(e, tr.dts[n], tr.mus[n], gpu_lib.STEP_FROZEN_MU | gpu_lib.STEP_FIXED_DT)
+        return ADJ.drag(c, e)[0].item()
+
+    assert abs(J_frozen(2.0, 2.0) - J) <= 1e-12 * max(abs(J), 1.0)
+    fdM = (J_frozen(2.0 + h, 2.0) - J_frozen(2.0 - h, 2.0)) / (2 * h)
+    assert abs(fdM - dJdM) <= 1e-5 * max(abs(dJdM), 1e-3), (fdM, dJdM)
+    ha = math.degrees(h)
+    fda = (J_frozen(2.0, 2.0 + ha) - J_frozen(2.0, 2.0 - ha)) / (2 * h)
+    assert abs(fda - dJda) <= 1e-5 * max(abs(dJda), 1e-3), (fda, dJda)
