@@ -144,13 +144,15 @@ class ShardedOracle:
         return u[5], dt
 
 
-def _rank_main(rank, world, port, owner):
+def _rank_main(rank, world, port, owner, wall_form):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import solver as S
         from paper_2506_16076_gb300 import shard, workloads as W
+        import dataclasses
         w = W.small_multipatch(W.ADIABATIC)
+        w = dataclasses.replace(w, params=dataclasses.replace(w.params, wall_form=wall_form))
         st0 = W.random_smooth_state(w, seed=23, amp=0.05)
         so = ShardedOracle(w, owner, rank, shard.DistComm())
         st, dts = st0, []
@@ -167,8 +169,10 @@ def _rank_main(rank, world, port, owner):
         dist.destroy_process_group()
 
 
-def test_sharded_oracle_steps_over_gloo_equal_single_domain():
+@pytest.mark.parametrize("wall_form", [0, 1])
+def test_sharded_oracle_steps_over_gloo_equal_single_domain(wall_form):
+    # wall_form 1: the product-rule form of the adiabatic wall patch (Remark adiabatic)
     from paper_2506_16076_gb300 import shard, workloads as W
     owner = shard.partition(W.small_multipatch(W.ADIABATIC), 2)
     assert sorted(set(owner)) == [0, 1]
-    mp.spawn(_rank_main, args=(2, _free_port(), owner), nprocs=2, join=True)
+    mp.spawn(_rank_main, args=(2, _free_port(), owner, wall_form), nprocs=2, join=True)
