@@ -2,7 +2,7 @@
 // context's plan builder (fc_host.cpp) and the allocation-free entry (fc_noalloc.cu).
 //
 // A twiddle w = (c, s) is stored in ratio form: w = S (1 + i t) with S = c, t = s / c
-// when |c| >= |s|, else w = S i (1 - i t') with S = s, t' = -c / s (flag set), so that
+// when |c| >= |s|, else w = S i (1 + i t) with S = s, t = -c / s (flag set), so that
 // w b = S u with u = b' + i t b' (b' = b, or i b when flagged): two FMAs, |t| <= 1 and
 // |S| >= 1/sqrt 2, the real factor S left to the butterfly's FMAs.
 //

@@ -27,6 +27,11 @@
 //     the continuation length the library picks for every line length N0..N1
 //     (choose_continuation), one "N C" pair per line.
 //
+//   line_engine_host records L1 L2 ...
+//     the FMA-form butterfly records of every candidate stage order (fc_tables.h) read
+//     back and checked against the twiddles they encode; prints "L order max_err max_t
+//     min_S" per candidate.
+//
 //   line_engine_host adw d
 //     the no-slip adiabatic wall weights (adiabatic_weights) for d, one per line.
 //
@@ -39,7 +44,9 @@
 #include "../paper_2506_16076_gb300/csrc/fc_host.cpp"
 #include "../paper_2506_16076_gb300/csrc/fc_line.cuh"
 
+#include <complex>
 #include <cstdio>
+#include <cstring>
 #include <random>
 
 namespace {
@@ -56,6 +63,97 @@ void derive(double2* A, int Lmax, const fcx::Plan& P, int n, int C, int fcm, dou
   else
     mul_deriv_slot(A, P.L, 2, scale * TWO_PI / ((double)P.L * (double)P.L), B.rp.data() + P.dmul, 0, 1);
   fft_inplace<true>(A, P, 2, B.tw.data(), B.rp.data(), 0, 1);
+}
+
+// the FMA-form records of every candidate stage order of each length (fc_tables.h), read
+// back in the device kernels' order: each twiddle rebuilt from its ratio form against
+// exp(+-2 pi i e / L), the inverse records with their stored scales S (S3 = (S3/S1) S1 and
+// so on), the forward rotations up to their real factor; prints "L order max_err max_t min_S"
+int run_records(int argc, char** argv) {
+  using namespace fcx;
+  fc_ctx c;
+  Builder B{&c};
+  const long double PI = 3.14159265358979323846264338327950288L;
+  for (int a = 2; a < argc; ++a) {
+    const int L = atoi(argv[a]);
+    const int pi = B.plan(L);
+    for (const Plan& P : B.cands[pi]) {
+      long double err = 0, tmax = 0, smin = 1e30L;
+      auto rebuild = [&](long double S, long double t, bool f) {  // S (1 + i t) or S i (1 + i t)
+        tmax = std::max(tmax, fabsl(t));
+        return f ? std::complex<long double>(-S * t, S) : std::complex<long double>(S, S * t);
+      };
+      // inverse records
+      const double2* rec = B.tw.data() + P.fmd;
+      int span = 1;
+      for (int st = P.nst - 1; st >= 0; --st) {
+        const int R = P.rad[st];
+        if (span > 1 && (R == 2 || R == 4 || R == 8)) {
+          const int RS = R == 2 ? 2 : (R == 4 ? 4 : 8);
+          const int tws = L / (R * span);
+          for (int j = 0; j < span; ++j) {
+            const double2* q = rec + j * RS;
+            long long fl;
+            memcpy(&fl, &q[0].x, sizeof(fl));
+            long double t[8] = {0}, S[8] = {1};
+            t[1] = q[0].y;
+            if (R == 2) {
+              S[1] = q[1].x;
+            } else if (R == 4) {
+              t[2] = q[1].x, t[3] = q[1].y, S[2] = q[2].x, S[1] = q[2].y, S[3] = (long double)q[3].x * S[1];
+            } else {
+              t[2] = q[1].x, t[3] = q[1].y, t[4] = q[2].x, t[5] = q[2].y, t[6] = q[3].x, t[7] = q[3].y;
+              S[4] = q[4].x, S[2] = q[4].y, S[1] = q[7].x;
+              S[6] = (long double)q[5].x * S[2], S[5] = (long double)q[5].y * S[1];
+              S[3] = (long double)q[6].y * S[1], S[7] = (long double)q[6].x * S[3];
+              err = std::max(err, fabsl((long double)q[7].y - S[1] * 0.70710678118654752440L));
+            }
+            for (int r = 1; r < R; ++r) {
+              smin = std::min(smin, fabsl(S[r]));
+              const long double ang = 2.0L * PI * (long double)(((long long)r * j * tws) % L) / L;
+              const std::complex<long double> w = rebuild(S[r], t[r], (fl >> (r - 1)) & 1);
+              err = std::max(err, std::abs(w - std::complex<long double>(cosl(ang), sinl(ang))));
+            }
+          }
+          rec += span * RS;
+        }
+        span *= R;
+      }
+      // forward rotation records (factors folded elsewhere): direction only
+      rec = B.tw.data() + P.fmf;
+      span = L;
+      for (int st = 0; st < P.nst; ++st) {
+        const int R = P.rad[st];
+        span /= R;
+        if (R == 2 || R == 4 || R == 8) {
+          const int tws = L / (R * span);
+          if (span > 1) {
+            for (int j = 0; j < span; ++j) {
+              const double2* h = rec + j * (R / 2);
+              long long fl;
+              memcpy(&fl, &h[0].x, sizeof(fl));
+              for (int r = 1; r < R; ++r) {
+                const double tr = r == 1 ? h[0].y : (r % 2 == 0 ? h[r / 2].x : h[r / 2].y);
+                const std::complex<long double> d = rebuild(1.0L, tr, (fl >> (r - 1)) & 1);
+                const long double ang = -2.0L * PI * (long double)(((long long)r * j * tws) % L) / L;
+                const std::complex<long double> w(cosl(ang), sinl(ang));
+                err = std::max(err, fabsl(std::imag(w * std::conj(d))) / std::abs(d));
+              }
+            }
+            rec += span * (R / 2);
+          }
+          rec += (L / R) * (R / 2);
+        } else if ((P.fmod >> st) & 1) {
+          const int H = (R - 1) / 2;
+          rec += (L / R) * ((2 * H + 2 * H * H + 1) / 2);
+        }
+      }
+      printf("%d ", L);
+      for (int s = 0; s < P.nst; ++s) printf("%s%d", s ? "." : "", P.rad[s]);
+      printf(" %.3Le %.6Lf %.6Lf\n", err, tmax, smin == 1e30L ? 1.0L : smin);
+    }
+  }
+  return 0;
 }
 
 int run_plans(int argc, char** argv) {
@@ -264,6 +362,7 @@ int run_adw(char** argv) {
 
 int main(int argc, char** argv) {
   if (argc >= 2 && std::string(argv[1]) == "plans") return run_plans(argc, argv);
+  if (argc >= 2 && std::string(argv[1]) == "records") return run_records(argc, argv);
   if (argc == 4 && std::string(argv[1]) == "fc") return run_fc(argv[2], argv[3]);
   if (argc == 4 && std::string(argv[1]) == "grid") return run_grid(argv[2], argv[3]);
   if (argc == 7 && std::string(argv[1]) == "policy") return run_policy(argv);

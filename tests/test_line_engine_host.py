@@ -63,6 +63,21 @@ def test_every_candidate_stage_order_differentiates_exactly(harness):
     assert float(worst[2]) < 2e-14, worst
 
 
+def test_fma_records_encode_their_twiddles(harness):
+    # the ratio-form records of the FMA butterflies (every candidate stage order): each
+    # twiddle rebuilt from S, t and its flag equals exp(+-2 pi i e / L) to rounding, with
+    # |t| <= 1 and |S| >= 1/sqrt 2 (the bounds that keep the ratio form accurate)
+    exe, env = harness
+    lengths = [L for L in range(16, 1200) if _smooth7(L)] + [4096, 2187, 3125, 2401]
+    r = subprocess.run([exe, "records", *map(str, lengths)], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    rows = [ln.split() for ln in r.stdout.splitlines()]
+    assert len(rows) >= len(lengths)
+    assert max(float(x[2]) for x in rows) < 1e-15, max(rows, key=lambda x: float(x[2]))
+    assert max(float(x[3]) for x in rows) <= 1.0 + 1e-15
+    assert min(float(x[4]) for x in rows) >= 0.7071067
+
+
 ALPHA_F, P_F = 10.0, 14  # the paper's filter parameters (Sec. 4.3.1)
 
 
