@@ -16,12 +16,16 @@ long-double data, pinned against the explicit sum of its definition.
 
 Modules:
   fc         FC-Gram continuation, derivative, filter (Sec. 2.2, Sec. 4.3)
-  euler      Euler fluxes, EOS, sound speed, MWSB, proxy (Sec. 2.1, Sec. 5.1)
+  euler      Euler fluxes, EOS, sound speed, MWSB, proxy (Sec. 2.1, Sec. 5.1); the product
+             rules of the adiabatic-wall form (Remark adiabatic)
   geometry   patches, metrics, fringes, donors, Neville interpolation (Sec. 3)
   viscosity  SDNN stand-in classification, preliminary viscosity, SB operator (Sec. 5)
-  solver     semi-discrete operator L, SSPRK(5,4) step, BCs, exchange, dt (Sec. 4, Alg. 1)
+  solver     semi-discrete operator L (flux form; product-rule form on adiabatic wall
+             patches when Params.wall_form = 1), SSPRK(5,4) step, BCs, exchange, dt
+             (Sec. 4, Alg. 1)
   riemann    exact Riemann solver for the shock-tube pin (textbook; not in the paper)
-  adjoint    discrete adjoint of the stage/step with mu and dt frozen
+  adjoint    discrete adjoint of the stage/step with mu and dt frozen (either wall form;
+             the product-rule form's pointwise Jacobian by the complex step)
 
 Parity unpinned: the SDNN stand-in classifier (the paper's network and weights
 are not published) is pinned only against its own training labels and the
